@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Benchmark of the probe side of the adaptive geospatial join on one GB300.
+
+Workload (city-scale plain join): 300 Voronoi polygons (20-400 vertices)
+tiling a 45 km x 50 km box and 1e8 FP64 points from a 32-cluster Gaussian
+mixture plus 20 % uniform noise (seeded, synthetic stand-ins for the paper's
+NYC neighbourhoods and taxi points).  One step joins the same device-resident
+points twice: once against the approximate index (eps = 4 m) and once
+against the exact index (trained on a 1 % sample), so `value` counts 2 n
+point-joins per step.  Points (1.6 GB) exceed L2, so no flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank holds its own index replica and joins its own 1e8
+points (weak scaling); the join has no collective.  `--impl reference` times
+the CPU oracle (the reference for this method) on bounded samples of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "points joined/sec at 1 GB300 (approx eps and exact) vs plain join; p50/p99 latency"
+LAUNCHES_PER_STEP = {"approx": 2, "exact": 6}   # k_zero + k_join_approx; k_zero + probe + scan + scatter + pip + csr
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-points", type=int, default=100_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def workload(n: int, rank: int):
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c2_city_polygons()
+    seed = 3 + 1000 * rank
+    pts = synth.points_mixture(n, synth.BOX_CITY, seed=seed, dist_seed=3)
+    train = synth.points_mixture(max(n // 100, 1000), synth.BOX_CITY, seed=4, dist_seed=3)
+    return polys, pts, train
+
+
+def cpu_oracle_rate(polys, cells, ro, refs, pts, budget_s: float = 12.0):
+    """Oracle points/s on the host cores for approx (sorted-vector probe of the
+    logical covering) and exact (grid-prefiltered brute force), each on a
+    bounded prefix sample of the same points sized to ~budget_s/2 seconds."""
+    import oracle
+    ps = oracle.PolySet(polys)
+    cores = os.cpu_count() or 1
+    out = {}
+    for mode in ("approx", "exact"):
+        m = 20000
+        while True:
+            t0 = time.perf_counter()
+            if mode == "approx":
+                oracle.join_approx_logical(cells, ro, refs, pts[:m])
+            else:
+                ps.join_exact(pts[:m])
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 8 or m >= len(pts):
+                break
+            m = min(len(pts), int(m * max(2.0, (budget_s / 2) / max(dt, 1e-3))))
+        out[mode] = {"points": m, "seconds": dt, "rate": m / dt}
+    # one step = an approx join and an exact join of the same points
+    t_step_per_point = 1.0 / out["approx"]["rate"] + 1.0 / out["exact"]["rate"]
+    return {"value": 2.0 / t_step_per_point, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "sample": (f"approx: sorted-vector probe on the first {out['approx']['points']} points; exact: "
+                       f"grid-prefiltered brute force on the first {out['exact']['points']} points; "
+                       f"{cores} threads; rate = 2 / (1/approx + 1/exact)"),
+            "per_mode_points_per_s": {k: v["rate"] for k, v in out.items()}}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import paper_1802_09488_gb300 as agj
+    n = min(args.n_points, 20_000_000)
+    polys, pts, train = workload(n, 0)
+    ix = agj.Index(polys, agj.APPROX, 4.0, host_only=True)
+    cells, ro, refs = ix.logical()
+    import oracle
+    ps = oracle.PolySet(polys)
+    cores = os.cpu_count() or 1
+    # size each step's sample to ~6 s of CPU work
+    m = 200_000
+    t0 = time.perf_counter()
+    oracle.join_approx_logical(cells, ro, refs, pts[:m])
+    ps.join_exact(pts[:m])
+    dt = time.perf_counter() - t0
+    m = int(min(n, max(50_000, m * 6.0 / max(dt, 1e-3))))
+    times = []
+    for it in range(args.warmup + args.steps):
+        sl = pts[(it * 7919) % max(1, n - m):][:m]
+        t0 = time.perf_counter()
+        oracle.join_approx_logical(cells, ro, refs, sl)
+        ps.join_exact(sl)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = 2.0 * m * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "c2-city-300polys-mixture-points", "eps_m": 4.0, "exact_train": "1% sample",
+                       "step": "approx join + exact join of the same points",
+                       "reference": "CPU oracle (oracle/oracle.c) on the host cores, bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{m} points per step (approx sorted-vector probe + exact brute force), "
+                                       f"{cores} threads"},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    import paper_1802_09488_gb300 as agj
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.n_points
+    polys, pts_np, train = workload(n, rank)
+    t0 = time.perf_counter()
+    ia = agj.Index(polys, agj.APPROX, 4.0)
+    ie = agj.Index(polys, agj.EXACT, 0.0, train=train)
+    build_s = time.perf_counter() - t0
+    d_pts = torch.from_numpy(pts_np).cuda()
+    pa, pe = agj.Pairs(ia, n), agj.Pairs(ie, n)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 0)):
+        agj.join(ia, d_pts, pa)
+        agj.join(ie, d_pts, pe)
+    nnz_a, nnz_e = pa.check(), pe.check()
+    st_a = pa.status.cpu().numpy().view(np.uint64)
+    st_e = pe.status.cpu().numpy().view(np.uint64)
+    gathers_per_pt = float(st_a[3]) / n
+    cands_per_pt = float(st_e[2]) / n
+
+    barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.4)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        agj.join(ia, d_pts, pa)
+        ev[k][1].record(stream)
+        agj.join(ie, d_pts, pe)
+        ev[k][2].record(stream)
+    barrier()
+    clk = clocks.stop()
+    approx_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    exact_ms = [b.elapsed_time(c) for _, b, c in ev]
+    total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # correctness of the timed runs
+    assert pa.check() == nnz_a and pe.check() == nnz_e
+
+    value = world * 2.0 * n * args.steps / (total_ms / 1000.0)
+    peaks = measured_peaks()
+    k_pts = nnz_a / n
+    bytes_per_pt = 16 + 8 * gathers_per_pt + 4 + 4 * k_pts
+    t_approx_s = statistics.mean(approx_ms) / 1000.0
+    achieved = bytes_per_pt * n / t_approx_s / 1e9
+    roofline = {"kernel": "k_join_approx", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peaks["source"],
+                "algorithmic_bytes_per_point": bytes_per_pt,
+                "note": "bytes = 16 (point) + 8 x trie entries read + 4 (offset) + 4 x pairs, per point"}
+
+    def pct(v, q):
+        s = sorted(v)
+        return s[min(len(s) - 1, int(round(q / 100.0 * (len(s) - 1))))]
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c2-city-300polys-1e8-mixture-points", "n_points_per_gpu": n, "polygons": len(polys),
+                   "eps_m": 4.0, "exact_train_points": len(train), "step": "approx join + exact join of the same points",
+                   "l2": "inputs (16 B x 1e8 = 1.6 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+        "modes": {
+            "approx": {"points_per_s": n / (statistics.mean(approx_ms) / 1000.0), "p50_ms": pct(approx_ms, 50),
+                       "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_per_pt},
+            "exact": {"points_per_s": n / (statistics.mean(exact_ms) / 1000.0), "p50_ms": pct(exact_ms, 50),
+                      "p99_ms": pct(exact_ms, 99), "nnz": nnz_e, "candidates_per_point": cands_per_pt},
+        },
+        "index": {"approx": ia.stats(), "exact": ie.stats(), "build_s": build_s},
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": args.steps * (LAUNCHES_PER_STEP["approx"] + LAUNCHES_PER_STEP["exact"]),
+    }
+
+    if not args.no_e2e:
+        # end to end through the public host API: pinned host points in,
+        # host CSR out, both modes per step
+        h_pts = torch.from_numpy(pts_np).pin_memory()
+        h_off = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+        h_ids_a = torch.empty(max(nnz_a, 1), dtype=torch.int32).pin_memory()
+        h_ids_e = torch.empty(max(nnz_e, 1), dtype=torch.int32).pin_memory()
+        staging = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+        ksteps = max(2, min(args.steps, 5))
+        agj.join_host(ia, h_pts, pa, staging, h_off, h_ids_a)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            agj.join_host(ia, h_pts, pa, staging, h_off, h_ids_a)
+            agj.join_host(ie, h_pts, pe, staging, h_off, h_ids_e)
+        barrier()
+        dt = time.perf_counter() - t0
+        e2e_val = world * 2.0 * n * ksteps / dt
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_val = world * 2.0 * n * ksteps / float(t.item())
+        result["e2e"] = {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": 2 * 16 * n,
+                         "d2h_bytes_per_step": 2 * 4 * (n + 1) + 4 * (nnz_a + nnz_e) + 2 * 32, "steps": ksteps}
+        del staging, h_pts
+
+    if rank == 0 and not args.no_cpu_baseline:
+        cells, ro, refs = ia.logical()
+        result["cpu_baseline"] = cpu_oracle_rate(polys, cells, ro, refs, pts_np)
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+if __name__ == "__main__":
+    main()

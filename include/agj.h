@@ -1,0 +1,255 @@
+/*
+ * agj.h — C ABI of the GB300-native adaptive geospatial join (probe side).
+ *
+ * Method: Kipf et al., "Adaptive Geospatial Joins for Modern Hardware".
+ *   §III-A  five phases: build logical index, build physical index, training,
+ *           probe, refine; parameters: precision (metres) and memory budget.
+ *   §III-B  logical index = "super covering" of coverings and interior
+ *           coverings with precision-preserving conflict resolution
+ *           (Listing "Build super covering").
+ *   §III-C  physical index = Adaptive Cell Trie (256-ary radix tree over cell
+ *           ids, tagged 8-byte entries) + lookup table of reference lists.
+ *   §III-D  training on historical points.
+ *   §III-E  probe (Listings "Probe Adaptive Cell Trie", "The probe algorithm").
+ *
+ * Conventions for every entry point:
+ *   - returns AGJ_OK (0) or a positive AGJ_E* status; agj_strerror() names it;
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are CPU memory (pinned memory makes copies
+ *     asynchronous, pageable memory is accepted too);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); work is enqueued on it and runs asynchronously unless the
+ *     entry point says it synchronises;
+ *   - points are n x {lat, lng} FP64 degrees, interleaved (16 bytes per point,
+ *     16-byte aligned); a point is valid iff both are finite, |lat| <= 90 and
+ *     |lng| <= 180; an invalid point joins no polygon (an empty CSR row) and
+ *     is not an error;
+ *   - polygon ids are input positions 0 .. n_polys-1 (fewer than 2^30 - 1,
+ *     §III-C: 30-bit payloads).
+ */
+#ifndef AGJ_H
+#define AGJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------------- */
+/* status codes                                                             */
+/* ---------------------------------------------------------------------- */
+#define AGJ_OK            0
+#define AGJ_EINVAL        1   /* null pointer, bad size, malformed polygon, invalid vertex */
+#define AGJ_EUNSUPPORTED  2   /* polygon not within one cube face, >= 2^30-1 polygons */
+#define AGJ_EBUDGET       3   /* approximate index would exceed the memory budget (§III-A) */
+#define AGJ_ENOMEM        4   /* host or device allocation failed */
+#define AGJ_ECUDA         5   /* a CUDA runtime call failed */
+#define AGJ_ETIMEOUT      6   /* a bounded device wait gave up (device status word) */
+#define AGJ_EBUSY         7   /* server admission refused (queue or memory full) */
+#define AGJ_ECAPACITY     8   /* output or scratch buffer too small for this join */
+#define AGJ_EDEVICE       9   /* a device-side bounds check failed (index corrupt) */
+
+const char* agj_strerror(int status);
+
+/* Human-readable reason of the calling thread's last agj_build failure
+ * ("" if none); valid until the thread's next agj_build. */
+const char* agj_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* polygons and index build (host)                                          */
+/* ---------------------------------------------------------------------- */
+
+/* One simple polygon: a ring of n_vertices >= 3 (lat, lng) degree pairs,
+ * implicitly closed, either orientation, all on one cube face.  Edges are
+ * geodesics (straight in the face's gnomonic (u,v) plane).  ST_Covers
+ * semantics (§II): points on edges and vertices are inside. */
+typedef struct {
+    uint32_t n_vertices;
+    const double* latlng;      /* host, 2 * n_vertices doubles */
+} agj_polygon;
+
+typedef enum {
+    AGJ_APPROX = 0,   /* §III-A approximate join: candidate cells refined until
+                         their diagonal is below the precision; no PIP */
+    AGJ_EXACT  = 1    /* §III-A exact join: trained index + PIP on candidates */
+} agj_mode;
+
+/* Build options; zero-initialise and set what you need.  0 selects the
+ * default noted beside each field. */
+typedef struct {
+    uint32_t max_cover_cells;     /* 0 -> 128 (§V defaults) */
+    uint32_t max_cover_level;     /* 0 -> 30  */
+    uint32_t max_interior_cells;  /* 0 -> 256 */
+    uint32_t max_interior_level;  /* 0 -> 20  */
+    uint64_t memory_budget_bytes; /* 0 -> unlimited in approx mode; in exact
+                                     mode 4x the untrained trie size */
+    const double* train_latlng;   /* host, exact mode: training points (§III-D), may be NULL */
+    uint64_t n_train;
+    uint32_t max_train_level;     /* 0 -> 24 */
+    uint32_t n_threads;           /* host build threads, 0 -> all cores */
+    uint32_t host_only;           /* 1: build the host index only, no device copy
+                                     (for inspection; agj_join then returns AGJ_EINVAL) */
+} agj_build_opts;
+
+typedef struct agj_index agj_index;
+
+/*
+ * Builds the logical index (coverings + interior coverings merged by the
+ * super-covering listing, §III-B), refines it (approx: candidate cells split
+ * until diagonal + 2e-5 m < precision_m, §III-A; exact: training, §III-D),
+ * builds the Adaptive Cell Trie and lookup table (§III-C) on the host and
+ * copies them, with the polygons' face (u,v) vertices for refinement, to
+ * the current device on `stream` (the call synchronises on `stream` before
+ * returning).  precision_m is used in approx mode only.
+ * Ownership: *out is owned by the caller and released with agj_free.
+ * Errors: AGJ_EINVAL (null, n_vertices < 3, invalid vertex, precision_m <= 0
+ * in approx mode), AGJ_EUNSUPPORTED (polygon spans faces, too many
+ * polygons), AGJ_EBUDGET (approx index above memory_budget_bytes),
+ * AGJ_ENOMEM, AGJ_ECUDA.
+ */
+int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, agj_mode mode,
+              const agj_build_opts* opts, void* stream, agj_index** out);
+
+/* Releases the index and its device memory (synchronises the device). */
+void agj_free(agj_index* index);
+
+typedef struct {
+    uint32_t mode;             /* agj_mode */
+    uint32_t n_polys;
+    uint64_t n_cells;          /* logical cells (super covering) */
+    uint64_t n_cand_cells;     /* cells with >= 1 candidate reference */
+    uint64_t n_nodes;          /* trie nodes (256 x 8 bytes each) */
+    uint64_t n_lut_words;      /* lookup-table uint32 words */
+    uint64_t device_bytes;     /* bytes resident on the device */
+    uint32_t max_refs;         /* largest reference list of a cell */
+    uint32_t max_cand_refs;    /* largest candidate list of a cell */
+    uint32_t max_depth;        /* deepest trie level below the face roots */
+    uint32_t max_level;        /* finest cell level */
+    double   build_seconds;
+} agj_stats;
+
+int agj_index_stats(const agj_index* index, agj_stats* out);
+
+/*
+ * Copies the logical index (the super covering) to host arrays: cells
+ * ascending by id, cell k's references refs[ref_off[k] .. ref_off[k+1]) with
+ * ref = polygon_id << 1 | interior (§III-B "polygon reference").  Call with
+ * NULL arrays to query n_cells and n_refs; then with arrays of those sizes
+ * (cells: n_cells, ref_off: n_cells + 1, refs: n_refs).
+ */
+int agj_index_logical(const agj_index* index, uint64_t* cells, uint64_t* ref_off, uint32_t* refs,
+                      uint64_t* n_cells, uint64_t* n_refs);
+
+/*
+ * The super-covering merge alone (§III-B, Listing "Build super covering"),
+ * for callers that bring their own coverings: inserts (cells[k], refs[k]) in
+ * order (ref = polygon_id << 1 | interior); a duplicate cell merges
+ * references, an ancestor/descendant conflict replaces the ancestor c1 by
+ * the descendant c2 plus the difference cells d (3 per level between them),
+ * all carrying c1's references, and c2 also gets the new reference.  When
+ * one polygon is referenced both as true and as candidate, true wins.
+ * Output: out_cells ascending, out_refs[out_off[k] .. out_off[k+1]).  Call
+ * with NULL outputs to get *n_out_cells and *n_out_refs first.  Host only.
+ */
+int agj_supercover(const uint64_t* cells, const uint32_t* refs, uint64_t n, uint64_t* out_cells, uint64_t* out_off,
+                   uint32_t* out_refs, uint64_t* n_out_cells, uint64_t* n_out_refs);
+
+/*
+ * The lookup-table encoding (§III-C "Lookup table") the trie uses for
+ * cells with more than two references: list k (refs[ref_off[k] ..
+ * ref_off[k+1]), ref = polygon_id << 1 | interior, in the caller's order) is
+ * stored as [n_true, true ids..., n_cand, candidate ids...] in one uint32
+ * array, each distinct list once; offsets[k] = its word offset.  Call with
+ * words == NULL to get *n_words first.  Host only.
+ */
+int agj_lut_encode(const uint32_t* refs, const uint64_t* ref_off, uint64_t n_lists, uint32_t* words,
+                   uint64_t* offsets, uint64_t* n_words);
+
+/* Copies the flattened trie to host: nodes (n_nodes * 256 uint64 tagged
+ * entries), the lookup table (n_lut_words) and the face table (6 x
+ * {root node or 0xFFFFFFFF, prefix length in key bits, prefix}).  NULL arrays
+ * are skipped. */
+int agj_index_trie(const agj_index* index, uint64_t* nodes, uint32_t* lut, uint64_t face_table[18]);
+
+/* ---------------------------------------------------------------------- */
+/* the probe: join points against an index (device)                         */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Output of a join as CSR: the polygon ids joined with point p are
+ * ids[offsets[p] .. offsets[p+1]), ascending and unique; offsets[n] = nnz.
+ * All buffers are device memory.  `scratch` is device work space used by
+ * the join (tile states of the one-pass scan, candidate queues in exact
+ * mode); its size comes from agj_join_requirements.
+ */
+typedef struct {
+    uint32_t* offsets;        /* n + 1 */
+    uint32_t* ids;            /* ids_capacity */
+    uint64_t  ids_capacity;
+    void*     scratch;        /* scratch_bytes, 256-byte aligned */
+    uint64_t  scratch_bytes;
+    uint64_t* status;         /* 4 x uint64 device words: [0] nnz, [1] error flags,
+                                 [2] candidate pairs refined (exact mode),
+                                 [3] trie node entries read by the walk */
+} agj_pairs;
+
+typedef struct {
+    uint64_t ids_capacity;    /* ids that any join of n points can produce */
+    uint64_t scratch_bytes;
+} agj_requirements;
+
+/* Sizes of the buffers a join of up to n points needs (host only). */
+int agj_join_requirements(const agj_index* index, uint64_t n, agj_requirements* out);
+
+/* Allocates an agj_pairs for up to n points with cudaMallocAsync on
+ * `stream`; release with agj_pairs_free on a stream ordered after use. */
+int agj_pairs_alloc(const agj_index* index, uint64_t n, void* stream, agj_pairs* out);
+int agj_pairs_free(agj_pairs* pairs, void* stream);
+
+/*
+ * The probe (§III-E, Listing "The probe algorithm"): for each point, its
+ * 64-bit cell id, the trie walk from its face root (Listing "Probe Adaptive
+ * Cell Trie"), the references of the cell found; approx mode outputs every
+ * reference, exact mode outputs true hits and the candidates that pass the
+ * FP64 ST_Covers test.  d_points: device, n x {lat, lng}, 16-byte aligned,
+ * borrowed.  `out` buffers must satisfy agj_join_requirements(index, n).
+ * Asynchronous on `stream`; out->status[0] holds nnz when the stream
+ * reaches that point.  n == 0 writes offsets[0] = 0.  n must be < 2^32.
+ * Errors (returned immediately): AGJ_EINVAL, AGJ_ECAPACITY (buffers too
+ * small for n), AGJ_ECUDA (launch failed).  Device-side conditions are
+ * reported in out->status[1] (bit 0 ids capacity exceeded, bit 1 scan wait
+ * timed out, bit 2 trie bounds check, bit 3 candidate queue overflow) and
+ * by agj_join_check.
+ */
+int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out);
+
+/* Synchronises `stream`, reads out->status and returns AGJ_OK, or the first
+ * device-side error as a status code; *nnz receives the pair count. */
+int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz);
+
+/*
+ * End-to-end join from host memory: copies h_points (n x {lat, lng}) to the
+ * device, joins, and copies the CSR back (h_offsets: n + 1, h_ids: up to
+ * h_ids_capacity).  Uses `work` (from agj_pairs_alloc or caller buffers for
+ * n points) plus d_points_staging (device, n x 16 bytes).  Synchronises
+ * `stream`.  *nnz receives the pair count; AGJ_ECAPACITY if h_ids is too
+ * small (h_offsets is still filled).
+ */
+int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, double* d_points_staging,
+                  agj_pairs* work, uint32_t* h_offsets, uint32_t* h_ids, uint64_t h_ids_capacity,
+                  uint64_t* nnz, void* stream);
+
+/* Cell ids of points with the device kernel (FP64 spec, bit-exact); for
+ * checking the id step alone.  d_ids: device, n uint64. */
+int agj_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, void* stream);
+
+/* Cell ids of points on the host with the same spec (host code). */
+int agj_cell_ids_host(const double* h_points, uint64_t n, uint64_t* h_ids);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AGJ_H */

@@ -1,0 +1,14 @@
+"""GB300-native adaptive geospatial join, probe side.
+
+Kipf et al., "Adaptive Geospatial Joins for Modern Hardware": points are
+mapped to 64-bit quadtree/Hilbert cell ids, looked up in an Adaptive Cell
+Trie over polygon coverings (true-hit and candidate references), and only
+candidate references get an exact point-in-polygon test.  The native library
+(include/agj.h) does all of it; this package is its thin binding plus the
+seeded synthetic workloads.
+"""
+from .native import (APPROX, EXACT, AgjError, Index, Pairs, cell_ids, cell_ids_host, join, join_host, lib,
+                     supercover)
+
+__all__ = ["APPROX", "EXACT", "AgjError", "Index", "Pairs", "join", "join_host", "cell_ids", "cell_ids_host", "lib",
+           "supercover"]

@@ -1,0 +1,250 @@
+// agj_capi.cpp — the extern "C" boundary declared in include/agj.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "../../include/agj.h"
+#include "agj_geom.cuh"
+#include "agj_index.h"
+#include "agj_launch.h"
+
+struct agj_index {
+    agj::Index X;
+};
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+thread_local std::string g_last_error;
+
+}  // namespace
+
+extern "C" {
+
+const char* agj_strerror(int status) {
+    switch (status) {
+        case AGJ_OK: return "ok";
+        case AGJ_EINVAL: return "invalid argument";
+        case AGJ_EUNSUPPORTED: return "unsupported input";
+        case AGJ_EBUDGET: return "memory budget exceeded";
+        case AGJ_ENOMEM: return "out of memory";
+        case AGJ_ECUDA: return "CUDA error";
+        case AGJ_ETIMEOUT: return "device wait timed out";
+        case AGJ_EBUSY: return "busy";
+        case AGJ_ECAPACITY: return "buffer too small";
+        case AGJ_EDEVICE: return "device-side check failed";
+        default: return "unknown status";
+    }
+}
+
+// Last build error message of the calling thread (diagnostics only).
+const char* agj_last_error(void) { return g_last_error.c_str(); }
+
+int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, agj_mode mode,
+              const agj_build_opts* opts, void* stream, agj_index** out) {
+    if (!out) return AGJ_EINVAL;
+    *out = nullptr;
+    if (mode != AGJ_APPROX && mode != AGJ_EXACT) return AGJ_EINVAL;
+    agj_build_opts o;
+    memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    agj::BuildParams bp;
+    bp.mode = mode;
+    bp.precision_m = precision_m;
+    bp.max_cover_cells = o.max_cover_cells ? o.max_cover_cells : 128;
+    bp.max_cover_level = o.max_cover_level ? std::min<uint32_t>(o.max_cover_level, 30) : 30;
+    bp.max_interior_cells = o.max_interior_cells ? o.max_interior_cells : 256;
+    bp.max_interior_level = o.max_interior_level ? std::min<uint32_t>(o.max_interior_level, 30) : 20;
+    bp.budget = o.memory_budget_bytes;
+    bp.train = o.train_latlng;
+    bp.n_train = o.train_latlng ? o.n_train : 0;
+    bp.max_train_level = o.max_train_level ? std::min<uint32_t>(o.max_train_level, 30) : 24;
+    bp.threads = o.n_threads;
+    agj_index* h = new (std::nothrow) agj_index();
+    if (!h) return AGJ_ENOMEM;
+    int rc;
+    try {
+        rc = agj::build_host(polys, n_polys, bp, &h->X, &g_last_error);
+    } catch (const std::bad_alloc&) {
+        rc = AGJ_ENOMEM;
+    }
+    if (rc == AGJ_OK && !o.host_only) rc = agj::upload_index(&h->X, as_stream(stream));
+    if (rc != AGJ_OK) {
+        agj_free(h);
+        return rc;
+    }
+    *out = h;
+    return AGJ_OK;
+}
+
+void agj_free(agj_index* index) {
+    if (!index) return;
+    if (index->X.d_blob) {
+        cudaDeviceSynchronize();
+        cudaFree(index->X.d_blob);
+    }
+    delete index;
+}
+
+int agj_index_stats(const agj_index* index, agj_stats* out) {
+    if (!index || !out) return AGJ_EINVAL;
+    *out = index->X.stats;
+    return AGJ_OK;
+}
+
+int agj_index_logical(const agj_index* index, uint64_t* cells, uint64_t* ref_off, uint32_t* refs, uint64_t* n_cells,
+                      uint64_t* n_refs) {
+    if (!index) return AGJ_EINVAL;
+    const agj::Index& X = index->X;
+    if (n_cells) *n_cells = X.cells.size();
+    if (n_refs) *n_refs = X.refs.size();
+    if (cells) std::copy(X.cells.begin(), X.cells.end(), cells);
+    if (ref_off) std::copy(X.ref_off.begin(), X.ref_off.end(), ref_off);
+    if (refs) std::copy(X.refs.begin(), X.refs.end(), refs);
+    return AGJ_OK;
+}
+
+int agj_supercover(const uint64_t* cells, const uint32_t* refs, uint64_t n, uint64_t* out_cells, uint64_t* out_off,
+                   uint32_t* out_refs, uint64_t* n_out_cells, uint64_t* n_out_refs) {
+    if (n && (!cells || !refs)) return AGJ_EINVAL;
+    for (uint64_t k = 0; k < n; ++k) {
+        // a cell id: face <= 5 and its lowest set (marker) bit at an even position
+        if (cells[k] == 0 || (cells[k] >> 61) > 5 || (__builtin_ctzll(cells[k]) & 1)) return AGJ_EINVAL;
+    }
+    std::vector<uint64_t> oc, oo;
+    std::vector<uint32_t> orf;
+    agj::supercover(cells, refs, n, &oc, &oo, &orf);
+    if (n_out_cells) *n_out_cells = oc.size();
+    if (n_out_refs) *n_out_refs = orf.size();
+    if (out_cells) std::copy(oc.begin(), oc.end(), out_cells);
+    if (out_off) std::copy(oo.begin(), oo.end(), out_off);
+    if (out_refs) std::copy(orf.begin(), orf.end(), out_refs);
+    return AGJ_OK;
+}
+
+int agj_lut_encode(const uint32_t* refs, const uint64_t* ref_off, uint64_t n_lists, uint32_t* words,
+                   uint64_t* offsets, uint64_t* n_words) {
+    if (n_lists && (!refs || !ref_off)) return AGJ_EINVAL;
+    std::vector<uint32_t> w;
+    std::vector<uint64_t> o;
+    agj::lut_encode(refs, ref_off, n_lists, &w, &o);
+    if (n_words) *n_words = w.size();
+    if (words) std::copy(w.begin(), w.end(), words);
+    if (offsets) std::copy(o.begin(), o.end(), offsets);
+    return AGJ_OK;
+}
+
+int agj_index_trie(const agj_index* index, uint64_t* nodes, uint32_t* lut, uint64_t face_table[18]) {
+    if (!index) return AGJ_EINVAL;
+    const agj::Index& X = index->X;
+    if (nodes) std::copy(X.nodes.begin(), X.nodes.end(), nodes);
+    if (lut) std::copy(X.lut.begin(), X.lut.end(), lut);
+    if (face_table)
+        for (int f = 0; f < 6; ++f) {
+            face_table[3 * f] = X.faces[f].root;
+            face_table[3 * f + 1] = X.faces[f].prefix_bits;
+            face_table[3 * f + 2] = X.faces[f].prefix;
+        }
+    return AGJ_OK;
+}
+
+int agj_join_requirements(const agj_index* index, uint64_t n, agj_requirements* out) {
+    if (!index || !out) return AGJ_EINVAL;
+    return agj::join_requirements(index->X, n, out);
+}
+
+int agj_pairs_alloc(const agj_index* index, uint64_t n, void* stream, agj_pairs* out) {
+    if (!index || !out) return AGJ_EINVAL;
+    agj_requirements r;
+    agj::join_requirements(index->X, n, &r);
+    memset(out, 0, sizeof *out);
+    cudaStream_t s = as_stream(stream);
+    void *off = nullptr, *ids = nullptr, *scr = nullptr, *st = nullptr;
+    if (cudaMallocAsync(&off, (n + 1) * 4, s) != cudaSuccess ||
+        cudaMallocAsync(&ids, std::max<uint64_t>(r.ids_capacity, 1) * 4, s) != cudaSuccess ||
+        cudaMallocAsync(&scr, r.scratch_bytes, s) != cudaSuccess || cudaMallocAsync(&st, 64, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (off) cudaFreeAsync(off, s);
+        if (ids) cudaFreeAsync(ids, s);
+        if (scr) cudaFreeAsync(scr, s);
+        if (st) cudaFreeAsync(st, s);
+        return AGJ_ENOMEM;
+    }
+    out->offsets = static_cast<uint32_t*>(off);
+    out->ids = static_cast<uint32_t*>(ids);
+    out->ids_capacity = r.ids_capacity;
+    out->scratch = scr;
+    out->scratch_bytes = r.scratch_bytes;
+    out->status = static_cast<uint64_t*>(st);
+    return AGJ_OK;
+}
+
+int agj_pairs_free(agj_pairs* pairs, void* stream) {
+    if (!pairs) return AGJ_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    if (pairs->offsets) cudaFreeAsync(pairs->offsets, s);
+    if (pairs->ids) cudaFreeAsync(pairs->ids, s);
+    if (pairs->scratch) cudaFreeAsync(pairs->scratch, s);
+    if (pairs->status) cudaFreeAsync(pairs->status, s);
+    memset(pairs, 0, sizeof *pairs);
+    return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+}
+
+int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out) {
+    if (!index || !index->X.d_blob) return AGJ_EINVAL;
+    return agj::launch_join(index->X, d_points, n, as_stream(stream), out);
+}
+
+int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz) {
+    if (!pairs || !pairs->status) return AGJ_EINVAL;
+    uint64_t st[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(st, pairs->status, sizeof st, cudaMemcpyDeviceToHost, as_stream(stream)) != cudaSuccess)
+        return AGJ_ECUDA;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return AGJ_ECUDA;
+    if (nnz) *nnz = st[0];
+    if (st[1] & 1ull) return AGJ_ECAPACITY;
+    if (st[1] & 2ull) return AGJ_ETIMEOUT;
+    if (st[1] & 4ull) return AGJ_EDEVICE;
+    if (st[1] & 8ull) return AGJ_ECAPACITY;
+    return AGJ_OK;
+}
+
+int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, double* d_points_staging,
+                  agj_pairs* work, uint32_t* h_offsets, uint32_t* h_ids, uint64_t h_ids_capacity, uint64_t* nnz,
+                  void* stream) {
+    if (!index || !index->X.d_blob || !work || !h_offsets || (n && (!h_points || !d_points_staging)))
+        return AGJ_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    if (n && cudaMemcpyAsync(d_points_staging, h_points, n * 16, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return AGJ_ECUDA;
+    int rc = agj::launch_join(index->X, d_points_staging, n, s, work);
+    if (rc != AGJ_OK) return rc;
+    if (cudaMemcpyAsync(h_offsets, work->offsets, (n + 1) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return AGJ_ECUDA;
+    uint64_t total = 0;
+    rc = agj_join_check(work, stream, &total);
+    if (nnz) *nnz = total;
+    if (rc != AGJ_OK) return rc;
+    if (total > h_ids_capacity) return AGJ_ECAPACITY;
+    if (total && cudaMemcpyAsync(h_ids, work->ids, total * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return AGJ_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+}
+
+int agj_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, void* stream) {
+    if (n && (!d_points || !d_ids)) return AGJ_EINVAL;
+    return agj::launch_cell_ids(d_points, n, d_ids, as_stream(stream));
+}
+
+int agj_cell_ids_host(const double* h_points, uint64_t n, uint64_t* h_ids) {
+    if (n && (!h_points || !h_ids)) return AGJ_EINVAL;
+    for (uint64_t k = 0; k < n; ++k) h_ids[k] = agj::point_cell_id(h_points[2 * k], h_points[2 * k + 1]);
+    return AGJ_OK;
+}
+
+}  // extern "C"

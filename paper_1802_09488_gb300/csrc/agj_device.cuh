@@ -1,0 +1,88 @@
+// agj_device.cuh — device-side view of an index and the per-point probe
+// steps (cell id, face/prefix stage, trie walk, entry decode).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "agj_geom.cuh"
+
+namespace agj {
+
+struct DevFace {
+    uint32_t root;          // node index, 0xFFFFFFFF = no cells on this face
+    uint32_t prefix_bits;   // key bits after the face bits (multiple of 8)
+    uint64_t prefix;        // right-aligned
+};
+
+// Everything a kernel needs from one index; passed by value.
+struct DevIndex {
+    const uint64_t* nodes;      // n_nodes x 256 tagged entries
+    const uint32_t* lut;        // lookup table
+    const double2* poly_uv;     // polygon vertices in face (u,v)
+    const int64_t* poly_vkey;   // order-preserving integer keys of the vertices' v
+    const int64_t* poly_ukey;   // ... and of u
+    const uint32_t* poly_off;   // n_polys + 1
+    const int64_t* poly_bbox;   // 4 keys per polygon: umin umax vmin vmax
+    const int8_t* poly_face;
+    uint64_t n_nodes;
+    uint64_t n_lut;
+    uint32_t n_polys;
+    uint32_t max_depth;
+    DevFace faces[6];
+};
+
+constexpr uint32_t kNoRootDev = 0xFFFFFFFFu;
+constexpr uint32_t kInvalidPayloadDev = 0x7FFFFFFFu;
+
+// Error flag bits in status[1].
+constexpr uint64_t kErrIdsCapacity = 1ull << 0;
+constexpr uint64_t kErrScanTimeout = 1ull << 1;
+constexpr uint64_t kErrTrieBounds = 1ull << 2;
+constexpr uint64_t kErrQueueOverflow = 1ull << 3;
+
+// Order-preserving map of a double onto int64 (sign-magnitude to two's
+// complement); -0.0 and +0.0 map to the same key, so comparisons of keys
+// equal IEEE comparisons for non-NaN values.
+AGJ_HD int64_t dkey(double x) {
+#ifdef __CUDA_ARCH__
+    const int64_t b = __double_as_longlong(x);
+#else
+    int64_t b;
+    memcpy(&b, &x, 8);
+#endif
+    return b < 0 ? -(b & 0x7FFFFFFFFFFFFFFFll) : b;
+}
+
+// Number of references (true + candidate) an entry holds.
+__device__ __forceinline__ void entry_counts(const DevIndex& X, uint64_t e, uint32_t* n_true, uint32_t* n_cand) {
+    const uint32_t tag = (uint32_t)(e & 3ull);
+    *n_true = 0;
+    *n_cand = 0;
+    if (tag == 1) {
+        const uint32_t p = (uint32_t)(e >> 2) & 0x7FFFFFFFu;
+        if (p == kInvalidPayloadDev) return;
+        if (p & 1u) *n_true = 1; else *n_cand = 1;
+    } else if (tag == 2) {
+        const uint32_t p1 = (uint32_t)(e >> 2) & 0x7FFFFFFFu, p2 = (uint32_t)(e >> 33) & 0x7FFFFFFFu;
+        *n_true = (p1 & 1u) + (p2 & 1u);
+        *n_cand = 2 - *n_true;
+    } else if (tag == 3) {
+        const uint32_t off = (uint32_t)(e >> 2) & 0x7FFFFFFFu;
+        const uint32_t nt = __ldg(X.lut + off);
+        *n_true = nt;
+        *n_cand = __ldg(X.lut + off + 1 + nt);
+    }
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+}  // namespace agj

@@ -1,0 +1,92 @@
+// agj_index.h — host-side index representation shared by the builder (C++)
+// and the CUDA front end.  No CUDA types here so that the builder compiles
+// with a plain C++ compiler.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/agj.h"
+
+namespace agj {
+
+// Tagged 8-byte trie entry (§III-C "Adaptive Cell Trie"):
+//   low 2 bits = tag
+//   tag 0: child pointer, stored as node_index << 11 (the byte offset of the
+//          child's 256 x 8-byte node); the value 0 is the sentinel (false hit)
+//   tag 1: one inline payload in bits 2..32
+//   tag 2: two inline payloads in bits 2..32 and 33..63
+//   tag 3: word offset into the lookup table in bits 2..32
+// A payload is polygon_id << 1 | interior (31 bits); 0x7FFFFFFF is the
+// invalid payload (false hit).
+constexpr uint64_t kTagMask = 3;
+constexpr uint64_t kTagPtr = 0, kTagOne = 1, kTagTwo = 2, kTagLut = 3;
+constexpr uint32_t kPayloadMask = 0x7FFFFFFFu;
+constexpr uint32_t kInvalidPayload = 0x7FFFFFFFu;
+constexpr uint32_t kNodeEntries = 256;
+constexpr int kNodeShift = 11;               // log2(256 * 8)
+constexpr uint32_t kNoRoot = 0xFFFFFFFFu;
+constexpr uint32_t kMaxPolys = (1u << 30) - 1;
+
+// Face table entry (§IV-B stage 1: roots, common prefixes, prefix lengths).
+// prefix_bits counts key bits after the 3 face bits (a multiple of 8); the
+// prefix is right-aligned.
+struct FaceRoot {
+    uint32_t root;
+    uint32_t prefix_bits;
+    uint64_t prefix;
+};
+
+struct Index {
+    agj_mode mode = AGJ_APPROX;
+    uint32_t n_polys = 0;
+    double precision_m = 0;
+    // logical index (super covering)
+    std::vector<uint64_t> cells;
+    std::vector<uint64_t> ref_off;
+    std::vector<uint32_t> refs;
+    // physical index
+    std::vector<uint64_t> nodes;
+    std::vector<uint32_t> lut;
+    FaceRoot faces[6];
+    // polygons in face (u,v)
+    std::vector<double> poly_uv;      // 2 per vertex
+    std::vector<uint32_t> poly_off;   // n_polys + 1
+    std::vector<double> poly_bbox;    // 4 per polygon: umin umax vmin vmax
+    std::vector<int8_t> poly_face;
+    agj_stats stats{};
+    // device copies (owned)
+    void* d_blob = nullptr;
+    uint64_t blob_bytes = 0;
+    uint64_t off_nodes = 0, off_lut = 0, off_uv = 0, off_vkey = 0, off_ukey = 0, off_poff = 0, off_bbox = 0,
+             off_face = 0;
+    int device = 0;
+};
+
+struct BuildParams {
+    agj_mode mode;
+    double precision_m;
+    uint32_t max_cover_cells, max_cover_level, max_interior_cells, max_interior_level;
+    uint64_t budget;
+    const double* train;
+    uint64_t n_train;
+    uint32_t max_train_level;
+    uint32_t threads;
+};
+
+// Host build of the logical and physical index (no CUDA calls).  Returns an
+// AGJ_* status; on failure *err_msg says why.
+int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp, Index* out,
+               std::string* err_msg);
+
+// The super-covering merge on given (cell, reference) pairs, in order.
+void supercover(const uint64_t* cells, const uint32_t* refs, uint64_t n, std::vector<uint64_t>* out_cells,
+                std::vector<uint64_t>* out_off, std::vector<uint32_t>* out_refs);
+
+// Lookup-table encoding of reference lists (deduplicated).
+void lut_encode(const uint32_t* refs, const uint64_t* ref_off, uint64_t n_lists, std::vector<uint32_t>* words,
+                std::vector<uint64_t>* offsets);
+
+}  // namespace agj

@@ -1,0 +1,16 @@
+// agj_launch.h — host entry points of the CUDA translation unit(s).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "agj_index.h"
+
+namespace agj {
+
+// Copies the flattened index and the polygons to one device allocation.
+int upload_index(Index* X, cudaStream_t s);
+int join_requirements(const Index& X, uint64_t n, agj_requirements* r);
+int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, agj_pairs* out);
+int launch_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, cudaStream_t s);
+
+}  // namespace agj

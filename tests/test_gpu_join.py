@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+* cell ids: bit-exact (integer output of FP64 arithmetic done the same way);
+* approx join: bit-exact CSR against the oracle's sorted-vector probe of the
+  index's logical covering (§II, §III-B), which itself is checked against the
+  exact join and the eps bound on the CPU (test_host_index.py);
+* exact join: bit-exact CSR against brute-force ST_Covers over all polygons
+  (§III-A: filter and refine yields the plain join).
+Sizes span many tiles of 1024 points and a ragged tail; the full-size city
+workload (1e8 points) is checked on sampled rows plus size-independent
+properties.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def agj(torch):
+    import paper_1802_09488_gb300 as m
+    m.lib()
+    return m
+
+
+def _dev(torch, pts):
+    return torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float64)).cuda()
+
+
+def _csr_equal(a_off, a_ids, b_off, b_ids, rows=None):
+    a_off = np.asarray(a_off, dtype=np.int64)
+    b_off = np.asarray(b_off, dtype=np.int64)
+    if rows is None:
+        assert np.array_equal(a_off, b_off)
+        assert np.array_equal(np.asarray(a_ids, dtype=np.int64), np.asarray(b_ids, dtype=np.int64))
+        return
+    for r in rows:
+        assert list(a_ids[a_off[r]:a_off[r + 1]]) == list(b_ids[b_off[r]:b_off[r + 1]]), r
+
+
+def test_cell_ids_bit_exact(torch, agj, oracle):
+    rng = np.random.default_rng(31)
+    n = 1_000_003
+    lat = np.degrees(np.arcsin(rng.uniform(-1, 1, n)))
+    lng = rng.uniform(-180, 180, n)
+    pts = np.stack([lat, lng], -1)
+    pts[:8] = [[np.nan, 0], [91, 0], [0, 181], [90, 180], [-90, -180], [0, 0], [45, 45], [35.26438968, 45]]
+    got = agj.cell_ids(_dev(torch, pts)).cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, oracle.cell_ids(pts))
+    from paper_1802_09488_gb300 import synth
+    w = synth.points_mixture(500_000, synth.BOX_CITY, 3)
+    assert np.array_equal(agj.cell_ids(_dev(torch, w)).cpu().numpy().view(np.uint64), oracle.cell_ids(w))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    from paper_1802_09488_gb300 import synth
+    return synth.c1_tiny(100_000)
+
+
+def test_c1_approx_bit_exact(torch, agj, oracle, c1):
+    ix = agj.Index(c1.polygons, agj.APPROX, c1.eps_m)
+    pr = agj.join(ix, _dev(torch, c1.points))
+    off, ids = pr.to_host()
+    cells, ro, refs = ix.logical()
+    eo, ei = oracle.join_approx_logical(cells, ro, refs, c1.points)
+    _csr_equal(off, ids, eo, ei)
+    st = pr.status.cpu().numpy()
+    assert st[0] == len(ids) and st[1] == 0
+
+
+def test_c1_exact_bit_exact(torch, agj, oracle, c1):
+    ix = agj.Index(c1.polygons, agj.EXACT, 0, train=c1.points[:1000])
+    pr = agj.join(ix, _dev(torch, c1.points))
+    off, ids = pr.to_host()
+    eo, ei = oracle.PolySet(c1.polygons).join_exact(c1.points)
+    _csr_equal(off, ids, eo, ei)
+    assert pr.status.cpu().numpy()[2] > 0          # candidates were refined
+
+
+def test_c1_exact_untrained_and_boundary_points(torch, agj, oracle, c1):
+    """Points exactly on polygon vertices and edge midpoints (ST_Covers counts
+    them inside, §II), plus invalid and far-away points."""
+    ix = agj.Index(c1.polygons, agj.EXACT, 0)
+    verts = np.concatenate(c1.polygons)
+    mids = np.concatenate([0.5 * (p + np.roll(p, -1, axis=0)) for p in c1.polygons])
+    extra = np.array([[np.nan, -73.9], [40.7, np.inf], [95.0, 0.0], [10.0, 20.0], [-40.7, 106.05], [40.7, -73.95]])
+    pts = np.concatenate([verts, mids, extra, c1.points[:5000]])
+    pr = agj.join(ix, _dev(torch, pts))
+    off, ids = pr.to_host()
+    eo, ei = oracle.PolySet(c1.polygons).join_exact(pts)
+    _csr_equal(off, ids, eo, ei)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 1023, 1024, 1025, 4097, 65537])
+def test_ragged_sizes(torch, agj, oracle, c1, n):
+    for mode in (agj.APPROX, agj.EXACT):
+        ix = agj.Index(c1.polygons, mode, c1.eps_m)
+        pts = c1.points[:n]
+        pr = agj.join(ix, _dev(torch, pts.reshape(-1, 2)))
+        off, ids = pr.to_host()
+        assert len(off) == n + 1 and off[0] == 0 and off[-1] == len(ids)
+        if mode == agj.APPROX:
+            cells, ro, refs = ix.logical()
+            eo, ei = oracle.join_approx_logical(cells, ro, refs, pts.reshape(-1, 2))
+        else:
+            eo, ei = oracle.PolySet(c1.polygons).join_exact(pts.reshape(-1, 2))
+        _csr_equal(off, ids, eo, ei)
+
+
+def test_pairs_reuse_and_capacity_errors(torch, agj, c1):
+    ix = agj.Index(c1.polygons, agj.APPROX, c1.eps_m)
+    pr = agj.Pairs(ix, 10_000)
+    a = agj.join(ix, _dev(torch, c1.points[:10_000]), pr)
+    o1, i1 = a.to_host()
+    b = agj.join(ix, _dev(torch, c1.points[:10_000]), pr)   # same buffers, reset per call
+    o2, i2 = b.to_host()
+    assert np.array_equal(o1, o2) and np.array_equal(i1, i2)
+    pr.c.scratch_bytes = 16                                  # too small: refused before any launch
+    with pytest.raises(agj.AgjError) as e:
+        agj.join(ix, _dev(torch, c1.points[:10_000]), pr)
+    assert e.value.status == 8
+
+
+@pytest.fixture(scope="module")
+def city_small():
+    from paper_1802_09488_gb300 import synth
+    return synth.c2_city(2_000_000, n_train=200_000)
+
+
+def test_city_approx_and_exact_2m(torch, agj, oracle, city_small):
+    w = city_small
+    pts = _dev(torch, w.points)
+    ia = agj.Index(w.polygons, agj.APPROX, w.eps_m)
+    off, ids = agj.join(ia, pts).to_host()
+    cells, ro, refs = ia.logical()
+    eo, ei = oracle.join_approx_logical(cells, ro, refs, w.points)
+    _csr_equal(off, ids, eo, ei)
+    ie = agj.Index(w.polygons, agj.EXACT, 0, train=w.train)
+    off, ids = agj.join(ie, pts).to_host()
+    xo, xi = oracle.PolySet(w.polygons).join_exact(w.points)
+    _csr_equal(off, ids, xo, xi)
+
+
+def test_city_full_size_sampled(torch, agj, oracle):
+    """The 1e8-point city workload in the launch configuration the benchmark
+    times: sampled rows against the oracle, and CSR properties on all rows."""
+    from paper_1802_09488_gb300 import synth
+    w = synth.c2_city(100_000_000, n_train=1_000_000)
+    pts = _dev(torch, w.points)
+    rng = np.random.default_rng(77)
+    rows = np.sort(rng.choice(len(w.points), 20000, replace=False))
+    ps = oracle.PolySet(w.polygons)
+    for mode in (agj.APPROX, agj.EXACT):
+        ix = agj.Index(w.polygons, mode, w.eps_m, train=w.train if mode == agj.EXACT else None)
+        pr = agj.join(ix, pts)
+        nnz = pr.check()
+        off = pr.offsets.cpu().numpy().view(np.uint32).astype(np.int64)
+        assert off[0] == 0 and off[-1] == nnz and np.all(np.diff(off) >= 0)
+        sub = w.points[rows]
+        if mode == agj.APPROX:
+            cells, ro, refs = ix.logical()
+            eo, ei = oracle.join_approx_logical(cells, ro, refs, sub)
+        else:
+            eo, ei = ps.join_exact(sub)
+        ids = pr.ids[:nnz].cpu().numpy().view(np.uint32)
+        for k, r in enumerate(rows):
+            assert ids[off[r]:off[r + 1]].tolist() == ei[eo[k]:eo[k + 1]].tolist(), (mode, r)
+        del pr, ix
+        torch.cuda.empty_cache()
