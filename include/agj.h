@@ -225,6 +225,36 @@ int agj_pairs_free(agj_pairs* pairs, void* stream);
  */
 int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out);
 
+/*
+ * Approximate join that allocates nothing.  The paper has no counterpart;
+ * this entry point exists for callers that cannot call cudaMalloc (or any
+ * allocating routine) when they join: code running under a device-memory
+ * budget that was split up front, plugins hosted by another framework that
+ * owns every device allocation, and latency-bound loops where an allocation
+ * could synchronise the device and stall other streams.
+ *
+ * It computes exactly what agj_join computes for an AGJ_APPROX index, with
+ * the same kernel; its scan work space is a static device array of the
+ * library, sized for at most AGJ_NOALLOC_MAX_POINTS points per call, held
+ * by every device that loads the library until the process exits.
+ * The caller passes the inputs and outputs: d_points (device, n x {lat, lng},
+ * 16-byte aligned), d_offsets (device, n + 1 uint32), d_ids (device,
+ * ids_capacity uint32, at least n * max_refs of agj_index_stats) and
+ * d_status (device, 4 uint64 words, same meaning as agj_pairs.status).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.
+ * All calls on one device share the array: calls whose kernels overlap on
+ * the GPU (different streams, no ordering between them) race and give wrong
+ * results; order them on one stream or with events.
+ * Errors: AGJ_EINVAL (null or misaligned pointer, exact-mode index, index
+ * built with host_only), AGJ_ECAPACITY (n > AGJ_NOALLOC_MAX_POINTS, or
+ * ids_capacity too small), AGJ_ECUDA.  Device-side conditions land in
+ * d_status[1] as for agj_join.  Asynchronous on `stream`.
+ */
+#define AGJ_NOALLOC_MAX_POINTS (1ull << 24)
+int agj_join_approx_noalloc(const agj_index* index, const double* d_points, uint64_t n, uint32_t* d_offsets,
+                            uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, void* stream);
+
 /* Synchronises `stream`, reads out->status and returns AGJ_OK, or the first
  * device-side error as a status code; *nnz receives the pair count. */
 int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz);

@@ -200,6 +200,13 @@ int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* s
     return agj::launch_join(index->X, d_points, n, as_stream(stream), out);
 }
 
+int agj_join_approx_noalloc(const agj_index* index, const double* d_points, uint64_t n, uint32_t* d_offsets,
+                            uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, void* stream) {
+    if (!index) return AGJ_EINVAL;
+    return agj::launch_join_approx_noalloc(index->X, d_points, n, d_offsets, d_ids, ids_capacity, d_status,
+                                           as_stream(stream));
+}
+
 int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz) {
     if (!pairs || !pairs->status) return AGJ_EINVAL;
     uint64_t st[4] = {0, 0, 0, 0};

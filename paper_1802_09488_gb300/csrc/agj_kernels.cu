@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "agj_device.cuh"
@@ -772,6 +773,77 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
                                                                      L.queue_cap, out->offsets, out->ids, out->ids_capacity, tiles,
                                                                      hdr, out->status);
     }
+    return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// approximate join without any allocation
+// ---------------------------------------------------------------------------
+// The one-pass approximate join needs work space for its tile scan: a
+// 256-byte header (the tile counter) and one 8-byte state per tile of
+// kTile points.  For callers that must not allocate, that work space is this
+// file-scope device array, sized for joins of up to kNoAllocMaxPoints points
+// (16384 tiles, 128 KiB + 256 B).  Every device that loads the library holds
+// one copy until the process exits.  All calls on a device share it, so
+// calls whose kernels overlap on the GPU race; the header and the tile
+// states a call uses are cleared at the start of every call.
+constexpr uint64_t kNoAllocMaxPoints = 1ull << 24;
+constexpr uint64_t kNoAllocHeaderWords = 32;
+constexpr uint64_t kNoAllocTiles = kNoAllocMaxPoints / kTile;
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocHeaderWords + kNoAllocTiles];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint64_t* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  The host-side
+// name of the array is only a stand-in, so the address is looked up once per
+// device with that device current and cached.
+int noalloc_scratch(uint64_t** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return AGJ_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) { cudaGetLastError(); return AGJ_ECUDA; }
+        g_noalloc_ptr[dev] = static_cast<uint64_t*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return AGJ_OK;
+}
+
+}  // namespace
+
+int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t n, uint32_t* d_offsets,
+                               uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, cudaStream_t s) {
+    if (X.mode != AGJ_APPROX || !X.d_blob) return AGJ_EINVAL;
+    if (!d_offsets || !d_status || (n && !d_points)) return AGJ_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return AGJ_EINVAL;
+    if (n > kNoAllocMaxPoints) return AGJ_ECAPACITY;
+    const uint64_t need = n * std::max<uint64_t>(X.stats.max_refs, 1);
+    if (ids_capacity < need) return AGJ_ECAPACITY;
+    if (need && !d_ids) return AGJ_EINVAL;
+    uint64_t* sc = nullptr;
+    const int rc = noalloc_scratch(&sc);
+    if (rc != AGJ_OK) return rc;
+    const uint64_t n_tiles = (n + kTile - 1) / kTile;
+    const uint64_t zero_words = kNoAllocHeaderWords + n_tiles;
+    {
+        const int grid = (int)std::min<uint64_t>((zero_words + 255) / 256 + 1, (uint64_t)sm_count() * 4);
+        k_zero<<<grid, 256, 0, s>>>(sc, zero_words, d_status, 4);
+    }
+    if (n == 0) {
+        cudaMemsetAsync(d_offsets, 0, 4, s);
+        return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+    }
+    const DevIndex D = make_dev_index(X);
+    k_join_approx<kJoinBlock, kJoinPPT><<<(unsigned)n_tiles, kJoinBlock, 0, s>>>(
+        D, reinterpret_cast<const double2*>(d_points), (uint32_t)n, d_offsets, d_ids, ids_capacity,
+        sc + kNoAllocHeaderWords, reinterpret_cast<uint32_t*>(sc), d_status);
     return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
 

@@ -11,6 +11,10 @@ namespace agj {
 int upload_index(Index* X, cudaStream_t s);
 int join_requirements(const Index& X, uint64_t n, agj_requirements* r);
 int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, agj_pairs* out);
+// Approximate join whose work space is a file-scope device array (no
+// allocation); at most 2^24 points per call.
+int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t n, uint32_t* d_offsets,
+                               uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, cudaStream_t s);
 int launch_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, cudaStream_t s);
 
 }  // namespace agj
