@@ -231,6 +231,7 @@ def main():
     st_e = pe.status.cpu().numpy().view(np.uint64)
     gathers_per_pt = float(st_a[3]) / n
     cands_per_pt = float(st_e[2]) / n
+    fallback_a, fallback_e = pa.fallbacks(), pe.fallbacks()
 
     barrier()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -282,9 +283,11 @@ def main():
                    "l2": "inputs (16 B x 1e8 = 1.6 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
         "modes": {
             "approx": {"points_per_s": n / (statistics.mean(approx_ms) / 1000.0), "p50_ms": pct(approx_ms, 50),
-                       "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_per_pt},
+                       "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_per_pt,
+                       "fp64_id_fallbacks": fallback_a},
             "exact": {"points_per_s": n / (statistics.mean(exact_ms) / 1000.0), "p50_ms": pct(exact_ms, 50),
-                      "p99_ms": pct(exact_ms, 99), "nnz": nnz_e, "candidates_per_point": cands_per_pt},
+                      "p99_ms": pct(exact_ms, 99), "nnz": nnz_e, "candidates_per_point": cands_per_pt,
+                      "fp64_id_fallbacks": fallback_e},
         },
         "index": {"approx": ia.stats(), "exact": ie.stats(), "build_s": build_s},
         "roofline": roofline,

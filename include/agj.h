@@ -91,6 +91,8 @@ typedef struct {
     uint32_t n_threads;           /* host build threads, 0 -> all cores */
     uint32_t host_only;           /* 1: build the host index only, no device copy
                                      (for inspection; agj_join then returns AGJ_EINVAL) */
+    uint32_t no_fast_ids;         /* 1: always compute cell ids in FP64 (no certified
+                                     FP32 model); results are identical, only slower */
 } agj_build_opts;
 
 typedef struct agj_index agj_index;
@@ -128,6 +130,9 @@ typedef struct {
     uint32_t max_depth;        /* deepest trie level below the face roots */
     uint32_t max_level;        /* finest cell level */
     double   build_seconds;
+    uint32_t fast_ids;         /* 1: certified FP32 cell-id model in use */
+    uint32_t reserved;
+    double   fast_err_cells;   /* its error bound, in level-30 cells */
 } agj_stats;
 
 int agj_index_stats(const agj_index* index, agj_stats* out);
@@ -188,7 +193,9 @@ typedef struct {
     uint32_t* offsets;        /* n + 1 */
     uint32_t* ids;            /* ids_capacity */
     uint64_t  ids_capacity;
-    void*     scratch;        /* scratch_bytes, 256-byte aligned */
+    void*     scratch;        /* scratch_bytes, 256-byte aligned; after a join its
+                                 bytes 16..23 hold the number of points whose
+                                 walk recomputed the FP64 cell id (diagnostic) */
     uint64_t  scratch_bytes;
     uint64_t* status;         /* 4 x uint64 device words: [0] nnz, [1] error flags,
                                  [2] candidate pairs refined (exact mode),
@@ -274,6 +281,18 @@ int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, do
 /* Cell ids of points with the device kernel (FP64 spec, bit-exact); for
  * checking the id step alone.  d_ids: device, n uint64. */
 int agj_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, void* stream);
+
+/*
+ * The certified fast cell-id step on the host, with the same FP32 model and
+ * arithmetic the probe kernels use (agj_stats.fast_ids must be 1): for each
+ * point, h_levels[k] = 255 if the point lies outside the model's window (it
+ * joins nothing), else the number L of leading levels (0..30) whose digits
+ * are certified equal to the FP64 spec's, and h_ids[k] = the leaf id built
+ * from the model's (i, j): its first L levels equal the spec id's.
+ * AGJ_EUNSUPPORTED if the index has no fast model.  Host only.
+ */
+int agj_fast_ids_host(const agj_index* index, const double* h_points, uint64_t n, uint64_t* h_ids,
+                      uint8_t* h_levels);
 
 /* Cell ids of points on the host with the same spec (host code). */
 int agj_cell_ids_host(const double* h_points, uint64_t n, uint64_t* h_ids);

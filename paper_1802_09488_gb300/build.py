@@ -28,7 +28,7 @@ NVCCFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", *ARCH, "-Xcompiler
              f"-I{ROOT}/include", "--expt-relaxed-constexpr"]
 
 CU_SOURCES = ["agj_kernels.cu"]
-CXX_SOURCES = ["agj_build.cpp", "agj_capi.cpp"]
+CXX_SOURCES = ["agj_build.cpp", "agj_model.cpp", "agj_capi.cpp"]
 
 
 def _sources():
@@ -48,6 +48,8 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Builds libagj.so; extra nvcc flags may come from $AGJ_NVCC_EXTRA (for
+    example -DAGJ_PROBE_MIN_BLOCKS=4)."""
     if not force and up_to_date():
         return LIB
     if not os.path.exists(NVCC):
@@ -56,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs, objs = [], []
     for f in CU_SOURCES:
         obj = os.path.join(OUT, f.replace(".cu", ".o"))
-        cmd = [NVCC, *NVCCFLAGS, "-c", os.path.join(CSRC, f), "-o", obj]
+        cmd = [NVCC, *NVCCFLAGS, *os.environ.get("AGJ_NVCC_EXTRA", "").split(), "-c", os.path.join(CSRC, f), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         objs.append(obj)
     cxx = shutil.which("g++") or "g++"

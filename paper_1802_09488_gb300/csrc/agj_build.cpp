@@ -824,6 +824,9 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
         *err = "approximate index exceeds the memory budget";
         return AGJ_EBUDGET;
     }
+    if (bp.fast_ids) fit_fast_model(&X, threads);
+    X.stats.fast_ids = (uint32_t)X.model.enabled;
+    X.stats.fast_err_cells = X.model.enabled ? (double)X.model.err : 0.0;
     X.stats.mode = (uint32_t)bp.mode;
     X.stats.n_polys = n_polys;
     X.stats.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -65,6 +65,7 @@ int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, ag
     bp.n_train = o.train_latlng ? o.n_train : 0;
     bp.max_train_level = o.max_train_level ? std::min<uint32_t>(o.max_train_level, 30) : 24;
     bp.threads = o.n_threads;
+    bp.fast_ids = !o.no_fast_ids;
     agj_index* h = new (std::nothrow) agj_index();
     if (!h) return AGJ_ENOMEM;
     int rc;
@@ -246,6 +247,27 @@ int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, do
 int agj_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, void* stream) {
     if (n && (!d_points || !d_ids)) return AGJ_EINVAL;
     return agj::launch_cell_ids(d_points, n, d_ids, as_stream(stream));
+}
+
+int agj_fast_ids_host(const agj_index* index, const double* h_points, uint64_t n, uint64_t* h_ids,
+                      uint8_t* h_levels) {
+    if (!index || (n && (!h_points || !h_ids || !h_levels))) return AGJ_EINVAL;
+    const agj::FastModel& M = index->X.model;
+    if (!M.enabled) return AGJ_EUNSUPPORTED;
+    uint16_t lut[1024];
+    for (uint32_t t = 0; t < 1024; ++t) lut[t] = agj::hilbert_lut_entry(t);
+    for (uint64_t k = 0; k < n; ++k) {
+        uint32_t i, j;
+        int lc;
+        if (!agj::model_ij(M, h_points[2 * k], h_points[2 * k + 1], &i, &j, &lc)) {
+            h_ids[k] = 0;
+            h_levels[k] = 255;
+            continue;
+        }
+        h_ids[k] = agj::cell_id_lut(lut, M.face, i, j);
+        h_levels[k] = (uint8_t)lc;
+    }
+    return AGJ_OK;
 }
 
 int agj_cell_ids_host(const double* h_points, uint64_t n, uint64_t* h_ids) {

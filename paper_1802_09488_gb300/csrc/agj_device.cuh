@@ -30,6 +30,7 @@ struct DevIndex {
     uint32_t n_polys;
     uint32_t max_depth;
     DevFace faces[6];
+    FastModel model;            // certified fast cell ids (enabled == 0: FP64 ids)
 };
 
 constexpr uint32_t kNoRootDev = 0xFFFFFFFFu;
@@ -52,6 +53,34 @@ AGJ_HD int64_t dkey(double x) {
     memcpy(&b, &x, 8);
 #endif
     return b < 0 ? -(b & 0x7FFFFFFFFFFFFFFFll) : b;
+}
+
+// Walks the trie for one leaf cell id computed by the FP64 spec (Listing
+// "Probe Adaptive Cell Trie"): face bits select the root, the root's common
+// prefix must match, then one key byte per level until the entry is not a
+// child pointer.  Returns the final tagged entry (0 = false hit).
+__device__ __forceinline__ uint64_t walk_exact(const DevIndex& X, const DevFace* faces, uint64_t id, uint64_t* err,
+                                               uint32_t* gathers) {
+    if (id == kInvalidId) return 0;
+    const DevFace fr = faces[id >> 61];
+    if (fr.root == kNoRootDev) return 0;
+    uint64_t key = id << 3;
+    if (fr.prefix_bits) {
+        if ((key >> (64 - fr.prefix_bits)) != fr.prefix) return 0;
+        key <<= fr.prefix_bits;
+    }
+    const char* base = reinterpret_cast<const char*>(X.nodes);
+    const uint64_t* node = X.nodes + (uint64_t)fr.root * 256;
+    for (int d = 0; d < 8; ++d) {
+        const uint64_t e = __ldg(node + (key >> 56));
+        ++*gathers;
+        key <<= 8;
+        if ((e & 3ull) != 0ull || e == 0ull) return e;
+        if ((e >> 11) >= X.n_nodes) { atomicOr((unsigned long long*)err, kErrTrieBounds); return 0; }
+        node = reinterpret_cast<const uint64_t*>(base + e);
+    }
+    atomicOr((unsigned long long*)err, kErrTrieBounds);
+    return 0;
 }
 
 // Number of references (true + candidate) an entry holds.

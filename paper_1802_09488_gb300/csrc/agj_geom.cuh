@@ -39,6 +39,12 @@
 #include <cmath>
 #endif
 
+#ifdef __CUDA_ARCH__
+#define AGJ_UNROLL _Pragma("unroll")
+#else
+#define AGJ_UNROLL
+#endif
+
 namespace agj {
 
 constexpr int kLevels = 30;
@@ -212,6 +218,271 @@ AGJ_HD void face_uv_to_xyz(int face, double u, double v, double p[3]) {
         case 4: p[0] = v; p[1] = -1.0; p[2] = -u; break;
         default: p[0] = v; p[1] = u; p[2] = -1.0; break;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Certified fast cell ids
+// ---------------------------------------------------------------------------
+// The FP64 id above costs ~150-200 FP64 instructions per point, and FP64 runs
+// at a small fraction of the FP32 rate on this GPU.  For points inside an
+// index's lat/lng window the library instead evaluates a local FP32 model of
+// X = 2^30 s and Y = 2^30 t (degree-5 polynomials in the offsets from the
+// window centre, first-order terms in double-float) together with a bound
+// err on |model - spec| that the host derives when it fits the model.  The
+// spec's i = floor(X) then lies in [floor(X - err), floor(X + err)]; the
+// leading levels on which both ends agree are exactly the spec's, so the
+// prefix of the id up to that level is bit-exact.  A walk that needs a
+// deeper level than certified recomputes the FP64 id.
+//
+// All arithmetic here is IEEE FP32 / integer with explicit fmaf, so host and
+// device produce identical values (host code -ffp-contract=off, device code
+// -fmad=false); the host evaluates the very same function to bound the error.
+
+constexpr int kFastHiTerms = 18;   // coefficients of degrees 2..5
+
+struct FastModel {
+    int32_t enabled;
+    int32_t face;
+    int32_t path;                   // 1: each coordinate in one binade (raw-bit offsets); 2: general
+    int32_t n0x, n0y;               // integer parts of the constant terms (level-30 cells)
+    float f0x, f0y;                 // their fractional parts
+    float err;                      // bound on |model - spec| incl. rounding allowances (cells)
+    int64_t wlat_lo, wlat_hi, wlng_lo, wlng_hi;   // window: path 1 raw bits, path 2 order keys
+    int64_t lat0, lng0;             // centre: path 1 raw bits, path 2 units of 2^-47 degree
+    int32_t split;                  // bits in the low part of an offset (23 path 1, 24 path 2)
+    float sa_hi, sa_lo, sb_hi, sb_lo;   // scales of the offsets' two parts (powers of two)
+    float xl[4], yl[4];             // first order: c10 hi, c10 lo, c01 hi, c01 lo
+    float xh[kFastHiTerms], yh[kFastHiTerms];     // degrees 2..5 (layout in model_eval)
+};
+
+AGJ_HD int64_t double_bits(double x) {
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    int64_t b;
+    __builtin_memcpy(&b, &x, 8);
+    return b;
+#endif
+}
+
+AGJ_HD int32_t float_bits(float x) {
+#ifdef __CUDA_ARCH__
+    return __float_as_int(x);
+#else
+    int32_t b;
+    __builtin_memcpy(&b, &x, 4);
+    return b;
+#endif
+}
+
+// Order-preserving integer key of a double (sign-magnitude to two's
+// complement; -0.0 and +0.0 share a key; NaNs fall outside every finite range).
+AGJ_HD int64_t dkey_bits(int64_t b) { return b < 0 ? -(b & 0x7FFFFFFFFFFFFFFFll) : b; }
+
+// x (given by its bits, |x| < 256) in units of 2^-47, truncated toward zero.
+AGJ_HD int64_t deg_fixed47(int64_t b) {
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const int64_t m = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const int sh = e - 1028;
+    const int64_t f = sh >= 0 ? (m << sh) : (sh > -63 ? (m >> -sh) : 0);
+    return b < 0 ? -f : f;
+}
+
+AGJ_HD float model_fma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return std::fma(a, b, c);
+#endif
+}
+
+AGJ_HD float model_floor(float x) {
+#ifdef __CUDA_ARCH__
+    return floorf(x);
+#else
+    return std::floor(x);
+#endif
+}
+
+// Error-free sum: s + e == a + b exactly (Knuth).
+AGJ_HD void two_sum(float a, float b, float* s, float* e) {
+    const float x = a + b;
+    const float bv = x - a;
+    const float av = x - bv;
+    *s = x;
+    *e = (a - av) + (b - bv);
+}
+
+// Offsets of a point from the window centre, normalised and split into two
+// floats whose exact sum is the offset.  Returns false outside the window.
+AGJ_HD bool model_offsets(const FastModel& M, int64_t blat, int64_t blng, float* ah, float* al, float* bh, float* bl) {
+    int64_t da, db;
+    if (M.path == 1) {
+        // every lat (lng) of the window shares sign and exponent: raw bits are
+        // ordered like the values and their difference counts ulps
+        if (blat < M.wlat_lo || blat > M.wlat_hi || blng < M.wlng_lo || blng > M.wlng_hi) return false;
+        da = blat - M.lat0;
+        db = blng - M.lng0;
+    } else {
+        const int64_t klat = dkey_bits(blat), klng = dkey_bits(blng);
+        if (klat < M.wlat_lo || klat > M.wlat_hi || klng < M.wlng_lo || klng > M.wlng_hi) return false;
+        da = deg_fixed47(blat) - M.lat0;
+        db = deg_fixed47(blng) - M.lng0;
+    }
+    const int64_t mask = (1ll << M.split) - 1;
+    *ah = (float)(int32_t)(da >> M.split) * M.sa_hi;
+    *al = (float)(int32_t)(da & mask) * M.sa_lo;
+    *bh = (float)(int32_t)(db >> M.split) * M.sb_hi;
+    *bl = (float)(int32_t)(db & mask) * M.sb_lo;
+    return true;
+}
+
+// Model value minus its integer constant, as th + tl (floats; th carries the
+// large first-order and polynomial terms, tl the small remainder and the
+// constant's fraction f0).  Coefficients h: b^0: a^2..a^5 (h0..h3); b^1:
+// a^1..a^4 (h4..h7); b^2: a^0..a^3 (h8..h11); b^3: a^0..a^2 (h12..h14);
+// b^4: a^0, a^1 (h15, h16); b^5: h17.
+AGJ_HD void model_eval(const float l[4], const float h[kFastHiTerms], float f0, float ah, float al, float bh, float bl,
+                       float* th, float* tl) {
+    const float p1 = l[0] * ah;
+    const float e1 = model_fma(l[0], ah, -p1);
+    const float p2 = l[2] * bh;
+    const float e2 = model_fma(l[2], bh, -p2);
+    float corr = e1 + e2;
+    corr = model_fma(l[0], al, corr);
+    corr = model_fma(l[1], ah, corr);
+    corr = model_fma(l[2], bl, corr);
+    corr = model_fma(l[3], bh, corr);
+    const float a = ah + al, b = bh + bl;
+    const float q0 = (a * a) * model_fma(a, model_fma(a, model_fma(a, h[3], h[2]), h[1]), h[0]);
+    const float q1 = a * model_fma(a, model_fma(a, model_fma(a, h[7], h[6]), h[5]), h[4]);
+    const float q2 = model_fma(a, model_fma(a, model_fma(a, h[11], h[10]), h[9]), h[8]);
+    const float q3 = model_fma(a, model_fma(a, h[14], h[13]), h[12]);
+    const float q4 = model_fma(a, h[16], h[15]);
+    float t = model_fma(b, h[17], q4);
+    t = model_fma(b, t, q3);
+    t = model_fma(b, t, q2);
+    t = model_fma(b, t, q1);
+    const float poly = model_fma(b, t, q0);
+    float s1, r1, s2, r2;
+    two_sum(p1, p2, &s1, &r1);
+    two_sum(s1, poly, &s2, &r2);
+    *th = s2;
+    *tl = ((r1 + r2) + corr) + f0;
+}
+
+// floor(n0 + th + tl - err) and floor(n0 + th + tl + err) for small |tl|
+// (the floor of th is exact, so only the small remainder is rounded).
+AGJ_HD void model_cells(int32_t n0, float th, float tl, float err, int32_t* lo, int32_t* hi) {
+    const float k = model_floor(th);
+    const float base = (th - k) + tl;
+    const int32_t c = n0 + (int32_t)k;
+    *lo = c + (int32_t)model_floor(base - err);
+    *hi = c + (int32_t)model_floor(base + err);
+}
+
+// The model's value n0 + th + tl as a double (host-side bound checks).
+AGJ_HD double model_value(int32_t n0, float th, float tl) {
+    const float k = model_floor(th);
+    const float base = (th - k) + tl;
+    return (double)n0 + (double)k + (double)base;
+}
+
+AGJ_HD int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __clz((int)x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+// Fast certified (i, j) of a point.  Returns 0 when the point lies outside
+// the model window (no indexed cell can hold it: the window contains every
+// indexed cell), 1 with *lc = number of leading levels certified (0..30),
+// i and j set from the lower end of the error interval.
+AGJ_HD int model_ij(const FastModel& M, double lat, double lng, uint32_t* i, uint32_t* j, int* lc) {
+    float ah, al, bh, bl;
+    if (!model_offsets(M, double_bits(lat), double_bits(lng), &ah, &al, &bh, &bl)) return 0;
+    float xth, xtl, yth, ytl;
+    model_eval(M.xl, M.xh, M.f0x, ah, al, bh, bl, &xth, &xtl);
+    model_eval(M.yl, M.yh, M.f0y, ah, al, bh, bl, &yth, &ytl);
+    int32_t ilo, ihi, jlo, jhi;
+    model_cells(M.n0x, xth, xtl, M.err, &ilo, &ihi);
+    model_cells(M.n0y, yth, ytl, M.err, &jlo, &jhi);
+    if (ilo < 0 || jlo < 0 || ihi > 1073741823 || jhi > 1073741823) {
+        *i = 0; *j = 0; *lc = 0;
+        return 1;
+    }
+    const int li = clz32((uint32_t)(ilo ^ ihi)) - 2, lj = clz32((uint32_t)(jlo ^ jhi)) - 2;
+    *i = (uint32_t)ilo;
+    *j = (uint32_t)jlo;
+    *lc = li < lj ? li : lj;
+    return 1;
+}
+
+// Hilbert table for 4 levels at a time: index (o << 8) | (i4 << 4) | j4,
+// value (8 position bits << 2) | next orientation.
+struct HilbertLut {
+    uint16_t v[1024];
+};
+
+constexpr uint32_t hilbert_digit_c(uint32_t ib, uint32_t jb, uint32_t& o) {
+    if (o & 1u) { const uint32_t t = ib; ib = jb; jb = t; }
+    if (o & 2u) { ib ^= 1u; jb ^= 1u; }
+    const uint32_t d = (ib << 1) | (ib ^ jb);
+    if (d == 0u) o ^= 1u;
+    else if (d == 3u) o ^= 3u;
+    return d;
+}
+
+constexpr HilbertLut make_hilbert_lut() {
+    HilbertLut L{};
+    for (uint32_t idx = 0; idx < 1024; ++idx) {
+        uint32_t o = idx >> 8, pos = 0;
+        for (int l = 0; l < 4; ++l) pos = (pos << 2) | hilbert_digit_c((idx >> (7 - l)) & 1u, (idx >> (3 - l)) & 1u, o);
+        L.v[idx] = (uint16_t)((pos << 2) | o);
+    }
+    return L;
+}
+
+AGJ_HD uint16_t hilbert_lut_entry(uint32_t idx) {
+    uint32_t o = idx >> 8, pos = 0;
+    for (int l = 0; l < 4; ++l) {
+        const uint32_t ib = (idx >> (7 - l)) & 1u, jb = (idx >> (3 - l)) & 1u;
+        pos = (pos << 2) | hilbert_digit(ib, jb, &o);
+    }
+    return (uint16_t)((pos << 2) | o);
+}
+
+// The leaf id's key bytes (the id shifted left by the 3 face bits): byte b
+// holds the Hilbert digits of levels 4b+1 .. 4b+4, one table lookup each.
+// Levels 31-32 of the last byte are zero padding (the id has its marker and
+// zero tail there); the trie fills every combination of those bits for the
+// few cells that deep, so the walk reads the same entry either way.
+AGJ_HD uint64_t key_bytes_lut(const uint16_t* lut, int face, uint32_t i, uint32_t j) {
+    const uint32_t i32 = i << 2, j32 = j << 2;
+    uint32_t o = (uint32_t)face & 1u, hi = 0, lo = 0;
+    AGJ_UNROLL
+    for (int s = 0; s < 4; ++s) {
+        const uint32_t e = lut[(o << 8) | (((i32 >> (28 - 4 * s)) & 15u) << 4) | ((j32 >> (28 - 4 * s)) & 15u)];
+        hi = (hi << 8) | (e >> 2);
+        o = e & 3u;
+    }
+    AGJ_UNROLL
+    for (int s = 4; s < 8; ++s) {
+        const uint32_t e = lut[(o << 8) | (((i32 >> (28 - 4 * s)) & 15u) << 4) | ((j32 >> (28 - 4 * s)) & 15u)];
+        lo = (lo << 8) | (e >> 2);
+        o = e & 3u;
+    }
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Leaf cell id from level-30 (i, j) with the 4-level table (same value as
+// cell_id_from_ij(face, i, j, 30)).
+AGJ_HD uint64_t cell_id_lut(const uint16_t* lut, int face, uint32_t i, uint32_t j) {
+    const uint64_t key = key_bytes_lut(lut, face, i, j);
+    return ((uint64_t)face << 61) | ((key >> 4) << 1) | 1ull;
 }
 
 }  // namespace agj

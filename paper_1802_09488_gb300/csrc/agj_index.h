@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/agj.h"
+#include "agj_geom.cuh"
 
 namespace agj {
 
@@ -56,6 +57,7 @@ struct Index {
     std::vector<uint32_t> poly_off;   // n_polys + 1
     std::vector<double> poly_bbox;    // 4 per polygon: umin umax vmin vmax
     std::vector<int8_t> poly_face;
+    FastModel model{};                // certified fast cell ids (disabled: all zero)
     agj_stats stats{};
     // device copies (owned)
     void* d_blob = nullptr;
@@ -74,12 +76,17 @@ struct BuildParams {
     uint64_t n_train;
     uint32_t max_train_level;
     uint32_t threads;
+    bool fast_ids;
 };
 
 // Host build of the logical and physical index (no CUDA calls).  Returns an
 // AGJ_* status; on failure *err_msg says why.
 int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp, Index* out,
                std::string* err_msg);
+
+// Fits idx->model (the certified fast cell-id model) for the index's cells;
+// leaves it disabled when the cells span faces or too wide a window.
+void fit_fast_model(Index* idx, unsigned threads);
 
 // The super-covering merge on given (cell, reference) pairs, in order.
 void supercover(const uint64_t* cells, const uint32_t* refs, uint64_t n, std::vector<uint64_t>* out_cells,

@@ -2,10 +2,14 @@
 // launchers.
 //
 //   k_cell_ids       point -> 64-bit cell id (FP64 spec of agj_geom.cuh)
-//   k_join_approx    one pass per tile: cell id, face/prefix stage, trie walk
-//                    (Listing "Probe Adaptive Cell Trie"), entry decode, tile
-//                    scan with decoupled look-back, CSR write (approximate
-//                    join: every reference is output, §V "approx")
+//   k_probe_approx   per 128-point warp tile: cell id, face/prefix stage, trie
+//                    walk (Listing "Probe Adaptive Cell Trie"); stores each
+//                    point's tagged entry and the tile's reference count
+//   k_scan_counts    exclusive scan of tile counts (decoupled look-back over
+//                    CTA chunks of 4096 tiles)
+//   k_emit_approx    offsets and ids (every reference: §V "approx")
+//   k_join_approx    the same three steps in one pass with a per-tile
+//                    look-back (used where no work space can be allocated)
 //   k_probe_exact    cell id + walk + decode; true hits counted, candidate
 //                    references compacted by warp ballot into a queue
 //   k_poly_scan      per-polygon candidate counts -> queue segments + chunks
@@ -13,7 +17,8 @@
 //   k_pip            exact ST_Covers refine (§II "PIP"): one CTA per chunk of
 //                    one polygon's candidates, the polygon's edges staged in
 //                    shared memory and read by all threads (broadcast)
-//   k_csr_exact      true hits + passing candidates -> CSR (one pass, look-back)
+//   k_count_exact    per-tile pair counts (true hits + passing candidates)
+//   k_emit_exact     offsets and ids of the exact join
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,10 +35,15 @@
 namespace agj {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+__device__ const HilbertLut g_hilbert_lut = make_hilbert_lut();
 constexpr uint32_t kSpinLimit = 1u << 22;
+#ifndef AGJ_PROBE_MIN_BLOCKS
+#define AGJ_PROBE_MIN_BLOCKS 3   // resident CTAs per SM the probe kernels are compiled for
+#endif
 constexpr int kJoinBlock = 256;
-constexpr int kJoinPPT = 4;
-constexpr int kTile = kJoinBlock * kJoinPPT;
+constexpr int kJoinPPT = 2;
+constexpr int kWarpsPerBlock = kJoinBlock / 32;
+constexpr int kTile = 32 * kJoinPPT;           // points per warp tile (scan granularity)
 constexpr int kPipBlock = 256;
 constexpr int kPipSmemVerts = 2048;           // vertices staged per pass (32 B each)
 
@@ -114,77 +124,153 @@ __device__ uint64_t lookback(uint64_t* tiles, uint32_t tile, uint64_t total, uin
 }
 
 // ---------------------------------------------------------------------------
-// per-tile point staging + walk
+// per-point probe: cell id -> face root -> common prefix -> trie walk
 // ---------------------------------------------------------------------------
 
-// Cell ids and trie entries for PPT consecutive points per thread; walks of
-// the PPT points advance level by level together so their gathers overlap.
+// Walk state of one point.  The key bytes of the leaf id are produced one at
+// a time from the 4-level Hilbert table as the walk consumes them (byte b
+// holds levels 4b+1 .. 4b+4).
+struct Walk {
+    uint32_t i32, j32;      // (i, j) << 2: levels 31-32 are zero padding
+    uint32_t o;             // Hilbert orientation before byte b
+    uint32_t b;             // next key byte
+    uint32_t node;          // current trie node
+    int32_t cert;           // key bytes whose levels are all certified
+    int32_t st;             // 0 done, 1 walking, 2 needs the FP64 cell id
+};
+
+__device__ __forceinline__ uint32_t next_byte(const uint16_t* lut, Walk& w) {
+    const uint32_t sh = 28u - 4u * w.b;
+    const uint32_t e = lut[(w.o << 8) | (((w.i32 >> sh) & 15u) << 4) | ((w.j32 >> sh) & 15u)];
+    w.o = e & 3u;
+    ++w.b;
+    return e >> 2;
+}
+
+// Cell id + face/prefix stage (§IV-B stage 1) for one point.  With the
+// index's fast model (and exact == false) the id comes from the certified FP32
+// path; otherwise from the FP64 spec.  Leaves w.st = 0 when the point joins
+// nothing, 1 when the walk can start at w.node, 2 when an uncertified level
+// decides the prefix.
+__device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* faces, const uint16_t* lut, double lat,
+                                           double lng, bool exact, Walk& w) {
+    uint32_t i, j;
+    int lc, face;
+    w.st = 0;
+    if (!exact && X.model.enabled) {
+        if (!model_ij(X.model, lat, lng, &i, &j, &lc)) return;       // outside the window: in no cell
+        face = X.model.face;
+        if (lc >= kLevels) lc = kLevels + 2;                        // exact id: padding levels too
+    } else {
+        if (!point_valid(lat, lng)) return;
+        double u, v;
+        face = face_uv(lat, lng, &u, &v);
+        i = st_to_ij(uv_to_st(u));
+        j = st_to_ij(uv_to_st(v));
+        lc = kLevels + 2;
+    }
+    const DevFace fr = faces[face];
+    if (fr.root == kNoRootDev) return;
+    w.i32 = i << 2;
+    w.j32 = j << 2;
+    w.o = (uint32_t)face & 1u;
+    w.b = 0;
+    w.cert = lc >> 2;
+    const uint32_t nb = fr.prefix_bits >> 3;
+    for (uint32_t q = 0; q < nb; ++q) {
+        const uint32_t byte = next_byte(lut, w);
+        if (byte != (uint32_t)((fr.prefix >> (8 * (nb - 1 - q))) & 0xFFu)) {
+            w.st = (int32_t)q < w.cert ? 0 : 2;                     // certain mismatch: no cell
+            return;
+        }
+    }
+    if ((int32_t)nb > w.cert) { w.st = 2; return; }
+    w.node = fr.root;
+    w.st = 1;
+}
+
+// Walks of PPT points advance level by level together, so their gathers
+// (Listing "Probe Adaptive Cell Trie") are in flight at the same time.
+// Points whose walk needs an uncertified key byte get their FP64 id and walk
+// again alone (counted in *fallbacks).  Returns the trie entries read.
 template <int PPT>
-__device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFace* faces, const double2* s_pts, int first,
-                                                 int valid, uint64_t e[PPT], uint64_t* err) {
+__device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
+                                                 const uint64_t* s_root, const double* lat, const double* lng,
+                                                 const bool* valid, uint64_t e[PPT], uint64_t* err,
+                                                 uint32_t* fallbacks) {
     uint32_t gathers = 0;
-    uint64_t key[PPT];
-    const uint64_t* node[PPT];
-    bool act[PPT];
+    Walk w[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         e[k] = 0;
-        act[k] = false;
-        node[k] = X.nodes;
-        key[k] = 0;
-        if (k < valid) {
-            const double2 p = s_pts[first + k];
-            const uint64_t id = point_cell_id(p.x, p.y);
-            if (id != kInvalidId) {
-                const DevFace fr = faces[id >> 61];
-                if (fr.root != kNoRootDev) {
-                    uint64_t kk = id << 3;
-                    bool ok = true;
-                    if (fr.prefix_bits) {
-                        ok = (kk >> (64 - fr.prefix_bits)) == fr.prefix;
-                        kk <<= fr.prefix_bits;
-                    }
-                    if (ok) {
-                        act[k] = true;
-                        key[k] = kk;
-                        node[k] = X.nodes + (uint64_t)fr.root * 256;
-                    }
-                }
-            }
-        }
+        w[k].st = 0;
+        if (valid[k]) begin_walk(X, faces, lut, lat[k], lng[k], false, w[k]);
     }
-    const char* base = reinterpret_cast<const char*>(X.nodes);
 #pragma unroll 1
     for (int d = 0; d < 8; ++d) {
         uint64_t v[PPT];
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) v[k] = act[k] ? __ldg(node[k] + (key[k] >> 56)) : 0ull;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) gathers += act[k] ? 1u : 0u;
+        for (int k = 0; k < PPT; ++k) {
+            v[k] = 0;
+            if (w[k].st == 1) {
+                if (w[k].b >= (uint32_t)w[k].cert) {
+                    w[k].st = 2;
+                } else {
+                    const uint32_t byte = next_byte(lut, w[k]);
+                    // with the fast model every walk starts at the model face's root,
+                    // which each CTA holds in shared memory
+                    v[k] = (d == 0 && s_root) ? s_root[byte] : __ldg(X.nodes + (((uint64_t)w[k].node) << 8) + byte);
+                }
+            }
+        }
         bool any = false;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            if (!act[k]) continue;
-            key[k] <<= 8;
+            if (w[k].st != 1) continue;
+            ++gathers;
             if ((v[k] & 3ull) != 0ull || v[k] == 0ull) {
                 e[k] = v[k];
-                act[k] = false;
+                w[k].st = 0;
             } else if ((v[k] >> 11) >= X.n_nodes) {
                 atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
-                act[k] = false;
+                w[k].st = 0;
             } else {
-                node[k] = reinterpret_cast<const uint64_t*>(base + v[k]);
+                w[k].node = (uint32_t)(v[k] >> 11);
                 any = true;
             }
         }
         if (!any) break;
     }
 #pragma unroll
-    for (int k = 0; k < PPT; ++k)
-        if (act[k]) {
+    for (int k = 0; k < PPT; ++k) {
+        if (w[k].st == 1) {
             atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
             e[k] = 0;
+        } else if (w[k].st == 2) {
+            ++*fallbacks;
+            Walk x;
+            begin_walk(X, faces, lut, lat[k], lng[k], true, x);
+            e[k] = 0;
+            while (x.st == 1) {
+                if (x.b >= 8u) {
+                    atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
+                    break;
+                }
+                const uint32_t byte = next_byte(lut, x);
+                const uint64_t v = __ldg(X.nodes + (((uint64_t)x.node) << 8) + byte);
+                ++gathers;
+                if ((v & 3ull) != 0ull || v == 0ull) {
+                    e[k] = v;
+                    break;
+                }
+                if ((v >> 11) >= X.n_nodes) {
+                    atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
+                    break;
+                }
+                x.node = (uint32_t)(v >> 11);
+            }
         }
+    }
     return gathers;
 }
 
@@ -193,6 +279,32 @@ __device__ __forceinline__ void warp_count(uint32_t v, uint64_t* counter) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long*)counter, (unsigned long long)v);
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Per-CTA setup shared by the probe kernels: Hilbert table and face table in
+// shared memory, and, with the fast model, the model face's root node.
+// Returns the shared root (or null).
+__device__ __forceinline__ const uint64_t* cta_setup(const DevIndex& X, uint16_t* s_hlut, DevFace* s_faces,
+                                                     uint64_t* s_root) {
+    for (int t = threadIdx.x; t < 512; t += blockDim.x)
+        reinterpret_cast<uint32_t*>(s_hlut)[t] = reinterpret_cast<const uint32_t*>(g_hilbert_lut.v)[t];
+    if (threadIdx.x < 6) s_faces[threadIdx.x] = X.faces[threadIdx.x];
+    if (!s_root || !X.model.enabled) return nullptr;
+    const uint32_t root = X.faces[X.model.face].root;
+    if (root == kNoRootDev) return nullptr;
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(X.nodes + (uint64_t)root * 256);
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) reinterpret_cast<ulonglong2*>(s_root)[t] = __ldg(src + t);
+    return s_root;
 }
 
 __device__ __forceinline__ uint32_t payload_of(uint64_t e, int which) {
@@ -243,106 +355,115 @@ __global__ void k_cell_ids(const double2* __restrict__ pts, uint64_t n, uint64_t
     }
 }
 
-template <int BLOCK, int PPT>
-__global__ void __launch_bounds__(BLOCK) k_join_approx(DevIndex X, const double2* __restrict__ pts, uint32_t n,
-                                                       uint32_t* __restrict__ offsets, uint32_t* __restrict__ ids,
-                                                       uint64_t ids_cap, uint64_t* __restrict__ tiles,
-                                                       uint32_t* __restrict__ tile_counter, uint64_t* __restrict__ status) {
-    constexpr int TILE = BLOCK * PPT;
+// One warp tile = 32 lanes x PPT points, point base + lane + 32 k, so the
+// 16-byte point loads and the offset stores of a warp are contiguous.  Each
+// warp scans its own tile and looks back on its own tile state, so no CTA
+// barrier follows the setup.  Warp tiles are numbered from the CTA's ticket
+// (the order CTAs started), which keeps the look-back free of deadlock.
+template <int PPT>
+__global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS) k_join_approx(DevIndex X, const double2* __restrict__ pts, uint32_t n,
+                                                            uint32_t* __restrict__ offsets, uint32_t* __restrict__ ids,
+                                                            uint64_t ids_cap, uint64_t* __restrict__ tiles,
+                                                            uint32_t* __restrict__ tile_counter,
+                                                            uint64_t* __restrict__ status,
+                                                            uint64_t* __restrict__ fallback_counter) {
+    __shared__ __align__(16) uint16_t s_hlut[1024];
+    __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
-    __shared__ double2 s_pts[TILE];
-    __shared__ uint32_t s_warp[BLOCK / 32];
-    __shared__ uint32_t s_tile;
-    __shared__ uint64_t s_prefix;
-    if (threadIdx.x < 6) s_faces[threadIdx.x] = X.faces[threadIdx.x];
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __shared__ uint32_t s_cta;
+    const uint64_t* s_root = cta_setup(X, s_hlut, s_faces, s_rootbuf);
+    if (threadIdx.x == 0) s_cta = atomicAdd(tile_counter, 1u);
     __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t tbase = (uint64_t)tile * TILE;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wt = s_cta * kWarpsPerBlock + (threadIdx.x >> 5);
+    const uint64_t base = (uint64_t)wt * (32 * PPT);
+    if (base >= n) return;
+    const uint32_t n_wt = (uint32_t)((n + 32 * PPT - 1) / (32 * PPT));
+    double lat[PPT], lng[PPT];
+    bool valid[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const uint64_t p = tbase + (uint64_t)k * BLOCK + threadIdx.x;
-        if (p < n) s_pts[k * BLOCK + threadIdx.x] = pts[p];
+        const uint64_t p = base + lane + 32 * k;
+        valid[k] = p < n;
+        const double2 q = valid[k] ? __ldcs(pts + p) : make_double2(0.0, 0.0);   // streamed once: evict first
+        lat[k] = q.x;
+        lng[k] = q.y;
     }
-    __syncthreads();
-    const uint64_t my0 = tbase + (uint64_t)threadIdx.x * PPT;
-    const int valid = my0 >= n ? 0 : (int)min((uint64_t)PPT, n - my0);
     uint64_t e[PPT];
-    warp_count(probe_points<PPT>(X, s_faces, s_pts, threadIdx.x * PPT, valid, e, &status[1]), &status[3]);
-    uint32_t c[PPT], sum = 0;
+    uint32_t fallbacks = 0;
+    warp_count(probe_points<PPT>(X, s_faces, s_hlut, s_root, lat, lng, valid, e, &status[1], &fallbacks), &status[3]);
+    warp_count(fallbacks, fallback_counter);
+    uint32_t c[PPT], ex[PPT], run = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         uint32_t nt, nc;
         entry_counts(X, e[k], &nt, &nc);
         c[k] = nt + nc;
-        sum += c[k];
+        const uint32_t incl = warp_incl_scan(c[k]);
+        ex[k] = run + incl - c[k];
+        run += __shfl_sync(kFull, incl, 31);
     }
-    uint32_t block_total;
-    const uint32_t excl = block_excl_scan<BLOCK>(sum, &block_total, s_warp);
-    if (threadIdx.x < 32) {
-        const uint64_t pre = lookback(tiles, tile, block_total, status);
-        if (threadIdx.x == 0) s_prefix = pre;
-    }
-    __syncthreads();
-    uint64_t o = s_prefix + excl;
+    const uint64_t prefix = lookback(tiles, wt, run, status);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        if (k < valid) {
-            offsets[my0 + k] = (uint32_t)o;
-            if (c[k]) {
-                if (o + c[k] <= ids_cap) emit_all(X, e[k], ids, o);
-                else atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrIdsCapacity);
-            }
-            o += c[k];
+        if (!valid[k]) continue;
+        const uint64_t p = base + lane + 32 * k;
+        const uint64_t o = prefix + ex[k];
+        __stcs(offsets + p, (uint32_t)o);
+        if (c[k]) {
+            if (o + c[k] <= ids_cap) emit_all(X, e[k], ids, o);
+            else atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrIdsCapacity);
         }
     }
-    if (tile == gridDim.x - 1 && threadIdx.x == 0) {
-        const uint64_t nnz = s_prefix + block_total;
-        offsets[n] = (uint32_t)nnz;
-        status[0] = nnz;
+    if (wt == n_wt - 1 && lane == 0) {
+        offsets[n] = (uint32_t)(prefix + run);
+        status[0] = prefix + run;
     }
 }
 
-// Exact-mode probe: entries + compacted candidate queue.
-template <int BLOCK, int PPT>
-__global__ void __launch_bounds__(BLOCK) k_probe_exact(DevIndex X, const double2* __restrict__ pts, uint32_t n,
-                                                       uint64_t* __restrict__ entries, uint32_t* __restrict__ qbase,
-                                                       uint2* __restrict__ queue, uint64_t queue_cap,
-                                                       uint32_t* __restrict__ queue_len,
-                                                       uint32_t* __restrict__ poly_count, uint64_t* __restrict__ status) {
-    constexpr int TILE = BLOCK * PPT;
+// Exact-mode probe: entries + compacted candidate queue (warp ballot: one
+// atomic reserves a warp's slots).
+template <int PPT>
+__global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS) k_probe_exact(DevIndex X, const double2* __restrict__ pts, uint32_t n,
+                                                            uint64_t* __restrict__ entries, uint32_t* __restrict__ qbase,
+                                                            uint2* __restrict__ queue, uint64_t queue_cap,
+                                                            uint32_t* __restrict__ queue_len,
+                                                            uint32_t* __restrict__ poly_count,
+                                                            uint64_t* __restrict__ status,
+                                                            uint64_t* __restrict__ fallback_counter) {
+    __shared__ __align__(16) uint16_t s_hlut[1024];
+    __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
-    __shared__ double2 s_pts[TILE];
-    if (threadIdx.x < 6) s_faces[threadIdx.x] = X.faces[threadIdx.x];
-    const uint64_t tbase = (uint64_t)blockIdx.x * TILE;
+    const uint64_t* s_root = cta_setup(X, s_hlut, s_faces, s_rootbuf);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t base = ((uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * (32 * PPT);
+    if (base >= n) return;
+    double lat[PPT], lng[PPT];
+    bool valid[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const uint64_t p = tbase + (uint64_t)k * BLOCK + threadIdx.x;
-        if (p < n) s_pts[k * BLOCK + threadIdx.x] = pts[p];
+        const uint64_t p = base + lane + 32 * k;
+        valid[k] = p < n;
+        const double2 q = valid[k] ? __ldcs(pts + p) : make_double2(0.0, 0.0);
+        lat[k] = q.x;
+        lng[k] = q.y;
     }
-    __syncthreads();
-    const uint64_t my0 = tbase + (uint64_t)threadIdx.x * PPT;
-    const int valid = my0 >= n ? 0 : (int)min((uint64_t)PPT, n - my0);
     uint64_t e[PPT];
-    warp_count(probe_points<PPT>(X, s_faces, s_pts, threadIdx.x * PPT, valid, e, &status[1]), &status[3]);
+    uint32_t fallbacks = 0;
+    warp_count(probe_points<PPT>(X, s_faces, s_hlut, s_root, lat, lng, valid, e, &status[1], &fallbacks), &status[3]);
+    warp_count(fallbacks, fallback_counter);
     uint32_t nc[PPT], csum = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         uint32_t nt;
         entry_counts(X, e[k], &nt, &nc[k]);
         csum += nc[k];
-        if (k < valid) entries[my0 + k] = e[k];
+        if (valid[k]) entries[base + lane + 32 * k] = e[k];
     }
-    // warp-ballot compaction: one atomic per warp reserves the warp's slots
-    const int lane = threadIdx.x & 31;
-    uint32_t x = csum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
-    }
+    const uint32_t x = warp_incl_scan(csum);
     const uint32_t wtotal = __shfl_sync(kFull, x, 31);
-    if (__ballot_sync(kFull, csum != 0) == 0) return;
+    if (wtotal == 0) return;
     uint32_t wbase = 0;
     if (lane == 0) {
         wbase = atomicAdd(queue_len, wtotal);
@@ -353,19 +474,15 @@ __global__ void __launch_bounds__(BLOCK) k_probe_exact(DevIndex X, const double2
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (!nc[k]) continue;
-        const uint32_t p = (uint32_t)(my0 + k);
+        const uint32_t p = (uint32_t)(base + lane + 32 * k);
         qbase[p] = (uint32_t)q;
         const uint64_t ek = e[k];
         const uint32_t tag = (uint32_t)(ek & 3ull);
-        uint32_t polys[2];
-        uint32_t m = 0;
         if (tag == 1 || tag == 2) {
-            for (int w = 0; w < (int)tag; ++w) {
-                const uint32_t pl = payload_of(ek, w);
-                if (!(pl & 1u)) polys[m++] = pl >> 1;
-            }
-            for (uint32_t t = 0; t < m; ++t) {
-                if (q < queue_cap) { queue[q] = make_uint2(p, polys[t]); atomicAdd(&poly_count[polys[t]], 1u); }
+            for (int t = 0; t < (int)tag; ++t) {
+                const uint32_t pl = payload_of(ek, t);
+                if (pl & 1u) continue;
+                if (q < queue_cap) { queue[q] = make_uint2(p, pl >> 1); atomicAdd(&poly_count[pl >> 1], 1u); }
                 else atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrQueueOverflow);
                 ++q;
             }
@@ -378,6 +495,233 @@ __global__ void __launch_bounds__(BLOCK) k_probe_exact(DevIndex X, const double2
                 if (q < queue_cap) { queue[q] = make_uint2(p, pg); atomicAdd(&poly_count[pg], 1u); }
                 else atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrQueueOverflow);
                 ++q;
+            }
+        }
+    }
+}
+
+// Approximate join, step 1: cell id + walk for every point of a warp tile;
+// the tagged entry of each point is stored and the tile's number of
+// references is counted (no waiting on other tiles).
+template <int PPT>
+__global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS) k_probe_approx(
+    DevIndex X, const double2* __restrict__ pts, uint32_t n, uint64_t* __restrict__ entries,
+    uint32_t* __restrict__ tile_count, uint64_t* __restrict__ status, uint64_t* __restrict__ fallback_counter) {
+    __shared__ __align__(16) uint16_t s_hlut[1024];
+    __shared__ __align__(16) uint64_t s_rootbuf[256];
+    __shared__ DevFace s_faces[6];
+    const uint64_t* s_root = cta_setup(X, s_hlut, s_faces, s_rootbuf);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const uint64_t base = wt * (32 * PPT);
+    if (base >= n) return;
+    double lat[PPT], lng[PPT];
+    bool valid[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        valid[k] = p < n;
+        const double2 q = valid[k] ? __ldcs(pts + p) : make_double2(0.0, 0.0);   // streamed once: evict first
+        lat[k] = q.x;
+        lng[k] = q.y;
+    }
+    uint64_t e[PPT];
+    uint32_t fallbacks = 0;
+    warp_count(probe_points<PPT>(X, s_faces, s_hlut, s_root, lat, lng, valid, e, &status[1], &fallbacks), &status[3]);
+    warp_count(fallbacks, fallback_counter);
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        uint32_t nt, nc;
+        entry_counts(X, e[k], &nt, &nc);
+        c += nt + nc;
+        if (valid[k]) entries[base + lane + 32 * k] = e[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+    if (lane == 0) tile_count[wt] = c;
+}
+
+// Exclusive scan of the per-tile counts: CTA chunks of 16 x 256 counts, chained
+// by the decoupled look-back (a few hundred chunks, so the look-back is short).
+// The last chunk writes the total to offsets[n] and status[0].
+constexpr int kScanItems = 16;
+__global__ void __launch_bounds__(256) k_scan_counts(const uint32_t* __restrict__ tile_count, uint64_t m,
+                                                     uint32_t* __restrict__ tile_prefix, uint64_t* __restrict__ chunks,
+                                                     uint32_t* __restrict__ chunk_counter, uint32_t* __restrict__ offsets,
+                                                     uint32_t n, uint64_t* __restrict__ status) {
+    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_chunk;
+    __shared__ uint64_t s_prefix;
+    if (threadIdx.x == 0) s_chunk = atomicAdd(chunk_counter, 1u);
+    __syncthreads();
+    const uint32_t chunk = s_chunk;
+    const uint64_t i0 = (uint64_t)chunk * (256 * kScanItems) + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = i0 + k < m ? tile_count[i0 + k] : 0u;
+        sum += v[k];
+    }
+    uint32_t total;
+    const uint32_t excl = block_excl_scan<256>(sum, &total, s_warp);
+    if (threadIdx.x < 32) {
+        const uint64_t pre = lookback(chunks, chunk, total, status);
+        if (threadIdx.x == 0) s_prefix = pre;
+    }
+    __syncthreads();
+    uint64_t o = s_prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (i0 + k < m) tile_prefix[i0 + k] = (uint32_t)o;
+        o += v[k];
+    }
+    if (chunk == gridDim.x - 1 && threadIdx.x == 0) {
+        const uint64_t nnz = s_prefix + total;
+        offsets[n] = (uint32_t)nnz;
+        status[0] = nnz;
+    }
+}
+
+// Approximate join, step 3: offsets and ids of a warp tile from its stored
+// entries and its prefix.
+template <int PPT>
+__global__ void __launch_bounds__(kJoinBlock) k_emit_approx(DevIndex X, uint32_t n, const uint64_t* __restrict__ entries,
+                                                            const uint32_t* __restrict__ tile_prefix,
+                                                            uint32_t* __restrict__ offsets, uint32_t* __restrict__ ids,
+                                                            uint64_t ids_cap, uint64_t* __restrict__ status) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const uint64_t base = wt * (32 * PPT);
+    if (base >= n) return;
+    uint64_t e[PPT];
+    uint32_t c[PPT], ex[PPT], run = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        e[k] = p < n ? __ldcs(entries + p) : 0ull;
+        uint32_t nt, nc;
+        entry_counts(X, e[k], &nt, &nc);
+        c[k] = nt + nc;
+        const uint32_t incl = warp_incl_scan(c[k]);
+        ex[k] = run + incl - c[k];
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    const uint64_t prefix = tile_prefix[wt];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        if (p >= n) continue;
+        const uint64_t o = prefix + ex[k];
+        __stcs(offsets + p, (uint32_t)o);
+        if (c[k]) {
+            if (o + c[k] <= ids_cap) emit_all(X, e[k], ids, o);
+            else atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrIdsCapacity);
+        }
+    }
+}
+
+// Exact join: number of output pairs of one point (true references plus the
+// candidates that passed the PIP), -1 flags a corrupt queue position.
+__device__ __forceinline__ uint32_t exact_count(const DevIndex& X, uint64_t e, const uint32_t* qbase, uint64_t p,
+                                                const uint8_t* pass, uint64_t queue_cap, uint32_t* qb,
+                                                uint64_t* status) {
+    uint32_t nt, nc;
+    entry_counts(X, e, &nt, &nc);
+    *qb = 0;
+    if (!nc) return nt;
+    *qb = qbase[p];
+    if ((uint64_t)*qb + nc > queue_cap) {   // cannot happen: the queue holds n * max_cand_refs
+        atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrQueueOverflow);
+        return 0xFFFFFFFFu;
+    }
+    uint32_t c = nt;
+    for (uint32_t t = 0; t < nc; ++t) c += pass[*qb + t];
+    return c;
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(kJoinBlock) k_count_exact(DevIndex X, uint32_t n, const uint64_t* __restrict__ entries,
+                                                            const uint32_t* __restrict__ qbase,
+                                                            const uint8_t* __restrict__ pass, uint64_t queue_cap,
+                                                            uint32_t* __restrict__ tile_count,
+                                                            uint64_t* __restrict__ status) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const uint64_t base = wt * (32 * PPT);
+    if (base >= n) return;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        if (p >= n) continue;
+        uint32_t qb;
+        const uint32_t x = exact_count(X, entries[p], qbase, p, pass, queue_cap, &qb, status);
+        c += x == 0xFFFFFFFFu ? 0u : x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+    if (lane == 0) tile_count[wt] = c;
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(kJoinBlock) k_emit_exact(DevIndex X, uint32_t n, const uint64_t* __restrict__ entries,
+                                                           const uint32_t* __restrict__ qbase,
+                                                           const uint8_t* __restrict__ pass, uint64_t queue_cap,
+                                                           const uint32_t* __restrict__ tile_prefix,
+                                                           uint32_t* __restrict__ offsets, uint32_t* __restrict__ ids,
+                                                           uint64_t ids_cap, uint64_t* __restrict__ status) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const uint64_t base = wt * (32 * PPT);
+    if (base >= n) return;
+    uint64_t e[PPT];
+    uint32_t cnt[PPT], qb[PPT], ex[PPT], run = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        e[k] = p < n ? entries[p] : 0ull;
+        cnt[k] = p < n ? exact_count(X, e[k], qbase, p, pass, queue_cap, &qb[k], status) : 0u;
+        if (cnt[k] == 0xFFFFFFFFu) { cnt[k] = 0; e[k] = 0; }
+        const uint32_t incl = warp_incl_scan(cnt[k]);
+        ex[k] = run + incl - cnt[k];
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    const uint64_t prefix = tile_prefix[wt];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        if (p >= n) continue;
+        const uint64_t o = prefix + ex[k];
+        __stcs(offsets + p, (uint32_t)o);
+        if (!cnt[k]) continue;
+        if (o + cnt[k] > ids_cap) {
+            atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrIdsCapacity);
+            continue;
+        }
+        const uint64_t ek = e[k];
+        const uint32_t tag = (uint32_t)(ek & 3ull);
+        uint64_t w = o;
+        uint32_t ci = 0;
+        if (tag == 1 || tag == 2) {
+            for (int t = 0; t < (int)tag; ++t) {
+                const uint32_t pl = payload_of(ek, t);
+                if (pl & 1u) ids[w++] = pl >> 1;
+                else if (pass[qb[k] + ci++]) ids[w++] = pl >> 1;
+            }
+        } else if (tag == 3) {
+            const uint32_t off = payload_of(ek, 0);
+            const uint32_t nt = __ldg(X.lut + off);
+            const uint32_t* T = X.lut + off + 1;
+            const uint32_t nc = __ldg(X.lut + off + 1 + nt);
+            const uint32_t* Cc = X.lut + off + 2 + nt;
+            uint32_t a = 0, b = 0;
+            while (a < nt || b < nc) {
+                const uint32_t ta = a < nt ? __ldg(T + a) : 0xFFFFFFFFu;
+                const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
+                if (ta < cb) { ids[w++] = ta; ++a; }
+                else { if (pass[qb[k] + b]) ids[w++] = cb; ++b; }
             }
         }
     }
@@ -500,93 +844,6 @@ __global__ void __launch_bounds__(kPipBlock) k_pip(DevIndex X, const double2* __
     }
 }
 
-template <int BLOCK, int PPT>
-__global__ void __launch_bounds__(BLOCK) k_csr_exact(DevIndex X, uint32_t n, const uint64_t* __restrict__ entries,
-                                                     const uint32_t* __restrict__ qbase, const uint8_t* __restrict__ pass,
-                                                     uint64_t queue_cap,
-                                                     uint32_t* __restrict__ offsets, uint32_t* __restrict__ ids,
-                                                     uint64_t ids_cap, uint64_t* __restrict__ tiles,
-                                                     uint32_t* __restrict__ tile_counter, uint64_t* __restrict__ status) {
-    constexpr int TILE = BLOCK * PPT;
-    __shared__ uint32_t s_warp[BLOCK / 32];
-    __shared__ uint32_t s_tile;
-    __shared__ uint64_t s_prefix;
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t my0 = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * PPT;
-    const int valid = my0 >= n ? 0 : (int)min((uint64_t)PPT, n - my0);
-    uint64_t e[PPT];
-    uint32_t cnt[PPT], qb[PPT], sum = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        e[k] = k < valid ? entries[my0 + k] : 0ull;
-        uint32_t nt, nc;
-        entry_counts(X, e[k], &nt, &nc);
-        cnt[k] = nt;
-        qb[k] = 0;
-        if (nc) {
-            qb[k] = qbase[my0 + k];
-            if ((uint64_t)qb[k] + nc > queue_cap) {   // cannot happen: the queue holds n * max_cand_refs
-                atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrQueueOverflow);
-                e[k] = 0;
-                nc = 0;
-            }
-            for (uint32_t t = 0; t < nc; ++t) cnt[k] += pass[qb[k] + t];
-        }
-        sum += cnt[k];
-    }
-    uint32_t block_total;
-    const uint32_t excl = block_excl_scan<BLOCK>(sum, &block_total, s_warp);
-    if (threadIdx.x < 32) {
-        const uint64_t pre = lookback(tiles, tile, block_total, status);
-        if (threadIdx.x == 0) s_prefix = pre;
-    }
-    __syncthreads();
-    uint64_t o = s_prefix + excl;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (k >= valid) continue;
-        offsets[my0 + k] = (uint32_t)o;
-        if (!cnt[k]) continue;
-        if (o + cnt[k] > ids_cap) {
-            atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrIdsCapacity);
-            o += cnt[k];
-            continue;
-        }
-        const uint64_t ek = e[k];
-        const uint32_t tag = (uint32_t)(ek & 3ull);
-        uint64_t w = o;
-        uint32_t ci = 0;
-        if (tag == 1 || tag == 2) {
-            for (int t = 0; t < (int)tag; ++t) {
-                const uint32_t pl = payload_of(ek, t);
-                if (pl & 1u) ids[w++] = pl >> 1;
-                else if (pass[qb[k] + ci++]) ids[w++] = pl >> 1;
-            }
-        } else if (tag == 3) {
-            const uint32_t off = payload_of(ek, 0);
-            const uint32_t nt = __ldg(X.lut + off);
-            const uint32_t* T = X.lut + off + 1;
-            const uint32_t nc = __ldg(X.lut + off + 1 + nt);
-            const uint32_t* Cc = X.lut + off + 2 + nt;
-            uint32_t a = 0, b = 0;
-            while (a < nt || b < nc) {
-                const uint32_t ta = a < nt ? __ldg(T + a) : 0xFFFFFFFFu;
-                const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
-                if (ta < cb) { ids[w++] = ta; ++a; }
-                else { if (pass[qb[k] + b]) ids[w++] = cb; ++b; }
-            }
-        }
-        o += cnt[k];
-    }
-    if (tile == gridDim.x - 1 && threadIdx.x == 0) {
-        const uint64_t nnz = s_prefix + block_total;
-        offsets[n] = (uint32_t)nnz;
-        status[0] = nnz;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -596,27 +853,36 @@ namespace {
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 struct Layout {
-    uint64_t hdr = 0, tiles = 0, entries = 0, qbase = 0, queue = 0, pass = 0, sorted = 0;
-    uint64_t pcount = 0, pstart = 0, cursor = 0, cstart = 0, total = 0;
-    uint64_t n_tiles = 0, queue_cap = 0;
+    uint64_t hdr = 0, chunks = 0, pcount = 0, zero_end = 0;
+    uint64_t entries = 0, tcount = 0, tprefix = 0;
+    uint64_t qbase = 0, queue = 0, pass = 0, sorted = 0, pstart = 0, cursor = 0, cstart = 0, total = 0;
+    uint64_t n_tiles = 0, n_chunks = 0, queue_cap = 0;
 };
 
-// scratch: [header 256 B: tile counter u32, queue_len u32, n_chunks u32]
-//          [tile states] [exact: per-polygon candidate counts] -- the part
-//          zeroed before every join -- then, exact mode only, the candidate
-//          queue and its polygon-grouped order
+// scratch: [header 256 B: scan chunk counter u32, queue_len u32, n_chunks u32,
+//           unused u32, FP64-fallback counter u64]
+//          [scan chunk states] [exact: per-polygon candidate counts]
+//          -- the part zeroed before every join --
+//          [entries u64 per point] [tile counts u32] [tile prefixes u32]
+//          then, exact mode only, the candidate queue and its polygon order
 Layout layout(const Index& X, uint64_t n) {
     Layout L;
     L.n_tiles = (n + kTile - 1) / kTile;
+    L.n_chunks = (L.n_tiles + 256 * kScanItems - 1) / (256 * kScanItems);
     uint64_t o = 256;
-    L.tiles = o;
-    o += align256(std::max<uint64_t>(L.n_tiles, 1) * 8);
+    L.chunks = o;
+    o += align256(std::max<uint64_t>(L.n_chunks, 1) * 8);
+    if (X.mode == AGJ_EXACT) {
+        L.pcount = o;
+        o += align256((uint64_t)X.n_polys * 4 + 4);
+    }
+    L.zero_end = o;
+    L.entries = o; o += align256(n * 8 + 8);
+    L.tcount = o; o += align256(L.n_tiles * 4 + 4);
+    L.tprefix = o; o += align256(L.n_tiles * 4 + 4);
     if (X.mode == AGJ_EXACT) {
         const uint64_t P = X.n_polys;
-        L.pcount = o; o += align256(P * 4 + 4);
-        L.hdr = o;   // end of the zeroed prefix
         L.queue_cap = n * std::max<uint64_t>(X.stats.max_cand_refs, 1);
-        L.entries = o; o += align256(n * 8);
         L.qbase = o; o += align256(n * 4);
         L.queue = o; o += align256(L.queue_cap * 8);
         L.pass = o; o += align256(L.queue_cap);
@@ -624,8 +890,6 @@ Layout layout(const Index& X, uint64_t n) {
         L.pstart = o; o += align256((P + 1) * 4);
         L.cursor = o; o += align256(P * 4 + 4);
         L.cstart = o; o += align256((P + 1) * 4);
-    } else {
-        L.hdr = o;
     }
     L.total = o;
     return L;
@@ -661,6 +925,7 @@ DevIndex make_dev_index(const Index& X) {
     D.n_polys = X.n_polys;
     D.max_depth = X.stats.max_depth;
     for (int f = 0; f < 6; ++f) D.faces[f] = DevFace{X.faces[f].root, X.faces[f].prefix_bits, X.faces[f].prefix};
+    D.model = X.model;
     return D;
 }
 
@@ -723,6 +988,7 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
     const Layout L = layout(X, n);
     agj_requirements req;
     join_requirements(X, n, &req);
+    if (req.ids_capacity >= 0xFFFFFFFFull) return AGJ_ECAPACITY;    // offsets are 32-bit: split the batch
     if (!out->scratch || out->scratch_bytes < L.total || out->ids_capacity < req.ids_capacity ||
         (req.ids_capacity && !out->ids) || (reinterpret_cast<uintptr_t>(out->scratch) & 255u) != 0)
         return AGJ_ECAPACITY;
@@ -730,10 +996,14 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
     const DevIndex D = make_dev_index(X);
     const double2* pts = reinterpret_cast<const double2*>(d_points);
     uint32_t* hdr = reinterpret_cast<uint32_t*>(sc);
-    uint64_t* tiles = reinterpret_cast<uint64_t*>(sc + L.tiles);
-    // zero the header + tile states (+ polygon counts) and the status words
-    const uint64_t zero_words = L.hdr / 8;
+    uint64_t* fallbacks = reinterpret_cast<uint64_t*>(sc) + 2;
+    uint64_t* chunks = reinterpret_cast<uint64_t*>(sc + L.chunks);
+    uint64_t* entries = reinterpret_cast<uint64_t*>(sc + L.entries);
+    uint32_t* tcount = reinterpret_cast<uint32_t*>(sc + L.tcount);
+    uint32_t* tprefix = reinterpret_cast<uint32_t*>(sc + L.tprefix);
+    // zero the header, the scan chunk states (and polygon counts) and the status words
     {
+        const uint64_t zero_words = L.zero_end / 8;
         const int grid = (int)std::min<uint64_t>((zero_words + 255) / 256 + 1, (uint64_t)sm_count() * 4);
         k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint64_t*>(sc), zero_words, out->status, 4);
     }
@@ -741,12 +1011,14 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
         cudaMemsetAsync(out->offsets, 0, 4, s);
         return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
     }
-    const unsigned grid = (unsigned)L.n_tiles;
+    const unsigned grid = (unsigned)((L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (X.mode == AGJ_APPROX) {
-        k_join_approx<kJoinBlock, kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, pts, (uint32_t)n, out->offsets, out->ids,
-                                                                      out->ids_capacity, tiles, hdr, out->status);
+        k_probe_approx<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, pts, (uint32_t)n, entries, tcount, out->status, fallbacks);
+        k_scan_counts<<<(unsigned)L.n_chunks, 256, 0, s>>>(tcount, L.n_tiles, tprefix, chunks, hdr, out->offsets,
+                                                           (uint32_t)n, out->status);
+        k_emit_approx<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, (uint32_t)n, entries, tprefix, out->offsets, out->ids,
+                                                            out->ids_capacity, out->status);
     } else {
-        uint64_t* entries = reinterpret_cast<uint64_t*>(sc + L.entries);
         uint32_t* qbase = reinterpret_cast<uint32_t*>(sc + L.qbase);
         uint2* queue = reinterpret_cast<uint2*>(sc + L.queue);
         uint8_t* pass = reinterpret_cast<uint8_t*>(sc + L.pass);
@@ -755,8 +1027,8 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
         uint32_t* pstart = reinterpret_cast<uint32_t*>(sc + L.pstart);
         uint32_t* cursor = reinterpret_cast<uint32_t*>(sc + L.cursor);
         uint32_t* cstart = reinterpret_cast<uint32_t*>(sc + L.cstart);
-        k_probe_exact<kJoinBlock, kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, pts, (uint32_t)n, entries, qbase, queue,
-                                                                      L.queue_cap, hdr + 1, pcount, out->status);
+        k_probe_exact<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, pts, (uint32_t)n, entries, qbase, queue, L.queue_cap,
+                                                            hdr + 1, pcount, out->status, fallbacks);
         if (X.n_polys) {
             k_poly_scan<<<1, 1024, 0, s>>>(pcount, X.n_polys, pstart, cursor, cstart, hdr + 2);
             const int sgrid = sm_count() * 4;
@@ -769,9 +1041,12 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
             }
             k_pip<<<sm_count() * 2, kPipBlock, smem, s>>>(D, pts, queue, sorted, pstart, cstart, hdr + 2, pass);
         }
-        k_csr_exact<kJoinBlock, kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, (uint32_t)n, entries, qbase, pass,
-                                                                     L.queue_cap, out->offsets, out->ids, out->ids_capacity, tiles,
-                                                                     hdr, out->status);
+        k_count_exact<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, (uint32_t)n, entries, qbase, pass, L.queue_cap, tcount,
+                                                            out->status);
+        k_scan_counts<<<(unsigned)L.n_chunks, 256, 0, s>>>(tcount, L.n_tiles, tprefix, chunks, hdr, out->offsets,
+                                                           (uint32_t)n, out->status);
+        k_emit_exact<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, (uint32_t)n, entries, qbase, pass, L.queue_cap, tprefix,
+                                                           out->offsets, out->ids, out->ids_capacity, out->status);
     }
     return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
@@ -781,15 +1056,17 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
 // ---------------------------------------------------------------------------
 // The one-pass approximate join needs work space for its tile scan: a
 // 256-byte header (the tile counter) and one 8-byte state per tile of
-// kTile points.  For callers that must not allocate, that work space is this
+// kNoAllocTile points.  For callers that must not allocate, that work space is this
 // file-scope device array, sized for joins of up to kNoAllocMaxPoints points
-// (16384 tiles, 128 KiB + 256 B).  Every device that loads the library holds
+// (131072 warp tiles of 128 points: 1 MiB + 256 B).  Every device that loads the library holds
 // one copy until the process exits.  All calls on a device share it, so
 // calls whose kernels overlap on the GPU race; the header and the tile
 // states a call uses are cleared at the start of every call.
 constexpr uint64_t kNoAllocMaxPoints = 1ull << 24;
 constexpr uint64_t kNoAllocHeaderWords = 32;
-constexpr uint64_t kNoAllocTiles = kNoAllocMaxPoints / kTile;
+constexpr int kNoAllocPPT = 4;
+constexpr uint64_t kNoAllocTile = 32 * kNoAllocPPT;
+constexpr uint64_t kNoAllocTiles = kNoAllocMaxPoints / kNoAllocTile;
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocHeaderWords + kNoAllocTiles];
 
 namespace {
@@ -830,7 +1107,7 @@ int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t 
     uint64_t* sc = nullptr;
     const int rc = noalloc_scratch(&sc);
     if (rc != AGJ_OK) return rc;
-    const uint64_t n_tiles = (n + kTile - 1) / kTile;
+    const uint64_t n_tiles = (n + kNoAllocTile - 1) / kNoAllocTile;
     const uint64_t zero_words = kNoAllocHeaderWords + n_tiles;
     {
         const int grid = (int)std::min<uint64_t>((zero_words + 255) / 256 + 1, (uint64_t)sm_count() * 4);
@@ -841,9 +1118,9 @@ int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t 
         return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
     }
     const DevIndex D = make_dev_index(X);
-    k_join_approx<kJoinBlock, kJoinPPT><<<(unsigned)n_tiles, kJoinBlock, 0, s>>>(
+    k_join_approx<kNoAllocPPT><<<(unsigned)((n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock), kJoinBlock, 0, s>>>(
         D, reinterpret_cast<const double2*>(d_points), (uint32_t)n, d_offsets, d_ids, ids_capacity,
-        sc + kNoAllocHeaderWords, reinterpret_cast<uint32_t*>(sc), d_status);
+        sc + kNoAllocHeaderWords, reinterpret_cast<uint32_t*>(sc), d_status, sc + 2);
     return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
 

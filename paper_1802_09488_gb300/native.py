@@ -38,14 +38,16 @@ class BuildOpts(C.Structure):
     _fields_ = [("max_cover_cells", C.c_uint32), ("max_cover_level", C.c_uint32),
                 ("max_interior_cells", C.c_uint32), ("max_interior_level", C.c_uint32),
                 ("memory_budget_bytes", C.c_uint64), ("train_latlng", C.c_void_p), ("n_train", C.c_uint64),
-                ("max_train_level", C.c_uint32), ("n_threads", C.c_uint32), ("host_only", C.c_uint32)]
+                ("max_train_level", C.c_uint32), ("n_threads", C.c_uint32), ("host_only", C.c_uint32),
+                ("no_fast_ids", C.c_uint32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("mode", C.c_uint32), ("n_polys", C.c_uint32), ("n_cells", C.c_uint64),
                 ("n_cand_cells", C.c_uint64), ("n_nodes", C.c_uint64), ("n_lut_words", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("max_refs", C.c_uint32), ("max_cand_refs", C.c_uint32),
-                ("max_depth", C.c_uint32), ("max_level", C.c_uint32), ("build_seconds", C.c_double)]
+                ("max_depth", C.c_uint32), ("max_level", C.c_uint32), ("build_seconds", C.c_double),
+                ("fast_ids", C.c_uint32), ("reserved", C.c_uint32), ("fast_err_cells", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +93,7 @@ def lib():
             "agj_join_host": (i32, [P, P, u64, P, P, P, P, u64, P, P]),
             "agj_cell_ids": (i32, [P, u64, P, P]),
             "agj_cell_ids_host": (i32, [P, u64, P]),
+            "agj_fast_ids_host": (i32, [P, P, u64, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -121,7 +124,7 @@ class Index:
 
     def __init__(self, polygons, mode: int = APPROX, precision_m: float = 10.0, train=None,
                  budget_bytes: int = 0, threads: int = 0, max_cover_cells: int = 0, max_interior_cells: int = 0,
-                 max_interior_level: int = 0, host_only: bool = False, stream=None):
+                 max_interior_level: int = 0, host_only: bool = False, fast_ids: bool = True, stream=None):
         L = lib()
         self._polys = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 2) for p in polygons]
         arr = (Polygon * max(len(self._polys), 1))()
@@ -135,6 +138,7 @@ class Index:
         opts.max_interior_cells = int(max_interior_cells)
         opts.max_interior_level = int(max_interior_level)
         opts.host_only = 1 if host_only else 0
+        opts.no_fast_ids = 0 if fast_ids else 1
         self._train = None
         if train is not None:
             self._train = np.ascontiguousarray(train, dtype=np.float64).reshape(-1, 2)
@@ -189,6 +193,16 @@ class Index:
         _check(lib().agj_index_trie(self._h, _np_ptr(nodes), _np_ptr(lut), _np_ptr(ft)), "agj_index_trie")
         return nodes[:st["n_nodes"] * 256], lut[:st["n_lut_words"]], ft
 
+    def fast_ids_host(self, points: np.ndarray):
+        """(ids u64, certified levels u8; 255 = outside the window) of the
+        certified fast cell-id step, computed on the host."""
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 2)
+        ids = np.zeros(len(pts), dtype=np.uint64)
+        lv = np.zeros(len(pts), dtype=np.uint8)
+        _check(lib().agj_fast_ids_host(self._h, _np_ptr(pts), len(pts), _np_ptr(ids), _np_ptr(lv)),
+               "agj_fast_ids_host")
+        return ids, lv
+
     def requirements(self, n: int) -> tuple[int, int]:
         r = Requirements()
         _check(lib().agj_join_requirements(self._h, int(n), C.byref(r)), "agj_join_requirements")
@@ -221,12 +235,21 @@ class Pairs:
         _check(lib().agj_join_check(C.byref(self.c), _stream_ptr(stream), C.byref(nnz)), "agj_join (device status)")
         return int(nnz.value)
 
+    def fallbacks(self) -> int:
+        """Points of the last join whose walk recomputed the FP64 cell id."""
+        return int(self.scratch[16:24].cpu().view(torch_int64()).item())
+
     def to_host(self, stream=None):
         """(offsets u32[n+1], ids u32[nnz]) as numpy, after a status check."""
         nnz = self.check(stream)
         off = self.offsets[: self.n + 1].cpu().numpy().view(np.uint32)
         ids = self.ids[:nnz].cpu().numpy().view(np.uint32)
         return off, ids
+
+
+def torch_int64():
+    import torch
+    return torch.int64
 
 
 def join(index: Index, points, pairs: Pairs | None = None, stream=None) -> Pairs:

@@ -1,0 +1,76 @@
+"""The certified fast cell-id step (FP32 model + error bound) on the host.
+
+The probe kernels compute leaf ids from an FP32 model of the spec's (s,t)
+with a bound on its error, and trust only the levels on which both ends of
+the error interval agree.  The host runs the same arithmetic
+(agj_fast_ids_host); these tests check it against the oracle's FP64 ids:
+every certified prefix equals the oracle's, points reported outside the
+model's window lie in no indexed cell, and almost all points certify the
+levels the trie walk needs."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def agj():
+    import paper_1802_09488_gb300 as m
+    m.lib()
+    return m
+
+
+def _prefix_equal(a, b, levels):
+    """Leading `levels` levels (3 face bits + 2 bits per level) equal."""
+    a = a.astype(np.uint64)
+    b = b.astype(np.uint64)
+    bits = (3 + 2 * levels.astype(np.uint64))
+    sh = (np.uint64(64) - bits)
+    mask = np.where(bits >= 64, np.uint64(0xFFFFFFFFFFFFFFFF),
+                    ~((np.uint64(1) << sh) - np.uint64(1)))
+    return (a & mask) == (b & mask)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_certified_prefix_equals_oracle(agj, oracle, which):
+    from paper_1802_09488_gb300 import synth
+    if which == "c1":
+        polys, box, eps = synth.c1_tiny(10).polygons, synth.BOX_C1, 10.0
+        pts = synth.points_uniform(400_000, box, seed=41)
+    else:
+        polys, box, eps = synth.c2_city_polygons(), synth.BOX_CITY, 4.0
+        pts = synth.points_mixture(400_000, box, seed=42, dist_seed=3)
+    ix = agj.Index(polys, agj.APPROX, eps, host_only=True)
+    st = ix.stats()
+    assert st["fast_ids"] == 1 and 0 < st["fast_err_cells"] < 0.05
+    # points of the workload, a wider ring around the box, and exact grid points
+    rng = np.random.default_rng(43)
+    lat_lo, lat_hi, lng_lo, lng_hi = box.latlng_bounds()
+    ring = np.stack([rng.uniform(lat_lo - 0.2, lat_hi + 0.2, 200_000), rng.uniform(lng_lo - 0.2, lng_hi + 0.2, 200_000)], -1)
+    grid = np.stack(np.meshgrid(np.linspace(lat_lo, lat_hi, 300), np.linspace(lng_lo, lng_hi, 300)), -1).reshape(-1, 2)
+    allp = np.concatenate([pts, ring, grid])
+    ids, lv = ix.fast_ids_host(allp)
+    ref = oracle.cell_ids(allp)
+    inside = lv != 255
+    assert _prefix_equal(ids[inside], ref[inside], lv[inside]).all()
+    # outside the window: no indexed cell holds the point
+    cells, _, _ = ix.logical()
+    for cid in ref[~inside][::50]:
+        assert oracle.logical_find(cells, int(cid)) == -1
+    # the walk needs at most level 24 here; nearly every point certifies it
+    frac = np.mean(lv[:len(pts)] >= 24)
+    assert frac > 0.995, frac
+
+
+def test_fast_model_disabled_option(agj):
+    from paper_1802_09488_gb300 import synth
+    ix = agj.Index(synth.c1_tiny(10).polygons, agj.APPROX, 10.0, host_only=True, fast_ids=False)
+    assert ix.stats()["fast_ids"] == 0
+    with pytest.raises(agj.AgjError):
+        ix.fast_ids_host(np.zeros((1, 2)))
+
+
+def test_fast_model_off_for_wide_windows(agj):
+    """Polygons spread over more than a degree: no model (FP64 ids)."""
+    polys = [np.array([[40.0, -74.0], [40.01, -74.0], [40.0, -73.99]]),
+             np.array([[42.5, -71.0], [42.51, -71.0], [42.5, -70.99]])]
+    ix = agj.Index(polys, agj.APPROX, 10.0, host_only=True)
+    assert ix.stats()["fast_ids"] == 0

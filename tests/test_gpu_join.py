@@ -176,3 +176,23 @@ def test_city_full_size_sampled(torch, agj, oracle):
             assert ids[off[r]:off[r + 1]].tolist() == ei[eo[k]:eo[k + 1]].tolist(), (mode, r)
         del pr, ix
         torch.cuda.empty_cache()
+
+
+def test_fast_ids_match_fp64_path(torch, agj, oracle):
+    """The certified FP32 id path and the FP64 id path give identical CSR on
+    the city mixture, and only a few points fall back to FP64."""
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c2_city_polygons()
+    pts = synth.points_mixture(3_000_000, synth.BOX_CITY, seed=44, dist_seed=3)
+    d = _dev(torch, pts)
+    for mode in (agj.APPROX, agj.EXACT):
+        fast = agj.Index(polys, mode, 4.0, train=pts[:30000] if mode == agj.EXACT else None)
+        slow = agj.Index(polys, mode, 4.0, train=pts[:30000] if mode == agj.EXACT else None, fast_ids=False)
+        assert fast.stats()["fast_ids"] == 1 and slow.stats()["fast_ids"] == 0
+        pf = agj.join(fast, d)
+        of, idf = pf.to_host()
+        assert pf.fallbacks() < 0.002 * len(pts)
+        ps_ = agj.join(slow, d)
+        os_, ids_ = ps_.to_host()
+        assert ps_.fallbacks() == 0
+        _csr_equal(of, idf, os_, ids_)
