@@ -32,7 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "points joined/sec at 1 GB300 (approx eps and exact) vs plain join; p50/p99 latency"
-LAUNCHES_PER_STEP = {"approx": 2, "exact": 6}   # k_zero + k_join_approx; k_zero + probe + scan + scatter + pip + csr
+# approx: k_zero, k_probe_approx, k_scan_counts, k_emit_approx
+# exact:  k_zero, k_probe_exact, k_poly_scan, k_scatter, k_pip, k_scan_counts, k_emit_exact
+LAUNCHES_PER_STEP = {"approx": 4, "exact": 7}
 
 
 def parse():
@@ -232,25 +234,40 @@ def main():
     gathers_per_pt = float(st_a[3]) / n
     cands_per_pt = float(st_e[2]) / n
     fallback_a, fallback_e = pa.fallbacks(), pe.fallbacks()
+    refine_fb = pe.refine_fallbacks()
 
     barrier()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.4)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def mk():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)          # creates the handle
+        return e
+
+    step_ev = [(mk(), mk()) for _ in range(args.steps)]
+    stage_ev = [([mk() for _ in range(4)], [mk() for _ in range(4)]) for _ in range(args.steps)]
     barrier()
     for k in range(args.steps):
-        ev[k][0].record(stream)
-        agj.join(ia, d_pts, pa)
-        ev[k][1].record(stream)
-        agj.join(ie, d_pts, pe)
-        ev[k][2].record(stream)
+        step_ev[k][0].record(stream)
+        agj.join_timed(ia, d_pts, pa, stage_ev[k][0])
+        agj.join_timed(ie, d_pts, pe, stage_ev[k][1])
+        step_ev[k][1].record(stream)
     barrier()
     clk = clocks.stop()
-    approx_ms = [a.elapsed_time(b) for a, b, _ in ev]
-    exact_ms = [b.elapsed_time(c) for _, b, c in ev]
-    total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    approx_ms = [ev[0][0].elapsed_time(ev[0][3]) for ev in stage_ev]
+    exact_ms = [ev[1][0].elapsed_time(ev[1][3]) for ev in stage_ev]
+    stages = {
+        "approx": {"k_probe_approx": [ev[0][0].elapsed_time(ev[0][1]) for ev in stage_ev],
+                   "k_scan_counts": [ev[0][1].elapsed_time(ev[0][2]) for ev in stage_ev],
+                   "k_emit_approx": [ev[0][2].elapsed_time(ev[0][3]) for ev in stage_ev]},
+        "exact": {"k_probe_exact": [ev[1][0].elapsed_time(ev[1][1]) for ev in stage_ev],
+                  "refine (k_poly_scan + k_scatter + k_pip)": [ev[1][1].elapsed_time(ev[1][2]) for ev in stage_ev],
+                  "csr (k_scan_counts + k_emit_exact)": [ev[1][2].elapsed_time(ev[1][3]) for ev in stage_ev]},
+    }
+    total_ms = step_ev[0][0].elapsed_time(step_ev[-1][1])
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -261,14 +278,23 @@ def main():
     value = world * 2.0 * n * args.steps / (total_ms / 1000.0)
     peaks = measured_peaks()
     k_pts = nnz_a / n
-    bytes_per_pt = 16 + 8 * gathers_per_pt + 4 + 4 * k_pts
-    t_approx_s = statistics.mean(approx_ms) / 1000.0
-    achieved = bytes_per_pt * n / t_approx_s / 1e9
-    roofline = {"kernel": "k_join_approx", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peaks["source"],
-                "algorithmic_bytes_per_point": bytes_per_pt,
-                "note": "bytes = 16 (point) + 8 x trie entries read + 4 (offset) + 4 x pairs, per point"}
+    mean = statistics.mean
+
+    def roof(kernel, bytes_per_pt, ms, note):
+        achieved = bytes_per_pt * n / (ms / 1000.0) / 1e9
+        return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                "algorithmic_bytes_per_point": bytes_per_pt, "ms_per_launch": ms, "note": note}
+
+    t_pa = mean(stages["approx"]["k_probe_approx"])
+    t_pe = mean(stages["exact"]["k_probe_exact"])
+    r_pa = roof("k_probe_approx", 16 + 8 * gathers_per_pt + 8, t_pa,
+                "16 B point + 8 B per trie entry read + 8 B entry written, per point")
+    r_pe = roof("k_probe_exact", 16 + 8 * gathers_per_pt + 8 + 12 * cands_per_pt, t_pe,
+                "16 B point + 8 B per trie entry read + 8 B entry + 12 B per candidate queued, per point")
+    roofline = r_pa if t_pa >= t_pe else r_pe
+    join_roof = roof("approx join (probe + scan + emit)", 16 + 8 * gathers_per_pt + 4 + 4 * k_pts, mean(approx_ms),
+                     "the method's bytes: 16 B point + 8 B per trie entry + 4 B offset + 4 B per pair")
 
     def pct(v, q):
         s = sorted(v)
@@ -287,10 +313,13 @@ def main():
                        "fp64_id_fallbacks": fallback_a},
             "exact": {"points_per_s": n / (statistics.mean(exact_ms) / 1000.0), "p50_ms": pct(exact_ms, 50),
                       "p99_ms": pct(exact_ms, 99), "nnz": nnz_e, "candidates_per_point": cands_per_pt,
-                      "fp64_id_fallbacks": fallback_e},
+                      "fp64_id_fallbacks": fallback_e, "fp64_refine_fallbacks": refine_fb},
         },
         "index": {"approx": ia.stats(), "exact": ie.stats(), "build_s": build_s},
+        "stage_ms": {m: {k: mean(v) for k, v in d.items()} for m, d in stages.items()},
         "roofline": roofline,
+        "roofline_other_probe": r_pe if roofline is r_pa else r_pa,
+        "roofline_approx_join": join_roof,
         "clocks": clk,
         "gpu_launches": args.steps * (LAUNCHES_PER_STEP["approx"] + LAUNCHES_PER_STEP["exact"]),
     }

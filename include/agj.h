@@ -195,7 +195,9 @@ typedef struct {
     uint64_t  ids_capacity;
     void*     scratch;        /* scratch_bytes, 256-byte aligned; after a join its
                                  bytes 16..23 hold the number of points whose
-                                 walk recomputed the FP64 cell id (diagnostic) */
+                                 walk recomputed the FP64 cell id and bytes
+                                 24..31 the number of candidates whose refine
+                                 test fell back to FP64 (diagnostics) */
     uint64_t  scratch_bytes;
     uint64_t* status;         /* 4 x uint64 device words: [0] nnz, [1] error flags,
                                  [2] candidate pairs refined (exact mode),
@@ -262,6 +264,19 @@ int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* s
 int agj_join_approx_noalloc(const agj_index* index, const double* d_points, uint64_t n, uint32_t* d_offsets,
                             uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, void* stream);
 
+/*
+ * agj_join that also records four caller-created CUDA events (cudaEvent_t
+ * passed as void*) on `stream` at its stage boundaries, for timing the
+ * kernels with cudaEventElapsedTime:
+ *   approx: [0] before the probe kernel, [1] after it, [2] after the scan of
+ *           the tile counts, [3] after the emit kernel;
+ *   exact:  [0] before the probe kernel, [1] after it, [2] after the refine
+ *           (grouping + PIP), [3] after the scan and emit kernels.
+ * n == 0 records all four events back to back.
+ */
+int agj_join_timed(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out,
+                   void* const events[4]);
+
 /* Synchronises `stream`, reads out->status and returns AGJ_OK, or the first
  * device-side error as a status code; *nnz receives the pair count. */
 int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz);
@@ -293,6 +308,15 @@ int agj_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, void* stre
  */
 int agj_fast_ids_host(const agj_index* index, const double* h_points, uint64_t n, uint64_t* h_ids,
                       uint8_t* h_levels);
+
+/*
+ * The certified FP32 refine test on the host, with the same model and
+ * arithmetic the PIP kernel uses: for point k and polygon h_polys[k],
+ * h_out[k] = 1 (covered), 0 (not covered) or -1 (undecided: the kernel then
+ * recomputes the test in FP64).  Host only.
+ */
+int agj_covers_certified_host(const agj_index* index, const double* h_points, const uint32_t* h_polys, uint64_t n,
+                              int8_t* h_out);
 
 /* Cell ids of points on the host with the same spec (host code). */
 int agj_cell_ids_host(const double* h_points, uint64_t n, uint64_t* h_ids);

@@ -201,6 +201,17 @@ int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* s
     return agj::launch_join(index->X, d_points, n, as_stream(stream), out);
 }
 
+int agj_join_timed(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out,
+                   void* const events[4]) {
+    if (!index || !index->X.d_blob || !events) return AGJ_EINVAL;
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) {
+        if (!events[k]) return AGJ_EINVAL;
+        ev[k] = static_cast<cudaEvent_t>(events[k]);
+    }
+    return agj::launch_join(index->X, d_points, n, as_stream(stream), out, ev);
+}
+
 int agj_join_approx_noalloc(const agj_index* index, const double* d_points, uint64_t n, uint32_t* d_offsets,
                             uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, void* stream) {
     if (!index) return AGJ_EINVAL;
@@ -266,6 +277,24 @@ int agj_fast_ids_host(const agj_index* index, const double* h_points, uint64_t n
         }
         h_ids[k] = agj::cell_id_lut(lut, M.face, i, j);
         h_levels[k] = (uint8_t)lc;
+    }
+    return AGJ_OK;
+}
+
+int agj_covers_certified_host(const agj_index* index, const double* h_points, const uint32_t* h_polys, uint64_t n,
+                              int8_t* h_out) {
+    if (!index || (n && (!h_points || !h_polys || !h_out))) return AGJ_EINVAL;
+    const agj::Index& X = index->X;
+    for (uint64_t k = 0; k < n; ++k) {
+        const uint32_t poly = h_polys[k];
+        if (poly >= X.n_polys) return AGJ_EINVAL;
+        const agj::PolyLocal& L = X.poly_local[poly];
+        const uint32_t v0 = X.poly_off[poly], V = X.poly_off[poly + 1] - v0;
+        float pu, pv, dp;
+        int r = -1;
+        if (L.ok && agj::model_uv_local(X.model, h_points[2 * k], h_points[2 * k + 1], L, &pu, &pv, &dp))
+            r = agj::covers_certified(X.poly_luv.data() + v0, V, L, pu, pv, dp);
+        h_out[k] = (int8_t)r;
     }
     return AGJ_OK;
 }

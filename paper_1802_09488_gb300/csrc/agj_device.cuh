@@ -25,6 +25,8 @@ struct DevIndex {
     const uint32_t* poly_off;   // n_polys + 1
     const int64_t* poly_bbox;   // 4 keys per polygon: umin umax vmin vmax
     const int8_t* poly_face;
+    const PolyLocal* poly_local;  // certified refine: per-polygon reference, bound, bbox
+    const F2* poly_luv;           // certified refine: FP32 local vertex coordinates
     uint64_t n_nodes;
     uint64_t n_lut;
     uint32_t n_polys;

@@ -253,6 +253,13 @@ struct FastModel {
     float sa_hi, sa_lo, sb_hi, sb_lo;   // scales of the offsets' two parts (powers of two)
     float xl[4], yl[4];             // first order: c10 hi, c10 lo, c01 hi, c01 lo
     float xh[kFastHiTerms], yh[kFastHiTerms];     // degrees 2..5 (layout in model_eval)
+    // the same kind of model for U = 2^30 u and V = 2^30 v (the refine step)
+    int32_t uv_enabled;
+    int32_t n0u, n0v;
+    float f0u, f0v;
+    float err_uv;                   // bound on |model - 2^30 (u,v)|, same units
+    float ul[4], vl[4];
+    float uh[kFastHiTerms], vh[kFastHiTerms];
 };
 
 AGJ_HD int64_t double_bits(double x) {
@@ -483,6 +490,84 @@ AGJ_HD uint64_t key_bytes_lut(const uint16_t* lut, int face, uint32_t i, uint32_
 AGJ_HD uint64_t cell_id_lut(const uint16_t* lut, int face, uint32_t i, uint32_t j) {
     const uint64_t key = key_bytes_lut(lut, face, i, j);
     return ((uint64_t)face << 61) | ((key >> 4) << 1) | 1ull;
+}
+
+// ---------------------------------------------------------------------------
+// Certified ST_Covers in FP32 (the refine step)
+// ---------------------------------------------------------------------------
+// Coordinates are 2^30 (u, v) measured from a per-polygon integer reference
+// point, held in FP32: a vertex's local coordinates carry a rounding error of
+// at most PolyLocal::dv, a point's (from the U/V model) at most dp.  The ring
+// rule of the spec is decided from them only where the decision is certain:
+// every vertex v-comparison with the point must be farther apart than the
+// summed errors, and on every edge that straddles the point the orientation
+// must exceed its forward error bound (input errors times the other factors,
+// plus FP32 rounding of the products and the difference).  Then the spec's
+// FP64 orientation has the same sign and is not zero, so the crossing count
+// and the "on an edge" outcome are the spec's.  Anything closer returns -1
+// and the caller recomputes the point's (u, v) and the test in FP64.
+
+struct F2 {
+    float x, y;
+};
+
+struct PolyLocal {
+    int32_t ru, rv;                 // reference point, units of 2^-30 in (u, v)
+    float dv;                       // bound on the rounding of any local vertex coordinate
+    float bu0, bu1, bv0, bv1;       // local bbox (rounded values of the exact bbox)
+    int32_t ok;                     // 0: polygon too large for 24-bit local coordinates
+};
+
+AGJ_HD float fabs_f(float x) { return x < 0.0f ? -x : x; }
+
+// 1 covered, 0 not covered, -1 undecided.  verts: the ring's local
+// coordinates (implicitly closed).
+AGJ_HD int covers_certified(const F2* verts, uint32_t nv, const PolyLocal& P, float pu, float pv, float dp) {
+    const float D = (dp + P.dv) * 1.000001f;
+    if (pu < P.bu0 - D || pu > P.bu1 + D || pv < P.bv0 - D || pv > P.bv1 + D) return 0;
+    if (!(pu > P.bu0 + D && pu < P.bu1 - D && pv > P.bv0 + D && pv < P.bv1 - D)) return -1;
+    const float ev = 2.0f * P.dv, ep = dp + P.dv;
+    F2 A = verts[0];
+    float dA = pv - A.y;
+    if (fabs_f(dA) <= D) return -1;
+    int inside = 0;
+    for (uint32_t k = 0; k < nv; ++k) {
+        const F2 B = verts[k + 1 == nv ? 0 : k + 1];
+        const float dB = pv - B.y;
+        if (fabs_f(dB) <= D) return -1;
+        if ((dA > 0.0f) != (dB > 0.0f)) {
+            const float d1 = B.x - A.x, d3 = B.y - A.y, d4 = pu - A.x;
+            const float t1 = d1 * dA, t2 = d3 * d4;
+            const float o = t1 - t2;
+            const float e1 = ev + fabs_f(d1) * 6.0e-8f, e3 = ev + fabs_f(d3) * 6.0e-8f;
+            const float e2 = ep + fabs_f(dA) * 6.0e-8f, e4 = ep + fabs_f(d4) * 6.0e-8f;
+            const float bound = (fabs_f(d1) * e2 + fabs_f(dA) * e1 + e1 * e2 + fabs_f(d3) * e4 + fabs_f(d4) * e3 +
+                                 e3 * e4 + (fabs_f(t1) + fabs_f(t2)) * 2.4e-7f) * 1.0001f;
+            if (fabs_f(o) <= bound) return -1;
+            // upward edge (a.v < p.v < b.v) crosses when o > 0, downward when o < 0
+            if ((dA > 0.0f) == (o > 0.0f)) inside ^= 1;
+        }
+        A = B;
+        dA = dB;
+    }
+    return inside;
+}
+
+// The point's local (u, v) from the U/V model, with its error bound.
+// Returns false when the point is outside the model window.
+AGJ_HD bool model_uv_local(const FastModel& M, double lat, double lng, const PolyLocal& P, float* pu, float* pv,
+                           float* dp) {
+    float ah, al, bh, bl;
+    if (!M.uv_enabled || !model_offsets(M, double_bits(lat), double_bits(lng), &ah, &al, &bh, &bl)) return false;
+    float uth, utl, vth, vtl;
+    model_eval(M.ul, M.uh, M.f0u, ah, al, bh, bl, &uth, &utl);
+    model_eval(M.vl, M.vh, M.f0v, ah, al, bh, bl, &vth, &vtl);
+    const float xu = ((float)(M.n0u - P.ru) + uth) + utl;
+    const float xv = ((float)(M.n0v - P.rv) + vth) + vtl;
+    *pu = xu;
+    *pv = xv;
+    *dp = M.err_uv + (fabs_f(xu) + fabs_f(xv)) * 2.4e-7f + 1e-5f;
+    return true;
 }
 
 }  // namespace agj

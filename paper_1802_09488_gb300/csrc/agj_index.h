@@ -58,12 +58,14 @@ struct Index {
     std::vector<double> poly_bbox;    // 4 per polygon: umin umax vmin vmax
     std::vector<int8_t> poly_face;
     FastModel model{};                // certified fast cell ids (disabled: all zero)
+    std::vector<PolyLocal> poly_local;   // per polygon: reference point, rounding bound, bbox
+    std::vector<F2> poly_luv;            // per vertex: FP32 local coordinates
     agj_stats stats{};
     // device copies (owned)
     void* d_blob = nullptr;
     uint64_t blob_bytes = 0;
     uint64_t off_nodes = 0, off_lut = 0, off_uv = 0, off_vkey = 0, off_ukey = 0, off_poff = 0, off_bbox = 0,
-             off_face = 0;
+             off_face = 0, off_plocal = 0, off_pluv = 0;
     int device = 0;
 };
 
@@ -87,6 +89,9 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
 // Fits idx->model (the certified fast cell-id model) for the index's cells;
 // leaves it disabled when the cells span faces or too wide a window.
 void fit_fast_model(Index* idx, unsigned threads);
+
+// Local FP32 coordinates of every polygon for the certified refine step.
+void prepare_poly_local(Index* idx);
 
 // The super-covering merge on given (cell, reference) pairs, in order.
 void supercover(const uint64_t* cells, const uint32_t* refs, uint64_t n, std::vector<uint64_t>* out_cells,

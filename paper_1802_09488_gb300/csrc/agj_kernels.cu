@@ -16,8 +16,8 @@
 //   k_scatter        queue grouped by polygon
 //   k_pip            exact ST_Covers refine (§II "PIP"): one CTA per chunk of
 //                    one polygon's candidates, the polygon's edges staged in
-//                    shared memory and read by all threads (broadcast)
-//   k_count_exact    per-tile pair counts (true hits + passing candidates)
+//                    shared memory and read by all threads (broadcast); adds
+//                    passing candidates to their tile's pair count
 //   k_emit_exact     offsets and ids of the exact join
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -157,6 +157,7 @@ __device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* fac
     uint32_t i, j;
     int lc, face;
     w.st = 0;
+    w.b = 0;
     if (!exact && X.model.enabled) {
         if (!model_ij(X.model, lat, lng, &i, &j, &lc)) return;       // outside the window: in no cell
         face = X.model.face;
@@ -204,8 +205,13 @@ __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFac
     for (int k = 0; k < PPT; ++k) {
         e[k] = 0;
         w[k].st = 0;
+        w[k].b = 0;
         if (valid[k]) begin_walk(X, faces, lut, lat[k], lng[k], false, w[k]);
     }
+    uint32_t prefix_bytes[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) prefix_bytes[k] = w[k].b;
+    const uint32_t n_nodes32 = (uint32_t)min(X.n_nodes, (uint64_t)0xFFFFFFFFu);
 #pragma unroll 1
     for (int d = 0; d < 8; ++d) {
         uint64_t v[PPT];
@@ -227,20 +233,24 @@ __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFac
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             if (w[k].st != 1) continue;
-            ++gathers;
+            // child entries hold node << 11 with node < 2^32, so the low 32 bits
+            // of (v >> 11) name the node; checking them keeps every read in bounds
+            const uint32_t child = (uint32_t)(v[k] >> 11);
             if ((v[k] & 3ull) != 0ull || v[k] == 0ull) {
                 e[k] = v[k];
                 w[k].st = 0;
-            } else if ((v[k] >> 11) >= X.n_nodes) {
+            } else if (child >= n_nodes32) {
                 atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
                 w[k].st = 0;
             } else {
-                w[k].node = (uint32_t)(v[k] >> 11);
+                w[k].node = child;
                 any = true;
             }
         }
         if (!any) break;
     }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) gathers += w[k].b - prefix_bytes[k];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (w[k].st == 1) {
@@ -429,6 +439,7 @@ __global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS) k_probe_exac
                                                             uint2* __restrict__ queue, uint64_t queue_cap,
                                                             uint32_t* __restrict__ queue_len,
                                                             uint32_t* __restrict__ poly_count,
+                                                            uint32_t* __restrict__ tile_count,
                                                             uint64_t* __restrict__ status,
                                                             uint64_t* __restrict__ fallback_counter) {
     __shared__ __align__(16) uint16_t s_hlut[1024];
@@ -453,14 +464,20 @@ __global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS) k_probe_exac
     uint32_t fallbacks = 0;
     warp_count(probe_points<PPT>(X, s_faces, s_hlut, s_root, lat, lng, valid, e, &status[1], &fallbacks), &status[3]);
     warp_count(fallbacks, fallback_counter);
-    uint32_t nc[PPT], csum = 0;
+    uint32_t nc[PPT], csum = 0, tsum = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         uint32_t nt;
         entry_counts(X, e[k], &nt, &nc[k]);
         csum += nc[k];
+        tsum += nt;
         if (valid[k]) entries[base + lane + 32 * k] = e[k];
     }
+    // the tile's pair count starts at its true hits; the refine kernel adds the
+    // candidates that pass
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(kFull, tsum, o);
+    if (lane == 0) tile_count[base / (32 * PPT)] = tsum;
     const uint32_t x = warp_incl_scan(csum);
     const uint32_t wtotal = __shfl_sync(kFull, x, 31);
     if (wtotal == 0) return;
@@ -642,30 +659,6 @@ __device__ __forceinline__ uint32_t exact_count(const DevIndex& X, uint64_t e, c
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(kJoinBlock) k_count_exact(DevIndex X, uint32_t n, const uint64_t* __restrict__ entries,
-                                                            const uint32_t* __restrict__ qbase,
-                                                            const uint8_t* __restrict__ pass, uint64_t queue_cap,
-                                                            uint32_t* __restrict__ tile_count,
-                                                            uint64_t* __restrict__ status) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const uint64_t base = wt * (32 * PPT);
-    if (base >= n) return;
-    uint32_t c = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const uint64_t p = base + lane + 32 * k;
-        if (p >= n) continue;
-        uint32_t qb;
-        const uint32_t x = exact_count(X, entries[p], qbase, p, pass, queue_cap, &qb, status);
-        c += x == 0xFFFFFFFFu ? 0u : x;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
-    if (lane == 0) tile_count[wt] = c;
-}
-
-template <int PPT>
 __global__ void __launch_bounds__(kJoinBlock) k_emit_exact(DevIndex X, uint32_t n, const uint64_t* __restrict__ entries,
                                                            const uint32_t* __restrict__ qbase,
                                                            const uint8_t* __restrict__ pass, uint64_t queue_cap,
@@ -756,33 +749,93 @@ __global__ void __launch_bounds__(1024) k_poly_scan(const uint32_t* __restrict__
     }
 }
 
-__global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ queue_len,
-                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted, uint64_t queue_cap) {
+// Groups the candidate queue by polygon (counting-sort scatter).  Each CTA
+// takes chunks of kScatterChunk queue items, counts them per polygon with
+// shared-memory atomics, reserves each polygon's slots with one global atomic
+// per polygon and chunk, and writes the items' queue indices there.  With more
+// polygons than shared counters, every item reserves its slot globally.
+constexpr int kScatterChunk = 4096;
+constexpr int kScatterMaxPolys = 4096;
+__global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ queue_len,
+                                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted,
+                                                 uint64_t queue_cap, uint32_t n_polys) {
+    __shared__ uint32_t s_cnt[kScatterMaxPolys];
+    __shared__ uint32_t s_base[kScatterMaxPolys];
     const uint64_t len = min((uint64_t)*queue_len, queue_cap);
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < len; q += stride) {
-        const uint32_t pos = atomicAdd(&cursor[queue[q].y], 1u);
-        sorted[pos] = (uint32_t)q;
+    if (n_polys > (uint32_t)kScatterMaxPolys) {
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < len; q += stride) {
+            const uint32_t pos = atomicAdd(&cursor[queue[q].y], 1u);
+            sorted[pos] = (uint32_t)q;
+        }
+        return;
+    }
+    for (uint64_t c0 = (uint64_t)blockIdx.x * kScatterChunk; c0 < len; c0 += (uint64_t)gridDim.x * kScatterChunk) {
+        const uint64_t c1 = min(c0 + kScatterChunk, len);
+        for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) s_cnt[p] = 0;
+        __syncthreads();
+        for (uint64_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) atomicAdd(&s_cnt[queue[q].y], 1u);
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) {
+            const uint32_t c = s_cnt[p];
+            if (c) s_base[p] = atomicAdd(&cursor[p], c);
+            s_cnt[p] = 0;
+        }
+        __syncthreads();
+        for (uint64_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+            const uint32_t poly = queue[q].y;
+            sorted[s_base[poly] + atomicAdd(&s_cnt[poly], 1u)] = (uint32_t)q;
+        }
+        __syncthreads();
     }
 }
 
-// Refine: ST_Covers of (point, polygon) candidates, grouped by polygon.
-// Per chunk the polygon's vertices (u,v), and the integer keys of their u
-// and v, are staged in shared memory; every thread tests its candidate
-// against the same edge at the same time (shared-memory broadcast).  Edges
-// whose v-range misses the point are skipped with integer compares; only
-// edges straddling the point's v use FP64 (the orientation of the ring rule).
+// ST_Covers in FP64 exactly as the spec (the certified test's fallback):
+// same face, closed (u,v) bbox, ring rule with integer keys for the range
+// tests and FP64 orientation, vertices read from global memory.
+__device__ bool covers_fp64(const DevIndex& X, uint32_t poly, double lat, double lng) {
+    if (!point_valid(lat, lng)) return false;
+    double pu, pv;
+    const int f = face_uv(lat, lng, &pu, &pv);
+    if (f != X.poly_face[poly]) return false;
+    const int64_t puk = dkey(pu), pvk = dkey(pv);
+    const int64_t* bb = X.poly_bbox + 4ull * poly;
+    if (!(puk >= bb[0] && puk <= bb[1] && pvk >= bb[2] && pvk <= bb[3])) return false;
+    const uint32_t v0 = X.poly_off[poly], V = X.poly_off[poly + 1] - v0;
+    bool inside = false;
+    for (uint32_t k = 0; k < V; ++k) {
+        const uint32_t a = v0 + k, b = v0 + (k + 1 == V ? 0u : k + 1);
+        const int64_t av = X.poly_vkey[a], bv = X.poly_vkey[b];
+        const int64_t vlo = av < bv ? av : bv, vhi = av < bv ? bv : av;
+        if (pvk < vlo || pvk > vhi) continue;
+        const double2 A = X.poly_uv[a], B = X.poly_uv[b];
+        const double o = (B.x - A.x) * (pv - A.y) - (B.y - A.y) * (pu - A.x);
+        if (o == 0.0) {
+            const int64_t au = X.poly_ukey[a], bu = X.poly_ukey[b];
+            if (puk >= (au < bu ? au : bu) && puk <= (au < bu ? bu : au)) return true;
+        }
+        if ((av <= pvk && pvk < bv && o > 0.0) || (bv <= pvk && pvk < av && o < 0.0)) inside = !inside;
+    }
+    return inside;
+}
+
+// Refine: ST_Covers of (point, polygon) candidates, grouped by polygon.  Per
+// chunk of one polygon's candidates, the polygon's FP32 local vertices are
+// staged in shared memory and every thread tests its candidate against the
+// same edge at the same time (shared-memory broadcast).  The test is the
+// certified FP32 one (covers_certified); an undecided candidate (within the
+// error bounds of a vertex or an edge) is recomputed in FP64 (covers_fp64),
+// as is every candidate of a polygon too large for the FP32 local frame.
 __global__ void __launch_bounds__(kPipBlock) k_pip(DevIndex X, const double2* __restrict__ pts,
                                                    const uint2* __restrict__ queue, const uint32_t* __restrict__ sorted,
                                                    const uint32_t* __restrict__ poly_start,
                                                    const uint32_t* __restrict__ chunk_start,
-                                                   const uint32_t* __restrict__ n_chunks, uint8_t* __restrict__ pass) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    double2* s_uv = reinterpret_cast<double2*>(smem);
-    int64_t* s_vk = reinterpret_cast<int64_t*>(smem + sizeof(double2) * (kPipSmemVerts + 1));
-    int64_t* s_uk = s_vk + (kPipSmemVerts + 1);
+                                                   const uint32_t* __restrict__ n_chunks, uint8_t* __restrict__ pass,
+                                                   uint32_t* __restrict__ tile_count, uint64_t* __restrict__ undecided) {
+    __shared__ F2 s_lv[kPipSmemVerts];
     const uint32_t total = *n_chunks;
     const uint32_t P = X.n_polys;
+    uint32_t n_undecided = 0;
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         // polygon of chunk c: last poly with chunk_start <= c
         uint32_t lo = 0, hi = P;
@@ -794,54 +847,30 @@ __global__ void __launch_bounds__(kPipBlock) k_pip(DevIndex X, const double2* __
         const uint32_t q0 = poly_start[poly] + (c - chunk_start[poly]) * kPipBlock;
         const uint32_t q1 = min(q0 + kPipBlock, poly_start[poly + 1]);
         const uint32_t item = q0 + threadIdx.x;
-        const bool have = item < q1;
-        uint32_t qi = 0;
-        double pu = 0, pv = 0;
-        int64_t puk = 0, pvk = 0;
-        bool alive = false;
         const uint32_t v0 = X.poly_off[poly], V = X.poly_off[poly + 1] - v0;
-        if (have) {
-            qi = sorted[item];
+        const PolyLocal L = X.poly_local[poly];
+        const bool certified = X.model.uv_enabled && L.ok && V <= (uint32_t)kPipSmemVerts;
+        __syncthreads();
+        if (certified)
+            for (uint32_t t = threadIdx.x; t < V; t += blockDim.x) s_lv[t] = X.poly_luv[v0 + t];
+        __syncthreads();
+        if (item < q1) {
+            const uint32_t qi = sorted[item];
             const uint2 qp = queue[qi];
             const double2 pt = pts[qp.x];
-            if (point_valid(pt.x, pt.y)) {
-                const int f = face_uv(pt.x, pt.y, &pu, &pv);
-                puk = dkey(pu);
-                pvk = dkey(pv);
-                const int64_t* bb = X.poly_bbox + 4ull * poly;
-                alive = f == X.poly_face[poly] && puk >= bb[0] && puk <= bb[1] && pvk >= bb[2] && pvk <= bb[3];
+            int r = -1;
+            float pu, pv, dp;
+            if (certified && model_uv_local(X.model, pt.x, pt.y, L, &pu, &pv, &dp))
+                r = covers_certified(s_lv, V, L, pu, pv, dp);
+            if (r < 0) {
+                r = covers_fp64(X, poly, pt.x, pt.y) ? 1 : 0;
+                ++n_undecided;
             }
+            pass[qi] = (uint8_t)r;
+            if (r) atomicAdd(&tile_count[qp.x / kTile], 1u);
         }
-        bool inside = false, on_edge = false;
-        for (uint32_t s = 0; s < V; s += kPipSmemVerts) {
-            const uint32_t m = min((uint32_t)kPipSmemVerts, V - s);   // edges s .. s+m-1
-            __syncthreads();
-            for (uint32_t t = threadIdx.x; t <= m; t += blockDim.x) {
-                const uint32_t g = v0 + ((s + t) == V ? 0u : (s + t));
-                s_uv[t] = X.poly_uv[g];
-                s_vk[t] = X.poly_vkey[g];
-                s_uk[t] = X.poly_ukey[g];
-            }
-            __syncthreads();
-            if (__syncthreads_or(alive)) {
-                if (alive) {
-                    for (uint32_t k = 0; k < m; ++k) {
-                        const int64_t av = s_vk[k], bv = s_vk[k + 1];
-                        const int64_t vlo = av < bv ? av : bv, vhi = av < bv ? bv : av;
-                        if (pvk < vlo || pvk > vhi) continue;
-                        const double2 A = s_uv[k], B = s_uv[k + 1];
-                        const double o = (B.x - A.x) * (pv - A.y) - (B.y - A.y) * (pu - A.x);
-                        if (o == 0.0) {
-                            const int64_t au = s_uk[k], bu = s_uk[k + 1];
-                            if (puk >= (au < bu ? au : bu) && puk <= (au < bu ? bu : au)) on_edge = true;
-                        }
-                        if ((av <= pvk && pvk < bv && o > 0.0) || (bv <= pvk && pvk < av && o < 0.0)) inside = !inside;
-                    }
-                }
-            }
-        }
-        if (have) pass[qi] = (uint8_t)(alive && (on_edge || inside));
     }
+    warp_count(n_undecided, undecided);
 }
 
 // ---------------------------------------------------------------------------
@@ -860,7 +889,7 @@ struct Layout {
 };
 
 // scratch: [header 256 B: scan chunk counter u32, queue_len u32, n_chunks u32,
-//           unused u32, FP64-fallback counter u64]
+//           unused u32, FP64 cell-id fallbacks u64, FP64 refine fallbacks u64]
 //          [scan chunk states] [exact: per-polygon candidate counts]
 //          -- the part zeroed before every join --
 //          [entries u64 per point] [tile counts u32] [tile prefixes u32]
@@ -920,6 +949,8 @@ DevIndex make_dev_index(const Index& X) {
     D.poly_off = reinterpret_cast<const uint32_t*>(b + X.off_poff);
     D.poly_bbox = reinterpret_cast<const int64_t*>(b + X.off_bbox);
     D.poly_face = reinterpret_cast<const int8_t*>(b + X.off_face);
+    D.poly_local = reinterpret_cast<const PolyLocal*>(b + X.off_plocal);
+    D.poly_luv = reinterpret_cast<const F2*>(b + X.off_pluv);
     D.n_nodes = X.nodes.size() / 256;
     D.n_lut = X.lut.size();
     D.n_polys = X.n_polys;
@@ -940,6 +971,8 @@ int upload_index(Index* X, cudaStream_t s) {
     X->off_poff = o; o += align256(X->poly_off.size() * 4 + 4);
     X->off_bbox = o; o += align256((uint64_t)X->n_polys * 32 + 32);
     X->off_face = o; o += align256((uint64_t)X->n_polys + 1);
+    X->off_plocal = o; o += align256((uint64_t)X->n_polys * sizeof(PolyLocal) + 16);
+    X->off_pluv = o; o += align256(nv * sizeof(F2) + 16);
     X->blob_bytes = o;
     std::vector<unsigned char> host(o, 0);
     auto put = [&](uint64_t off, const void* src, size_t bytes) {
@@ -959,6 +992,8 @@ int upload_index(Index* X, cudaStream_t s) {
     put(X->off_poff, X->poly_off.data(), X->poly_off.size() * 4);
     put(X->off_bbox, bb.data(), bb.size() * 8);
     put(X->off_face, X->poly_face.data(), X->poly_face.size());
+    put(X->off_plocal, X->poly_local.data(), X->poly_local.size() * sizeof(PolyLocal));
+    put(X->off_pluv, X->poly_luv.data(), X->poly_luv.size() * sizeof(F2));
     if (cudaMalloc(&X->d_blob, o) != cudaSuccess) { cudaGetLastError(); X->d_blob = nullptr; return AGJ_ENOMEM; }
     if (cudaMemcpyAsync(X->d_blob, host.data(), o, cudaMemcpyHostToDevice, s) != cudaSuccess) return AGJ_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return AGJ_ECUDA;
@@ -981,7 +1016,11 @@ int launch_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, cudaStr
     return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
 
-int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, agj_pairs* out) {
+int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, agj_pairs* out,
+                cudaEvent_t const* events) {
+    auto mark = [&](int k) {
+        if (events) cudaEventRecord(events[k], s);
+    };
     if (!out || !out->offsets || !out->status || (n && !d_points)) return AGJ_EINVAL;
     if (n >= 0xFFFFFFFFull) return AGJ_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return AGJ_EINVAL;
@@ -1009,15 +1048,20 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
     }
     if (n == 0) {
         cudaMemsetAsync(out->offsets, 0, 4, s);
+        for (int k = 0; k < 4; ++k) mark(k);
         return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
     }
     const unsigned grid = (unsigned)((L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    mark(0);
     if (X.mode == AGJ_APPROX) {
         k_probe_approx<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, pts, (uint32_t)n, entries, tcount, out->status, fallbacks);
+        mark(1);
         k_scan_counts<<<(unsigned)L.n_chunks, 256, 0, s>>>(tcount, L.n_tiles, tprefix, chunks, hdr, out->offsets,
                                                            (uint32_t)n, out->status);
+        mark(2);
         k_emit_approx<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, (uint32_t)n, entries, tprefix, out->offsets, out->ids,
                                                             out->ids_capacity, out->status);
+        mark(3);
     } else {
         uint32_t* qbase = reinterpret_cast<uint32_t*>(sc + L.qbase);
         uint2* queue = reinterpret_cast<uint2*>(sc + L.queue);
@@ -1028,25 +1072,21 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
         uint32_t* cursor = reinterpret_cast<uint32_t*>(sc + L.cursor);
         uint32_t* cstart = reinterpret_cast<uint32_t*>(sc + L.cstart);
         k_probe_exact<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, pts, (uint32_t)n, entries, qbase, queue, L.queue_cap,
-                                                            hdr + 1, pcount, out->status, fallbacks);
+                                                            hdr + 1, pcount, tcount, out->status, fallbacks);
+        mark(1);
         if (X.n_polys) {
             k_poly_scan<<<1, 1024, 0, s>>>(pcount, X.n_polys, pstart, cursor, cstart, hdr + 2);
             const int sgrid = sm_count() * 4;
-            k_scatter<<<sgrid, 256, 0, s>>>(queue, hdr + 1, cursor, sorted, L.queue_cap);
-            const size_t smem = (sizeof(double2) + 16) * (kPipSmemVerts + 1);
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(k_pip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                attr = true;
-            }
-            k_pip<<<sm_count() * 2, kPipBlock, smem, s>>>(D, pts, queue, sorted, pstart, cstart, hdr + 2, pass);
+            k_scatter<<<sgrid, 256, 0, s>>>(queue, hdr + 1, cursor, sorted, L.queue_cap, X.n_polys);
+            k_pip<<<sm_count() * 4, kPipBlock, 0, s>>>(D, pts, queue, sorted, pstart, cstart, hdr + 2, pass, tcount,
+                                                        reinterpret_cast<uint64_t*>(sc) + 3);
         }
-        k_count_exact<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, (uint32_t)n, entries, qbase, pass, L.queue_cap, tcount,
-                                                            out->status);
+        mark(2);
         k_scan_counts<<<(unsigned)L.n_chunks, 256, 0, s>>>(tcount, L.n_tiles, tprefix, chunks, hdr, out->offsets,
                                                            (uint32_t)n, out->status);
         k_emit_exact<kJoinPPT><<<grid, kJoinBlock, 0, s>>>(D, (uint32_t)n, entries, qbase, pass, L.queue_cap, tprefix,
                                                            out->offsets, out->ids, out->ids_capacity, out->status);
+        mark(3);
     }
     return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }

@@ -10,7 +10,9 @@ namespace agj {
 // Copies the flattened index and the polygons to one device allocation.
 int upload_index(Index* X, cudaStream_t s);
 int join_requirements(const Index& X, uint64_t n, agj_requirements* r);
-int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, agj_pairs* out);
+// events: null, or 4 events recorded at the stage boundaries (see agj_join_timed).
+int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, agj_pairs* out,
+                cudaEvent_t const* events = nullptr);
 // Approximate join whose work space is a file-scope device array (no
 // allocation); at most 2^24 points per call.
 int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t n, uint32_t* d_offsets,

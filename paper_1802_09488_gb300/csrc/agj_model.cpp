@@ -15,6 +15,9 @@
 // offsets from the window centre normalised by powers of two (so that the
 // normalisation is exact in floating point).
 //
+// The same fit and bound give an FP32 model of U = 2^30 u and V = 2^30 v
+// (the polygon-test coordinates) for the refine step.
+//
 // Bound.  The device arithmetic is IEEE FP32 + int64 and is reproduced here
 // bit for bit (model_ij in agj_geom.cuh), so the model's value at any sample
 // is exactly what the GPU computes there.  The error |model - spec| is the sum
@@ -189,7 +192,8 @@ void fit_fast_model(Index* idx, unsigned threads) {
     const std::vector<Mono> mono = monomials();
     const int nm = (int)mono.size();
     const int G = 48;
-    std::vector<double> A((size_t)G * G * nm), bx((size_t)G * G), by((size_t)G * G);
+    std::vector<double> A((size_t)G * G * nm), bx((size_t)G * G), by((size_t)G * G), bu((size_t)G * G),
+        bv((size_t)G * G);
     double Xc, Yc, uc, vc;
     int fc;
     spec_xy(lat_c, lng_c, &Xc, &Yc, &fc, &uc, &vc);
@@ -204,9 +208,12 @@ void fit_fast_model(Index* idx, unsigned threads) {
             for (int k = 0; k < nm; ++k) A[r * nm + k] = std::pow(al, mono[k].p) * std::pow(be, mono[k].q);
             bx[r] = X - Xc;
             by[r] = Y - Yc;
+            bu[r] = (u - uc) * 1073741824.0;
+            bv[r] = (v - vc) * 1073741824.0;
         }
-    std::vector<double> cx, cy;
+    std::vector<double> cx, cy, cu, cv;
     if (!lstsq(A, bx, G * G, nm, &cx) || !lstsq(A, by, G * G, nm, &cy)) return;
+    const bool have_uv = lstsq(A, bu, G * G, nm, &cu) && lstsq(A, bv, G * G, nm, &cv);
     FastModel F;
     std::memset(&F, 0, sizeof F);
     F.enabled = 1;
@@ -266,13 +273,28 @@ void fit_fast_model(Index* idx, unsigned threads) {
         F.xh[k] = (float)cx[3 + k];
         F.yh[k] = (float)cy[3 + k];
     }
+    if (have_uv) {
+        const double U0 = uc * 1073741824.0 + cu[0], V0 = vc * 1073741824.0 + cv[0];
+        F.n0u = (int32_t)std::floor(U0);
+        F.n0v = (int32_t)std::floor(V0);
+        F.f0u = (float)(U0 - F.n0u);
+        F.f0v = (float)(V0 - F.n0v);
+        split(cu[1], &F.ul[0], &F.ul[1]);
+        split(cu[2], &F.ul[2], &F.ul[3]);
+        split(cv[1], &F.vl[0], &F.vl[1]);
+        split(cv[2], &F.vl[2], &F.vl[3]);
+        for (int k = 0; k < kFastHiTerms; ++k) {
+            F.uh[k] = (float)cu[3 + k];
+            F.vh[k] = (float)cv[3 + k];
+        }
+    }
     // sampled bound with the device-identical arithmetic: an (N+1) x (N+1)
     // grid including the window's edges and corners
     const int N = 1024;
-    std::vector<double> worst(N + 1, 0.0), worst_base(N + 1, 0.0);
+    std::vector<double> worst(N + 1, 0.0), worst_base(N + 1, 0.0), worst_uv(N + 1, 0.0);
     std::vector<uint8_t> bad(N + 1, 0);
     par((size_t)N + 1, threads ? threads : std::thread::hardware_concurrency(), [&](size_t ia) {
-        double w = 0, wb = 0;
+        double w = 0, wb = 0, wu = 0;
         const double lat = ia == (size_t)N ? lat_hi : lat_lo + (lat_hi - lat_lo) * (double)ia / N;
         for (int ib = 0; ib <= N; ++ib) {
             const double lng = ib == N ? lng_hi : lng_lo + (lng_hi - lng_lo) * (double)ib / N;
@@ -287,15 +309,34 @@ void fit_fast_model(Index* idx, unsigned threads) {
             const double dy = model_value(F.n0y, yth, ytl) - uv_to_st(v) * 1073741824.0;
             w = std::max(w, std::max(std::fabs(dx), std::fabs(dy)));
             wb = std::max(wb, (double)std::max(std::fabs((xth - model_floor(xth)) + xtl), std::fabs((yth - model_floor(yth)) + ytl)));
+            if (have_uv) {
+                float uth, utl, vth, vtl;
+                model_eval(F.ul, F.uh, F.f0u, ah, al, bh, bl, &uth, &utl);
+                model_eval(F.vl, F.vh, F.f0v, ah, al, bh, bl, &vth, &vtl);
+                // the model's real value n0 + th + tl (exact in double) against 2^30 (u, v)
+                const double du = ((double)F.n0u + (double)uth + (double)utl) - u * 1073741824.0;
+                const double dv = ((double)F.n0v + (double)vth + (double)vtl) - v * 1073741824.0;
+                wu = std::max(wu, std::max(std::fabs(du), std::fabs(dv)));
+            }
         }
         worst[ia] = w;
         worst_base[ia] = wb;
+        worst_uv[ia] = wu;
     });
-    double wmax = 0, bmax = 0;
+    double wmax = 0, bmax = 0, umax = 0;
     for (int k = 0; k <= N; ++k) {
         if (bad[k]) return;                                  // a window sample fell outside: inconsistent window
         wmax = std::max(wmax, worst[k]);
         bmax = std::max(bmax, worst_base[k]);
+        umax = std::max(umax, worst_uv[k]);
+    }
+    if (have_uv) {
+        const double eu = 2.0 * umax + std::ldexp(1.0, -16);
+        if (eu < 0.25) {
+            F.err_uv = (float)eu;
+            if ((double)F.err_uv < eu) F.err_uv = std::nextafter(F.err_uv, 1.0f);
+            F.uv_enabled = 1;
+        }
     }
     // 2 x sampled maximum, plus rounding of base +- err (|base| < 64: ulp <= 2^-17)
     if (!(bmax < 64.0)) return;
@@ -304,6 +345,38 @@ void fit_fast_model(Index* idx, unsigned threads) {
     F.err = (float)err;
     if ((double)F.err < err) F.err = std::nextafter(F.err, 1.0f);
     M = F;
+}
+
+void prepare_poly_local(Index* idx) {
+    const uint32_t P = idx->n_polys;
+    idx->poly_local.assign(P, PolyLocal{});
+    idx->poly_luv.assign(idx->poly_uv.size() / 2, F2{0.0f, 0.0f});
+    const double S = 1073741824.0;   // 2^30
+    for (uint32_t k = 0; k < P; ++k) {
+        const uint32_t a = idx->poly_off[k], b = idx->poly_off[k + 1];
+        double u0 = 1e300, u1 = -1e300, v0 = 1e300, v1 = -1e300;
+        for (uint32_t t = a; t < b; ++t) {
+            u0 = std::min(u0, idx->poly_uv[2 * t] * S); u1 = std::max(u1, idx->poly_uv[2 * t] * S);
+            v0 = std::min(v0, idx->poly_uv[2 * t + 1] * S); v1 = std::max(v1, idx->poly_uv[2 * t + 1] * S);
+        }
+        PolyLocal L{};
+        L.ru = (int32_t)std::llround(0.5 * (u0 + u1));
+        L.rv = (int32_t)std::llround(0.5 * (v0 + v1));
+        // local coordinates must stay well inside 24-bit range
+        L.ok = (u1 - L.ru < 8388608.0 && L.ru - u0 < 8388608.0 && v1 - L.rv < 8388608.0 && L.rv - v0 < 8388608.0) ? 1 : 0;
+        double dv = 0;
+        for (uint32_t t = a; t < b; ++t) {
+            const double lu = idx->poly_uv[2 * t] * S - L.ru, lv = idx->poly_uv[2 * t + 1] * S - L.rv;   // exact
+            const float fu = (float)lu, fv = (float)lv;
+            idx->poly_luv[t] = F2{fu, fv};
+            dv = std::max(dv, std::max(std::fabs((double)fu - lu), std::fabs((double)fv - lv)));
+        }
+        L.dv = (float)dv;
+        if ((double)L.dv < dv) L.dv = std::nextafter(L.dv, 1.0f);
+        L.bu0 = (float)(u0 - L.ru); L.bu1 = (float)(u1 - L.ru);
+        L.bv0 = (float)(v0 - L.rv); L.bv1 = (float)(v1 - L.rv);
+        idx->poly_local[k] = L;
+    }
 }
 
 }  // namespace agj

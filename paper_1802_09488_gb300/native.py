@@ -89,11 +89,13 @@ def lib():
             "agj_pairs_alloc": (i32, [P, u64, P, P]),
             "agj_pairs_free": (i32, [P, P]),
             "agj_join": (i32, [P, P, u64, P, P]),
+            "agj_join_timed": (i32, [P, P, u64, P, P, P]),
             "agj_join_check": (i32, [P, P, P]),
             "agj_join_host": (i32, [P, P, u64, P, P, P, P, u64, P, P]),
             "agj_cell_ids": (i32, [P, u64, P, P]),
             "agj_cell_ids_host": (i32, [P, u64, P]),
             "agj_fast_ids_host": (i32, [P, P, u64, P, P]),
+            "agj_covers_certified_host": (i32, [P, P, P, u64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -203,6 +205,15 @@ class Index:
                "agj_fast_ids_host")
         return ids, lv
 
+    def covers_certified_host(self, points: np.ndarray, polys: np.ndarray) -> np.ndarray:
+        """Certified FP32 refine decisions (1, 0, -1 undecided) on the host."""
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 2)
+        pl = np.ascontiguousarray(polys, dtype=np.uint32)
+        out = np.zeros(len(pts), dtype=np.int8)
+        _check(lib().agj_covers_certified_host(self._h, _np_ptr(pts), _np_ptr(pl), len(pts), _np_ptr(out)),
+               "agj_covers_certified_host")
+        return out
+
     def requirements(self, n: int) -> tuple[int, int]:
         r = Requirements()
         _check(lib().agj_join_requirements(self._h, int(n), C.byref(r)), "agj_join_requirements")
@@ -239,6 +250,10 @@ class Pairs:
         """Points of the last join whose walk recomputed the FP64 cell id."""
         return int(self.scratch[16:24].cpu().view(torch_int64()).item())
 
+    def refine_fallbacks(self) -> int:
+        """Candidates of the last exact join whose refine test ran in FP64."""
+        return int(self.scratch[24:32].cpu().view(torch_int64()).item())
+
     def to_host(self, stream=None):
         """(offsets u32[n+1], ids u32[nnz]) as numpy, after a status check."""
         nnz = self.check(stream)
@@ -262,6 +277,16 @@ def join(index: Index, points, pairs: Pairs | None = None, stream=None) -> Pairs
     pairs.n = n
     rc = lib().agj_join(index.handle, C.c_void_p(points.data_ptr()), n, _stream_ptr(stream), C.byref(pairs.c))
     _check(rc, "agj_join")
+    return pairs
+
+
+def join_timed(index: Index, points, pairs: Pairs, events, stream=None) -> Pairs:
+    """agj_join recording four torch.cuda.Event objects at the stage
+    boundaries (see include/agj.h, agj_join_timed)."""
+    arr = (C.c_void_p * 4)(*[C.c_void_p(e.cuda_event) for e in events])
+    pairs.n = points.shape[0]
+    _check(lib().agj_join_timed(index.handle, C.c_void_p(points.data_ptr()), points.shape[0], _stream_ptr(stream),
+                                C.byref(pairs.c), arr), "agj_join_timed")
     return pairs
 
 

@@ -74,3 +74,43 @@ def test_fast_model_off_for_wide_windows(agj):
              np.array([[42.5, -71.0], [42.51, -71.0], [42.5, -70.99]])]
     ix = agj.Index(polys, agj.APPROX, 10.0, host_only=True)
     assert ix.stats()["fast_ids"] == 0
+
+
+def test_certified_refine_equals_oracle(agj, oracle):
+    """The certified FP32 ST_Covers test, where it decides, equals the
+    oracle's FP64 predicate; random points are almost all decided, points
+    a few micrometres from an edge or on a vertex are left undecided."""
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c2_city_polygons()
+    ix = agj.Index(polys, agj.EXACT, 0, host_only=True)
+    ps = oracle.PolySet(polys)
+    rng = np.random.default_rng(45)
+    pts, pid = [], []
+    # random points against a random polygon and against the polygons covering them
+    cand = synth.points_mixture(20000, synth.BOX_CITY, seed=46, dist_seed=3)
+    for k in range(len(cand)):
+        q = int(rng.integers(0, len(polys)))
+        pts.append(cand[k]); pid.append(q)
+        hits = ps.hits_brute(*cand[k])
+        for h in hits:
+            pts.append(cand[k]); pid.append(h)
+    n_random_pairs = len(pts)
+    # points near edges: edge midpoints offset by 1e-4 .. 1e-11 degree, and vertices
+    for q in rng.choice(len(polys), 60, replace=False):
+        P = polys[q]
+        for t in range(0, len(P), max(1, len(P) // 8)):
+            a, b = P[t], P[(t + 1) % len(P)]
+            m = 0.5 * (a + b)
+            d = np.array([-(b - a)[1], (b - a)[0]])
+            d /= np.linalg.norm(d)
+            for off in (1e-4, 1e-6, 1e-8, 1e-9, 1e-10, 1e-11, -1e-11, -1e-9, -1e-6, -1e-4):
+                pts.append(m + off * d); pid.append(q)
+            pts.append(a.copy()); pid.append(q)
+    pts = np.array(pts); pid = np.array(pid, dtype=np.uint32)
+    got = ix.covers_certified_host(pts, pid)
+    want = np.array([ps.covers(int(q), *p) for p, q in zip(pts, pid)], dtype=np.int8)
+    decided = got >= 0
+    assert np.array_equal(got[decided], want[decided])
+    n_rand = n_random_pairs
+    assert np.mean(decided[:n_rand]) > 0.999
+    assert (~decided).sum() > 0          # the near-edge points exercise the fallback
