@@ -277,6 +277,65 @@ int agj_join_approx_noalloc(const agj_index* index, const double* d_points, uint
 int agj_join_timed(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out,
                    void* const events[4]);
 
+/* ---------------------------------------------------------------------- */
+/* batched form (no counterpart in the paper)                               */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * A plan that joins m (index, point batch) jobs of uneven sizes in one
+ * launch sequence: the probe and emit kernels are persistent grids striding
+ * over every job's warp tiles, the refine step covers the candidates of all
+ * exact jobs at once, and the sequence is captured once into a CUDA graph
+ * that each run replays.  The paper joins one point stream against one
+ * index; the batched form serves callers with many small or uneven batches,
+ * where one plain join per batch pays a launch sequence and a grid tail per
+ * batch.
+ *
+ * Every job computes exactly what agj_join computes for the same (index,
+ * points) - the same pairs, ids ascending per point, the same status words.
+ *
+ * agj_batch_create: indexes[j] (built on the current device, not host_only)
+ * and n[j] (< 2^32 points) fix the plan; the points and outputs are given
+ * per run.  opts may be NULL (defaults).  The plan owns one device
+ * allocation (work space for all jobs, agj_batch_device_bytes) and, with
+ * use_graph, an instantiated graph.  At most 65535 jobs (AGJ_EUNSUPPORTED
+ * beyond).  Errors: AGJ_EINVAL (null or foreign index, bad option),
+ * AGJ_ECAPACITY (a job's ids or the candidate queue
+ * would not fit 32-bit offsets), AGJ_ENOMEM, AGJ_ECUDA.
+ */
+typedef struct agj_batch agj_batch;
+typedef struct {
+    uint32_t points_per_lane;   /* 1, 2 or 4 points per lane of a warp tile (0 = 2) */
+    uint32_t ctas_per_sm;       /* 0: one warp per warp tile of all jobs; 1..8: persistent
+                                   probe grid of SMs x this CTAs */
+    uint32_t no_graph;          /* 1: enqueue the kernels on each run instead of a graph */
+    uint32_t reserved;
+} agj_batch_opts;
+int agj_batch_create(const agj_index* const* indexes, const uint64_t* n, uint32_t m, const agj_batch_opts* opts,
+                     agj_batch** out);
+
+/*
+ * Runs the plan: d_points[j] (device, n[j] x {lat, lng}, 16-byte aligned,
+ * borrowed) joined into outs[j], whose offsets, ids and status must satisfy
+ * agj_join_requirements(indexes[j], n[j]) (scratch is not needed: when
+ * outs[j].scratch is given with at least 32 bytes, its bytes 16..31 receive
+ * the job's diagnostics as agj_join writes them).  Asynchronous on
+ * `stream`; runs of one plan must be ordered (one stream), as they share its
+ * work space.  Errors: AGJ_EINVAL, AGJ_ECAPACITY, AGJ_ECUDA; device-side
+ * conditions land in outs[j].status[1] as for agj_join.
+ */
+int agj_batch_run(agj_batch* batch, const double* const* d_points, void* stream, agj_pairs* outs);
+uint64_t agj_batch_device_bytes(const agj_batch* batch);
+/* Frees the plan; the caller orders it after the plan's last run. */
+void agj_batch_free(agj_batch* batch);
+
+/*
+ * One-shot batched join: creates a plan with default options, runs it on
+ * `stream`, synchronises the stream and frees the plan.
+ */
+int agj_join_batched(const agj_index* const* indexes, const double* const* d_points, const uint64_t* n,
+                     uint32_t m, void* stream, agj_pairs* outs);
+
 /* Synchronises `stream`, reads out->status and returns AGJ_OK, or the first
  * device-side error as a status code; *nnz receives the pair count. */
 int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz);

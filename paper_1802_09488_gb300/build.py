@@ -27,7 +27,7 @@ CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
 NVCCFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
              f"-I{ROOT}/include", "--expt-relaxed-constexpr"]
 
-CU_SOURCES = ["agj_kernels.cu"]
+CU_SOURCES = ["agj_kernels.cu", "agj_batch.cu"]
 CXX_SOURCES = ["agj_build.cpp", "agj_model.cpp", "agj_capi.cpp"]
 
 

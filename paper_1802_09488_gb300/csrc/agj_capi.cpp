@@ -6,6 +6,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <vector>
 
 #include "../../include/agj.h"
 #include "agj_geom.cuh"
@@ -14,6 +15,10 @@
 
 struct agj_index {
     agj::Index X;
+};
+
+struct agj_batch {
+    agj::Batch* B;
 };
 
 namespace {
@@ -231,6 +236,53 @@ int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz) {
     if (st[1] & 4ull) return AGJ_EDEVICE;
     if (st[1] & 8ull) return AGJ_ECAPACITY;
     return AGJ_OK;
+}
+
+int agj_batch_create(const agj_index* const* indexes, const uint64_t* n, uint32_t m, const agj_batch_opts* opts,
+                     agj_batch** out) {
+    if (!out || (m && (!indexes || !n))) return AGJ_EINVAL;
+    *out = nullptr;
+    std::vector<const agj::Index*> xs(m);
+    for (uint32_t j = 0; j < m; ++j) {
+        if (!indexes[j]) return AGJ_EINVAL;
+        xs[j] = &indexes[j]->X;
+    }
+    agj_batch_opts o{};
+    if (opts) o = *opts;
+    agj_batch* h = new (std::nothrow) agj_batch();
+    if (!h) return AGJ_ENOMEM;
+    const int rc = agj::batch_create(xs.data(), n, m, (int)o.points_per_lane, (int)o.ctas_per_sm, o.no_graph == 0,
+                                     &h->B);
+    if (rc != AGJ_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return AGJ_OK;
+}
+
+int agj_batch_run(agj_batch* batch, const double* const* d_points, void* stream, agj_pairs* outs) {
+    if (!batch) return AGJ_EINVAL;
+    return agj::batch_run(batch->B, d_points, as_stream(stream), outs);
+}
+
+uint64_t agj_batch_device_bytes(const agj_batch* batch) { return batch ? agj::batch_device_bytes(batch->B) : 0; }
+
+void agj_batch_free(agj_batch* batch) {
+    if (!batch) return;
+    agj::batch_free(batch->B);
+    delete batch;
+}
+
+int agj_join_batched(const agj_index* const* indexes, const double* const* d_points, const uint64_t* n,
+                     uint32_t m, void* stream, agj_pairs* outs) {
+    agj_batch* b = nullptr;
+    int rc = agj_batch_create(indexes, n, m, nullptr, &b);
+    if (rc != AGJ_OK) return rc;
+    rc = agj_batch_run(b, d_points, stream, outs);
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess && rc == AGJ_OK) rc = AGJ_ECUDA;
+    agj_batch_free(b);
+    return rc;
 }
 
 int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, double* d_points_staging,

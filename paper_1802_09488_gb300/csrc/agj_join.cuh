@@ -1,0 +1,168 @@
+// agj_join.cuh — host side of one join launch sequence over a job source
+// (one job for the plain join, many for the batched form): the work-space
+// layout and the kernels enqueued on a stream.  Nothing here allocates or
+// synchronises, so the sequence can be captured into a CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "agj_index.h"
+#include "agj_probe.cuh"
+
+namespace agj {
+
+// defined in agj_kernels.cu
+int sm_count();
+DevIndex make_dev_index(const Index& X);
+// A job descriptor of (X, d_points, n, out) with its diagnostics in counters;
+// tile0 and poly0 are zero (the plain join's single job).
+JobDesc make_job(const Index& X, const double* d_points, uint64_t n, agj_pairs* out, uint64_t* counters);
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// Work space of one join launch sequence, as byte offsets into one buffer:
+//   [header 256 B: u32 tile-scan chunk counter, u32 queue length,
+//    u32 refine chunks, u32 polygon-scan chunk counter,
+//    u64 FP64 cell-id fallbacks, u64 FP64 refine fallbacks, u64 scan errors]
+//   [tile-scan chunk states] [exact: polygon-scan chunk states,
+//    per-polygon candidate counts]
+//   -- the part zeroed before every launch sequence --
+//   [entries u64 per point] [tile counts u32] [tile prefixes u32]
+//   then, with exact jobs, the queue bases, the candidate queue, its pass
+//   bytes, its polygon order and the per-polygon segments
+struct JoinLayout {
+    uint64_t chunks = 0, pchunks = 0, pcount = 0, zero_end = 0;
+    uint64_t entries = 0, tcount = 0, tprefix = 0;
+    uint64_t qbase = 0, queue = 0, pass = 0, sorted = 0, pstart = 0, cursor = 0, cstart = 0, total = 0;
+    uint64_t n_points = 0, n_tiles = 0, n_chunks = 0, n_pchunks = 0, queue_cap = 0, n_polys = 0;
+    bool exact = false;
+};
+
+constexpr uint64_t kHdrIdFallbacks = 2;    // u64 word of the header
+constexpr uint64_t kHdrRefineFallbacks = 3;
+constexpr uint64_t kHdrScanErr = 4;
+constexpr uint64_t kPolyScanPerCta = 256 * 4;
+
+// n_points / n_tiles: sizes of the (tile-padded) global point space and of
+// the tile space; exact: some
+// job refines; queue_cap: candidate queue slots; n_polys: polygons of the
+// exact jobs.
+inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, uint64_t queue_cap, uint64_t n_polys) {
+    JoinLayout L;
+    L.n_points = n_points;
+    L.n_tiles = n_tiles;
+    L.exact = exact;
+    L.n_chunks = (n_tiles + 256 * kScanItems - 1) / (256 * kScanItems);
+    uint64_t o = 256;
+    L.chunks = o;
+    o += align256(std::max<uint64_t>(L.n_chunks, 1) * 8);
+    if (exact) {
+        L.n_polys = n_polys;
+        L.queue_cap = queue_cap;
+        L.n_pchunks = (n_polys + kPolyScanPerCta - 1) / kPolyScanPerCta;
+        L.pchunks = o;
+        o += align256(std::max<uint64_t>(L.n_pchunks, 1) * 8);
+        L.pcount = o;
+        o += align256(n_polys * 4 + 4);
+    }
+    L.zero_end = o;
+    L.entries = o; o += align256(n_points * 8 + 8);
+    L.tcount = o; o += align256(n_tiles * 4 + 4);
+    L.tprefix = o; o += align256(n_tiles * 4 + 4);
+    if (exact) {
+        L.qbase = o; o += align256(n_points * 4 + 4);
+        L.queue = o; o += align256(queue_cap * 8 + 8);
+        L.pass = o; o += align256(queue_cap + 1);
+        L.sorted = o; o += align256(queue_cap * 4 + 4);
+        L.pstart = o; o += align256((n_polys + 1) * 4);
+        L.cursor = o; o += align256((n_polys + 1) * 4);
+        L.cstart = o; o += align256((n_polys + 1) * 4);
+    }
+    L.total = o;
+    return L;
+}
+
+inline JoinScratch join_scratch(const JoinLayout& L, char* sc) {
+    JoinScratch S;
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(sc);
+    S.entries = reinterpret_cast<uint64_t*>(sc + L.entries);
+    S.tile_count = reinterpret_cast<uint32_t*>(sc + L.tcount);
+    S.tile_prefix = reinterpret_cast<uint32_t*>(sc + L.tprefix);
+    S.qbase = L.exact ? reinterpret_cast<uint32_t*>(sc + L.qbase) : nullptr;
+    S.queue = L.exact ? reinterpret_cast<uint2*>(sc + L.queue) : nullptr;
+    S.pass = L.exact ? reinterpret_cast<uint8_t*>(sc + L.pass) : nullptr;
+    S.queue_len = hdr + 1;
+    S.poly_count = L.exact ? reinterpret_cast<uint32_t*>(sc + L.pcount) : nullptr;
+    S.queue_cap = L.queue_cap;
+    S.scan_err = reinterpret_cast<const uint64_t*>(sc) + kHdrScanErr;
+    return S;
+}
+
+struct JoinLaunch {
+    int probe_grid = 0;       // CTAs of the probe kernel
+    int emit_grid = 0;        // CTAs of the emit kernel
+    int sms = 1;              // for the grid-stride kernels
+    int pip_grid = 0;
+    const uint16_t* tile_job = nullptr;   // batched form: job of each tile
+    uint32_t* job_base = nullptr;         // batched form: tile prefix at each job's first tile
+};
+
+// Enqueues zeroing, probe, refine (exact jobs), scan and emit.  extra_zero /
+// n_extra: further words zeroed by the first kernel (the plain join's status).
+// events: null or 4 events recorded before the probe, after the probe, after
+// the refine (exact) or the scan (approximate), and at the end.
+template <int PPT, class Src, int MODE>
+cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const JoinLaunch& G, uint64_t* extra_zero,
+                         uint64_t n_extra, cudaStream_t s, cudaEvent_t const* events) {
+    auto mark = [&](int k) {
+        if (events) cudaEventRecord(events[k], s);
+    };
+    const JoinScratch S = join_scratch(L, sc);
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(sc);
+    {
+        const uint64_t zero_words = L.zero_end / 8;
+        const int grid = (int)std::min<uint64_t>((zero_words + n_extra + 255) / 256 + 1, (uint64_t)G.sms * 4);
+        k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint64_t*>(sc), zero_words, extra_zero, n_extra);
+    }
+    mark(0);
+    if (L.n_tiles) k_probe<PPT, Src, MODE><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+    mark(1);
+    const bool refine = MODE != kModeApprox && L.exact && L.n_polys;
+    if (refine && L.n_tiles) {
+        k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
+            S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.pstart),
+            reinterpret_cast<uint32_t*>(sc + L.cursor), reinterpret_cast<uint32_t*>(sc + L.cstart), hdr + 2,
+            reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3, reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
+        k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.queue_len, reinterpret_cast<uint32_t*>(sc + L.cursor),
+                                            reinterpret_cast<uint32_t*>(sc + L.sorted), L.queue_cap,
+                                            (uint32_t)L.n_polys);
+        k_pip<Src><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, (uint32_t)L.n_polys, S.queue,
+                                                    reinterpret_cast<const uint32_t*>(sc + L.sorted),
+                                                    reinterpret_cast<const uint32_t*>(sc + L.pstart),
+                                                    reinterpret_cast<const uint32_t*>(sc + L.cstart), hdr + 2, S.pass,
+                                                    S.tile_count);
+    }
+    if (MODE == kModeApprox) {
+        if (L.n_tiles)
+            k_scan_counts<<<(unsigned)L.n_chunks, 256, 0, s>>>(S.tile_count, L.n_tiles, S.tile_prefix,
+                                                               reinterpret_cast<uint64_t*>(sc + L.chunks), hdr,
+                                                               reinterpret_cast<uint64_t*>(sc) + kHdrScanErr,
+                                                               G.tile_job, G.job_base);
+        mark(2);
+    } else {
+        mark(2);
+        if (L.n_tiles)
+            k_scan_counts<<<(unsigned)L.n_chunks, 256, 0, s>>>(S.tile_count, L.n_tiles, S.tile_prefix,
+                                                               reinterpret_cast<uint64_t*>(sc + L.chunks), hdr,
+                                                               reinterpret_cast<uint64_t*>(sc) + kHdrScanErr,
+                                                               G.tile_job, G.job_base);
+    }
+    if (L.n_tiles) k_emit<PPT, Src, MODE><<<G.emit_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+    mark(3);
+    return cudaGetLastError();
+}
+
+}  // namespace agj

@@ -19,4 +19,13 @@ int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t 
                                uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, cudaStream_t s);
 int launch_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, cudaStream_t s);
 
+// Batched form (agj_batch.cu): a plan for m (index, point count) jobs with
+// its own work space and, with use_graph, an instantiated CUDA graph.
+struct Batch;
+int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, int ctas_per_sm, bool use_graph,
+                 Batch** out);
+int batch_run(Batch* B, const double* const* d_points, cudaStream_t s, agj_pairs* outs);
+uint64_t batch_device_bytes(const Batch* B);
+void batch_free(Batch* B);
+
 }  // namespace agj

@@ -1,0 +1,763 @@
+// agj_probe.cuh — device side of the join, shared by the plain join
+// (agj_kernels.cu) and the batched form (agj_batch.cu): the per-point probe
+// (cell id, face/prefix stage, trie walk, entry decode), scans, the refine
+// test, and the join kernels, templated on the points per lane (PPT) and on
+// the job source:
+//   OneJob    the plain join: one job descriptor passed by value;
+//   ManyJobs  the batched form: an array of job descriptors whose points and
+//             polygons are laid end to end in a global tile and polygon
+//             space; a tile or polygon finds its job by binary search.
+// Kernels iterate over global warp tiles with a grid stride, so the same code
+// runs as one CTA per tile group (plain join) or as a persistent grid
+// (batched form).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "agj_device.cuh"
+#include "agj_geom.cuh"
+
+namespace agj {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+static __device__ const HilbertLut g_hilbert_lut = make_hilbert_lut();
+constexpr uint32_t kSpinLimit = 1u << 22;
+#ifndef AGJ_PROBE_MIN_BLOCKS
+#define AGJ_PROBE_MIN_BLOCKS 3   // resident CTAs per SM the probe kernels are compiled for
+#endif
+constexpr int kJoinBlock = 256;
+constexpr int kJoinPPT = 2;                    // points per lane of the plain join
+constexpr int kWarpsPerBlock = kJoinBlock / 32;
+constexpr int kPipBlock = 256;
+constexpr int kPipSmemVerts = 2048;            // vertices staged per CTA (8 B each)
+constexpr int kScanItems = 16;
+
+// ---------------------------------------------------------------------------
+// scans
+// ---------------------------------------------------------------------------
+
+template <int BLOCK, class T>
+__device__ __forceinline__ T block_excl_scan(T v, T* total, T* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = BLOCK / 32;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < NW ? s_warp[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_warp[lane] = w;
+    }
+    __syncthreads();
+    *total = s_warp[NW - 1];
+    const T wp = warp ? s_warp[warp - 1] : T(0);
+    __syncthreads();
+    return wp + x - v;
+}
+
+// Decoupled look-back across tiles (run by one full warp).  Tile states are
+// 64-bit words: top 2 bits 0 = not ready, 1 = aggregate, 2 = inclusive
+// prefix; low 62 bits the value.  Tiles are numbered in the order their CTAs
+// started (atomic counter), so every predecessor is running or done and the
+// wait ends; it is bounded all the same and sets kErrScanTimeout in *err.
+__device__ __forceinline__ uint64_t lookback(uint64_t* tiles, uint32_t tile, uint64_t total, uint64_t* err) {
+    const int lane = threadIdx.x & 31;
+    constexpr uint64_t kVal = (1ull << 62) - 1ull;
+    if (tile == 0) {
+        if (lane == 0) st_release_u64(&tiles[0], (2ull << 62) | total);
+        return 0;
+    }
+    if (lane == 0) st_release_u64(&tiles[tile], (1ull << 62) | total);
+    uint64_t prefix = 0;
+    int64_t idx = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t t = idx - lane;
+        uint64_t st = 2ull << 62;
+        if (t >= 0) {
+            st = ld_acquire_u64(&tiles[t]);
+            while ((st >> 62) == 0ull) {
+                if (++spins > kSpinLimit) {
+                    atomicOr((unsigned long long*)err, (unsigned long long)kErrScanTimeout);
+                    st = 1ull << 62;
+                    break;
+                }
+                __nanosleep(32);
+                st = ld_acquire_u64(&tiles[t]);
+            }
+        }
+        const uint32_t inc = __ballot_sync(kFull, (st >> 62) == 2ull);
+        const int first = inc ? __ffs(inc) - 1 : 31;
+        uint64_t c = lane <= first ? (st & kVal) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+        prefix += __shfl_sync(kFull, c, 0);
+        if (inc) break;
+        idx -= 32;
+    }
+    if (lane == 0) st_release_u64(&tiles[tile], (2ull << 62) | (prefix + total));
+    return prefix;
+}
+
+// ---------------------------------------------------------------------------
+// per-point probe: cell id -> face root -> common prefix -> trie walk
+// ---------------------------------------------------------------------------
+
+// Walk state of one point.  The key bytes of the leaf id are produced one at
+// a time from the 4-level Hilbert table as the walk consumes them (byte b
+// holds levels 4b+1 .. 4b+4).
+struct Walk {
+    uint32_t i32, j32;      // (i, j) << 2: levels 31-32 are zero padding
+    uint32_t o;             // Hilbert orientation before byte b
+    uint32_t b;             // next key byte
+    uint32_t node;          // current trie node
+    int32_t cert;           // key bytes whose levels are all certified
+    int32_t st;             // 0 done, 1 walking, 2 needs the FP64 cell id
+};
+
+__device__ __forceinline__ uint32_t next_byte(const uint16_t* lut, Walk& w) {
+    const uint32_t sh = 28u - 4u * w.b;
+    const uint32_t e = lut[(w.o << 8) | (((w.i32 >> sh) & 15u) << 4) | ((w.j32 >> sh) & 15u)];
+    w.o = e & 3u;
+    ++w.b;
+    return e >> 2;
+}
+
+// Cell id + face/prefix stage (§IV-B stage 1) for one point.  With the
+// index's fast model (and exact == false) the id comes from the certified FP32
+// path; otherwise from the FP64 spec.  Leaves w.st = 0 when the point joins
+// nothing, 1 when the walk can start at w.node, 2 when an uncertified level
+// decides the prefix.
+__device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* faces, const uint16_t* lut, double lat,
+                                           double lng, bool exact, Walk& w) {
+    uint32_t i, j;
+    int lc, face;
+    w.st = 0;
+    w.b = 0;
+    if (!exact && X.model.enabled) {
+        if (!model_ij(X.model, lat, lng, &i, &j, &lc)) return;       // outside the window: in no cell
+        face = X.model.face;
+        if (lc >= kLevels) lc = kLevels + 2;                        // exact id: padding levels too
+    } else {
+        if (!point_valid(lat, lng)) return;
+        double u, v;
+        face = face_uv(lat, lng, &u, &v);
+        i = st_to_ij(uv_to_st(u));
+        j = st_to_ij(uv_to_st(v));
+        lc = kLevels + 2;
+    }
+    const DevFace fr = faces[face];
+    if (fr.root == kNoRootDev) return;
+    w.i32 = i << 2;
+    w.j32 = j << 2;
+    w.o = (uint32_t)face & 1u;
+    w.b = 0;
+    w.cert = lc >> 2;
+    const uint32_t nb = fr.prefix_bits >> 3;
+    for (uint32_t q = 0; q < nb; ++q) {
+        const uint32_t byte = next_byte(lut, w);
+        if (byte != (uint32_t)((fr.prefix >> (8 * (nb - 1 - q))) & 0xFFu)) {
+            w.st = (int32_t)q < w.cert ? 0 : 2;                     // certain mismatch: no cell
+            return;
+        }
+    }
+    if ((int32_t)nb > w.cert) { w.st = 2; return; }
+    w.node = fr.root;
+    w.st = 1;
+}
+
+// Walks of PPT points advance level by level together, so their gathers
+// (Listing "Probe Adaptive Cell Trie") are in flight at the same time.
+// Points whose walk needs an uncertified key byte get their FP64 id and walk
+// again alone (counted in *fallbacks).  Returns the trie entries read.
+template <int PPT>
+__device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
+                                                 const uint64_t* s_root, const double* lat, const double* lng,
+                                                 const bool* valid, uint64_t e[PPT], uint64_t* err,
+                                                 uint32_t* fallbacks) {
+    uint32_t gathers = 0;
+    Walk w[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        e[k] = 0;
+        w[k].st = 0;
+        w[k].b = 0;
+        if (valid[k]) begin_walk(X, faces, lut, lat[k], lng[k], false, w[k]);
+    }
+    uint32_t prefix_bytes[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) prefix_bytes[k] = w[k].b;
+    const uint32_t n_nodes32 = (uint32_t)min(X.n_nodes, (uint64_t)0xFFFFFFFFu);
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        uint64_t v[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            v[k] = 0;
+            if (w[k].st == 1) {
+                if (w[k].b >= (uint32_t)w[k].cert) {
+                    w[k].st = 2;
+                } else {
+                    const uint32_t byte = next_byte(lut, w[k]);
+                    // with the fast model every walk starts at the model face's root,
+                    // which each CTA holds in shared memory
+                    v[k] = (d == 0 && s_root) ? s_root[byte] : __ldg(X.nodes + (((uint64_t)w[k].node) << 8) + byte);
+                }
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (w[k].st != 1) continue;
+            // child entries hold node << 11 with node < 2^32, so the low 32 bits
+            // of (v >> 11) name the node; checking them keeps every read in bounds
+            const uint32_t child = (uint32_t)(v[k] >> 11);
+            if ((v[k] & 3ull) != 0ull || v[k] == 0ull) {
+                e[k] = v[k];
+                w[k].st = 0;
+            } else if (child >= n_nodes32) {
+                atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
+                w[k].st = 0;
+            } else {
+                w[k].node = child;
+                any = true;
+            }
+        }
+        if (!any) break;
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) gathers += w[k].b - prefix_bytes[k];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (w[k].st == 1) {
+            atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
+            e[k] = 0;
+        } else if (w[k].st == 2) {
+            ++*fallbacks;
+            Walk x;
+            begin_walk(X, faces, lut, lat[k], lng[k], true, x);
+            e[k] = 0;
+            while (x.st == 1) {
+                if (x.b >= 8u) {
+                    atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
+                    break;
+                }
+                const uint32_t byte = next_byte(lut, x);
+                const uint64_t v = __ldg(X.nodes + (((uint64_t)x.node) << 8) + byte);
+                ++gathers;
+                if ((v & 3ull) != 0ull || v == 0ull) {
+                    e[k] = v;
+                    break;
+                }
+                if ((v >> 11) >= X.n_nodes) {
+                    atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
+                    break;
+                }
+                x.node = (uint32_t)(v >> 11);
+            }
+        }
+    }
+    return gathers;
+}
+
+// Adds a per-thread count to a device counter with one atomic per warp.
+__device__ __forceinline__ void warp_count(uint32_t v, uint64_t* counter) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long*)counter, (unsigned long long)v);
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Per-CTA setup shared by the probe kernels: the Hilbert table in shared
+// memory and, when every tile of the CTA probes the same index X (else
+// null), its face table and, with the fast model, the model face's root
+// node.  Returns the shared root (or null).
+__device__ __forceinline__ const uint64_t* cta_setup(const DevIndex* X, uint16_t* s_hlut, DevFace* s_faces,
+                                                     uint64_t* s_root) {
+    for (int t = threadIdx.x; t < 512; t += blockDim.x)
+        reinterpret_cast<uint32_t*>(s_hlut)[t] = reinterpret_cast<const uint32_t*>(g_hilbert_lut.v)[t];
+    if (!X) return nullptr;
+    if (threadIdx.x < 6) s_faces[threadIdx.x] = X->faces[threadIdx.x];
+    if (!X->model.enabled) return nullptr;
+    const uint32_t root = X->faces[X->model.face].root;
+    if (root == kNoRootDev) return nullptr;
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(X->nodes + (uint64_t)root * 256);
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) reinterpret_cast<ulonglong2*>(s_root)[t] = __ldg(src + t);
+    return s_root;
+}
+
+__device__ __forceinline__ uint32_t payload_of(uint64_t e, int which) {
+    return (uint32_t)(e >> (which ? 33 : 2)) & 0x7FFFFFFFu;
+}
+
+// Writes every reference of entry e (approximate join), ascending ids.
+__device__ __forceinline__ void emit_all(const DevIndex& X, uint64_t e, uint32_t* ids, uint64_t o) {
+    const uint32_t tag = (uint32_t)(e & 3ull);
+    if (tag == 1) {
+        ids[o] = payload_of(e, 0) >> 1;
+    } else if (tag == 2) {
+        ids[o] = payload_of(e, 0) >> 1;
+        ids[o + 1] = payload_of(e, 1) >> 1;
+    } else if (tag == 3) {
+        const uint32_t off = payload_of(e, 0);
+        const uint32_t nt = __ldg(X.lut + off);
+        const uint32_t* T = X.lut + off + 1;
+        const uint32_t nc = __ldg(X.lut + off + 1 + nt);
+        const uint32_t* Cc = X.lut + off + 2 + nt;
+        uint32_t a = 0, b = 0;
+        while (a < nt || b < nc) {
+            const uint32_t ta = a < nt ? __ldg(T + a) : 0xFFFFFFFFu;
+            const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
+            if (ta < cb) { ids[o++] = ta; ++a; }
+            else { ids[o++] = cb; ++b; }
+        }
+    }
+}
+
+
+// Number of output pairs of one point of the exact join (true references
+// plus the candidates that passed the PIP); 0xFFFFFFFF flags a corrupt queue
+// position.
+__device__ __forceinline__ uint32_t exact_count(const DevIndex& X, uint64_t e, const uint32_t* qbase, uint64_t g,
+                                                const uint8_t* pass, uint64_t queue_cap, uint32_t* qb,
+                                                uint64_t* status) {
+    uint32_t nt, nc;
+    entry_counts(X, e, &nt, &nc);
+    *qb = 0;
+    if (!nc) return nt;
+    *qb = qbase[g];
+    if ((uint64_t)*qb + nc > queue_cap) {   // cannot happen: the queue holds every candidate
+        atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrQueueOverflow);
+        return 0xFFFFFFFFu;
+    }
+    uint32_t c = nt;
+    for (uint32_t t = 0; t < nc; ++t) c += pass[*qb + t];
+    return c;
+}
+
+// ST_Covers in FP64 exactly as the spec (the certified test's fallback):
+// same face, closed (u,v) bbox, ring rule with integer keys for the range
+// tests and FP64 orientation, vertices read from global memory.
+__device__ __forceinline__ bool covers_fp64(const DevIndex& X, uint32_t poly, double lat, double lng) {
+    if (!point_valid(lat, lng)) return false;
+    double pu, pv;
+    const int f = face_uv(lat, lng, &pu, &pv);
+    if (f != X.poly_face[poly]) return false;
+    const int64_t puk = dkey(pu), pvk = dkey(pv);
+    const int64_t* bb = X.poly_bbox + 4ull * poly;
+    if (!(puk >= bb[0] && puk <= bb[1] && pvk >= bb[2] && pvk <= bb[3])) return false;
+    const uint32_t v0 = X.poly_off[poly], V = X.poly_off[poly + 1] - v0;
+    bool inside = false;
+    for (uint32_t k = 0; k < V; ++k) {
+        const uint32_t a = v0 + k, b = v0 + (k + 1 == V ? 0u : k + 1);
+        const int64_t av = X.poly_vkey[a], bv = X.poly_vkey[b];
+        const int64_t vlo = av < bv ? av : bv, vhi = av < bv ? bv : av;
+        if (pvk < vlo || pvk > vhi) continue;
+        const double2 A = X.poly_uv[a], B = X.poly_uv[b];
+        const double o = (B.x - A.x) * (pv - A.y) - (B.y - A.y) * (pu - A.x);
+        if (o == 0.0) {
+            const int64_t au = X.poly_ukey[a], bu = X.poly_ukey[b];
+            if (puk >= (au < bu ? au : bu) && puk <= (au < bu ? bu : au)) return true;
+        }
+        if ((av <= pvk && pvk < bv && o > 0.0) || (bv <= pvk && pvk < av && o < 0.0)) inside = !inside;
+    }
+    return inside;
+}
+
+// ---------------------------------------------------------------------------
+// job sources
+// ---------------------------------------------------------------------------
+
+// One (index, points, output) job.  Its warp tiles are tile0 .. tile0 +
+// ceil(n / (32 PPT)) - 1 of the global tile space, and in exact mode its
+// polygons poly0 .. poly0 + n_polys - 1 of the global polygon space of the
+// refine step.  Per-point work space (stored entries, queue bases) is
+// indexed by the tile-padded global point index wt * 32 PPT + lane + 32 k,
+// which needs no job lookup.
+struct JobDesc {
+    DevIndex X;
+    const double2* pts;
+    uint32_t* offsets;        // n + 1
+    uint32_t* ids;
+    uint64_t* status;         // 4 words: nnz, error bits, candidates, trie entries read
+    uint64_t* counters;       // [0] FP64 cell-id fallbacks, [1] FP64 refine fallbacks
+    uint64_t ids_cap;
+    uint64_t tile0;
+    uint32_t n;
+    uint32_t poly0;
+    uint32_t exact;           // 1: exact join (refine candidates), 0: approximate join
+};
+
+// The plain join: one job, passed by value as a kernel parameter.
+struct OneJob {
+    JobDesc d;
+    static constexpr bool kSingle = true;
+    __device__ __forceinline__ uint32_t find_tile(uint64_t) const { return 0; }
+    __device__ __forceinline__ uint32_t find_poly(uint32_t) const { return 0; }
+    __device__ __forceinline__ const JobDesc& job(uint32_t) const { return d; }
+    __device__ __forceinline__ uint32_t job_base(uint32_t) const { return 0; }
+};
+
+// The batched form: m jobs in device memory, laid end to end.
+struct ManyJobs {
+    const JobDesc* d;
+    const uint16_t* tile_job; // job of each global tile
+    const uint32_t* base;     // per job: tile prefix (mod 2^32) at its first tile, written by the scan
+    const uint32_t* poly0;    // m + 1: first global polygon of each job, then the total
+    uint32_t m;
+    static constexpr bool kSingle = false;
+    // the last j with start[j] <= x (jobs with empty ranges are skipped over)
+    template <class T>
+    __device__ __forceinline__ uint32_t last_le(const T* start, T x) const {
+        uint32_t lo = 0, hi = m;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(start + mid) <= x) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ uint32_t find_tile(uint64_t wt) const { return __ldg(tile_job + wt); }
+    __device__ __forceinline__ uint32_t find_poly(uint32_t gp) const { return last_le(poly0, gp); }
+    __device__ __forceinline__ const JobDesc& job(uint32_t j) const { return d[j]; }
+    __device__ __forceinline__ uint32_t job_base(uint32_t j) const { return base[j]; }
+};
+
+// Join mode of a kernel instance: fixed, or read from each job (batched form).
+enum : int { kModeApprox = 0, kModeExact = 1, kModeAny = 2 };
+
+template <int MODE>
+__device__ __forceinline__ bool job_exact(const JobDesc& J) {
+    return MODE == kModeAny ? J.exact != 0u : MODE == kModeExact;
+}
+
+// The work space of the join kernels (global tile and point spaces).
+struct JoinScratch {
+    uint64_t* entries;        // tagged trie entry per point
+    uint32_t* tile_count;     // pairs per warp tile (exact: true hits, then + passing candidates)
+    uint32_t* tile_prefix;    // exclusive scan of tile_count (mod 2^32)
+    uint32_t* qbase;          // exact: first queue slot of each point with candidates
+    uint2* queue;             // exact: (job-local point, global polygon) candidates
+    uint8_t* pass;            // exact: PIP result per queue slot
+    uint32_t* queue_len;
+    uint32_t* poly_count;     // exact: candidates per global polygon
+    uint64_t queue_cap;
+    const uint64_t* scan_err; // error bits of the scans, merged into each job's status
+};
+
+// ---------------------------------------------------------------------------
+// join kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_zero(uint64_t* __restrict__ a, uint64_t na, uint64_t* __restrict__ b, uint64_t nb);
+
+// Step 1 of the join (Listing "Probe Adaptive Cell Trie" per point) for
+// warp tile wt = tile lt of job J: cell id + walk for every point of the tile (32 lanes x PPT
+// points, point base + lane + 32 k, so the 16-byte loads coalesce), the
+// tagged entry stored per point.  Approximate jobs count every reference of
+// the tile; exact jobs count the true hits and queue the candidate
+// references (warp ballot: one atomic reserves a warp's queue slots).  No
+// tile waits on another.
+template <int PPT, int MODE>
+__device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
+                                           const uint64_t* s_root, uint64_t wt, uint64_t lt, uint32_t gpoly0,
+                                           const JoinScratch& S) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t base = lt * (32 * PPT);
+    const uint64_t gbase = wt * (32 * PPT);
+    double lat[PPT], lng[PPT];
+    bool valid[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        valid[k] = p < J.n;
+        const double2 q = valid[k] ? __ldcs(J.pts + p) : make_double2(0.0, 0.0);   // streamed once
+        lat[k] = q.x;
+        lng[k] = q.y;
+    }
+    uint64_t e[PPT];
+    uint32_t fallbacks = 0;
+    warp_count(probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, valid, e, &J.status[1], &fallbacks),
+               &J.status[3]);
+    warp_count(fallbacks, &J.counters[0]);
+    const bool exact = job_exact<MODE>(J);
+    uint32_t nc[PPT], csum = 0, tsum = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        uint32_t nt;
+        entry_counts(J.X, e[k], &nt, &nc[k]);
+        tsum += exact ? nt : nt + nc[k];
+        csum += exact ? nc[k] : 0u;
+        S.entries[gbase + lane + 32 * k] = e[k];        // 0 for padding lanes
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(kFull, tsum, o);
+    if (lane == 0) S.tile_count[wt] = tsum;
+    if (MODE == kModeApprox || !exact) return;
+    const uint32_t x = warp_incl_scan(csum);
+    const uint32_t wtotal = __shfl_sync(kFull, x, 31);
+    if (wtotal == 0) return;
+    uint32_t wbase = 0;
+    if (lane == 0) {
+        wbase = atomicAdd(S.queue_len, wtotal);
+        atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
+    }
+    wbase = __shfl_sync(kFull, wbase, 0);
+    uint64_t q = (uint64_t)wbase + x - csum;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!nc[k]) continue;
+        const uint32_t p = (uint32_t)(base + lane + 32 * k);
+        S.qbase[gbase + lane + 32 * k] = (uint32_t)q;
+        const uint64_t ek = e[k];
+        const uint32_t tag = (uint32_t)(ek & 3ull);
+        const uint32_t* Cc = nullptr;
+        if (tag == 3) {
+            const uint32_t off = payload_of(ek, 0);
+            Cc = J.X.lut + off + 2 + __ldg(J.X.lut + off);
+        }
+        for (uint32_t t = 0, r = 0; t < nc[k]; ++r) {
+            uint32_t poly;
+            if (tag == 3) {
+                poly = __ldg(Cc + r);
+            } else {
+                const uint32_t pl = payload_of(ek, (int)r);
+                if (pl & 1u) continue;          // a true reference
+                poly = pl >> 1;
+            }
+            ++t;
+            const uint32_t gp = gpoly0 + poly;
+            if (q < S.queue_cap) {
+                S.queue[q] = make_uint2(p, gp);
+                atomicAdd(&S.poly_count[gp], 1u);
+            } else {
+                atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrQueueOverflow);
+            }
+            ++q;
+        }
+    }
+}
+
+// The plain join runs one warp per tile of its single job (job offsets are
+// compile-time zero).  The batched form runs one warp per tile of the global
+// tile space, or a persistent grid striding over it.
+template <int PPT, class Src, int MODE>
+__global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
+    k_probe(const Src src, uint64_t T, const JoinScratch S) {
+    __shared__ __align__(16) uint16_t s_hlut[1024];
+    __shared__ __align__(16) uint64_t s_rootbuf[256];
+    __shared__ DevFace s_faces[6];
+    const uint64_t* s_root = cta_setup(Src::kSingle ? &src.job(0).X : nullptr, s_hlut, s_faces, s_rootbuf);
+    __syncthreads();
+    uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if constexpr (Src::kSingle) {
+        if (wt < T) probe_tile<PPT, MODE>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S);
+    } else if ((uint64_t)gridDim.x * kWarpsPerBlock >= T) {     // one warp per tile
+        if (wt < T) {
+            const JobDesc& J = src.job(src.find_tile(wt));
+            probe_tile<PPT, MODE>(J, J.X.faces, s_hlut, nullptr, wt, wt - J.tile0, J.poly0, S);
+        }
+    } else {                                                     // persistent grid
+        for (; wt < T; wt += (uint64_t)gridDim.x * kWarpsPerBlock) {
+            const JobDesc& J = src.job(src.find_tile(wt));
+            probe_tile<PPT, MODE>(J, J.X.faces, s_hlut, nullptr, wt, wt - J.tile0, J.poly0, S);
+        }
+    }
+}
+
+// Exclusive scan of the tile counts over the whole tile space: CTA chunks of
+// 16 x 256 counts chained by the decoupled look-back (a few hundred chunks,
+// so the look-back is short).  Prefixes are kept mod 2^32: a job's offsets are
+// differences of two prefixes of its own tiles.
+// With tile_job (batched form), the prefix at each job's first tile is also
+// written to job_base[job].
+__global__ void k_scan_counts(const uint32_t* __restrict__ tile_count, uint64_t m, uint32_t* __restrict__ tile_prefix,
+                              uint64_t* __restrict__ chunks, uint32_t* __restrict__ chunk_counter,
+                              uint64_t* __restrict__ err, const uint16_t* __restrict__ tile_job,
+                              uint32_t* __restrict__ job_base);
+
+// Exclusive scans of the per-polygon candidate counts and of the per-polygon
+// refine chunks (kPipBlock candidates each), as one packed 64-bit scan
+// (count in the low 32 bits, chunks above) chained by the look-back.  The
+// CTA that finishes last writes the totals.
+__global__ void k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_polys,
+                            uint32_t* __restrict__ poly_start, uint32_t* __restrict__ cursor,
+                            uint32_t* __restrict__ chunk_start, uint32_t* __restrict__ n_chunks,
+                            uint64_t* __restrict__ chunks, uint32_t* __restrict__ chunk_counter,
+                            uint64_t* __restrict__ err);
+
+// Groups the candidate queue by polygon (counting-sort scatter).
+__global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ queue_len,
+                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted, uint64_t queue_cap,
+                          uint32_t n_polys);
+
+// Refine (Listing "Join" step 3 on candidate references): ST_Covers of
+// (point, polygon) candidates, grouped by polygon.  Per chunk of one
+// polygon's candidates, the polygon's FP32 local vertices are staged in
+// shared memory and every thread tests its candidate against the same edge at
+// the same time (shared-memory broadcast).  The test is the certified FP32
+// one (covers_certified); an undecided candidate (within the error bounds of
+// a vertex or an edge) is recomputed in FP64 (covers_fp64), as is every
+// candidate of a polygon too large for the FP32 local frame.  A passing
+// candidate adds one to its tile's pair count.
+template <class Src>
+__global__ void __launch_bounds__(kPipBlock) k_pip(const Src src, uint32_t tile_points, uint32_t P,
+                                                   const uint2* __restrict__ queue, const uint32_t* __restrict__ sorted,
+                                                   const uint32_t* __restrict__ poly_start,
+                                                   const uint32_t* __restrict__ chunk_start,
+                                                   const uint32_t* __restrict__ n_chunks, uint8_t* __restrict__ pass,
+                                                   uint32_t* __restrict__ tile_count) {
+    __shared__ F2 s_lv[kPipSmemVerts];
+    const uint32_t total = *n_chunks;
+    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+        // global polygon of chunk c: the last with chunk_start <= c
+        uint32_t lo = 0, hi = P;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (chunk_start[mid] <= c) lo = mid; else hi = mid;
+        }
+        const uint32_t gp = lo;
+        const JobDesc& J = src.job(src.find_poly(gp));
+        const uint32_t poly = gp - J.poly0;
+        const uint32_t q0 = poly_start[gp] + (c - chunk_start[gp]) * kPipBlock;
+        const uint32_t q1 = min(q0 + kPipBlock, poly_start[gp + 1]);
+        const uint32_t item = q0 + threadIdx.x;
+        const uint32_t v0 = J.X.poly_off[poly], V = J.X.poly_off[poly + 1] - v0;
+        const PolyLocal L = J.X.poly_local[poly];
+        const bool certified = J.X.model.uv_enabled && L.ok && V <= (uint32_t)kPipSmemVerts;
+        __syncthreads();
+        if (certified)
+            for (uint32_t t = threadIdx.x; t < V; t += blockDim.x) s_lv[t] = J.X.poly_luv[v0 + t];
+        __syncthreads();
+        if (item < q1) {
+            const uint32_t qi = sorted[item];
+            const uint2 qp = queue[qi];
+            const double2 pt = J.pts[qp.x];
+            int r = -1;
+            float pu, pv, dp;
+            if (certified && model_uv_local(J.X.model, pt.x, pt.y, L, &pu, &pv, &dp))
+                r = covers_certified(s_lv, V, L, pu, pv, dp);
+            if (r < 0) {
+                r = covers_fp64(J.X, poly, pt.x, pt.y) ? 1 : 0;
+                atomicAdd((unsigned long long*)&J.counters[1], 1ull);
+            }
+            pass[qi] = (uint8_t)r;
+            if (r) atomicAdd(&tile_count[J.tile0 + qp.x / tile_points], 1u);
+        }
+    }
+}
+
+// Last step of the join (Listing "Join", add to pairs) for warp tile wt =
+// tile lt of job j: offsets and ids of the tile from its stored entries and
+// its prefix (less the prefix at the job's first tile), ids ascending
+// per point (true and candidate references merged; exact jobs keep the
+// candidates that passed).  The job's last tile writes offsets[n] and nnz.
+template <int PPT, int MODE, class Src>
+__device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t wt, const JoinScratch& S) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t gbase = wt * (32 * PPT);
+    // the stored entries and the tile prefix do not depend on the job, so
+    // their loads overlap the job lookup
+    uint64_t e[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) e[k] = __ldcs(S.entries + gbase + lane + 32 * k);
+    const uint32_t tprefix = S.tile_prefix[wt];
+    const JobDesc& J = src.job(j);
+    const bool exact = job_exact<MODE>(J);
+    const uint64_t base = (wt - J.tile0) * (32 * PPT);
+    uint32_t cnt[PPT], qb[PPT], ex[PPT], run = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        qb[k] = 0;
+        if (exact) {
+            cnt[k] = exact_count(J.X, e[k], S.qbase, gbase + lane + 32 * k, S.pass, S.queue_cap, &qb[k], J.status);
+            if (cnt[k] == 0xFFFFFFFFu) { cnt[k] = 0; e[k] = 0; }
+        } else {
+            uint32_t nt, nc;
+            entry_counts(J.X, e[k], &nt, &nc);
+            cnt[k] = nt + nc;
+        }
+        const uint32_t incl = warp_incl_scan(cnt[k]);
+        ex[k] = run + incl - cnt[k];
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    const uint64_t prefix = (uint64_t)(uint32_t)(tprefix - src.job_base(j));
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        if (p >= J.n) continue;
+        const uint64_t o = prefix + ex[k];
+        __stcs(J.offsets + p, (uint32_t)o);
+        if (!cnt[k]) continue;
+        if (o + cnt[k] > J.ids_cap) {
+            atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrIdsCapacity);
+            continue;
+        }
+        if (!exact) {
+            emit_all(J.X, e[k], J.ids, o);
+            continue;
+        }
+        const uint64_t ek = e[k];
+        const uint32_t tag = (uint32_t)(ek & 3ull);
+        uint64_t w = o;
+        uint32_t ci = 0;
+        if (tag == 1 || tag == 2) {
+            for (int t = 0; t < (int)tag; ++t) {
+                const uint32_t pl = payload_of(ek, t);
+                if (pl & 1u) J.ids[w++] = pl >> 1;
+                else if (S.pass[qb[k] + ci++]) J.ids[w++] = pl >> 1;
+            }
+        } else if (tag == 3) {
+            const uint32_t off = payload_of(ek, 0);
+            const uint32_t nt = __ldg(J.X.lut + off);
+            const uint32_t* Tt = J.X.lut + off + 1;
+            const uint32_t nc = __ldg(J.X.lut + off + 1 + nt);
+            const uint32_t* Cc = J.X.lut + off + 2 + nt;
+            uint32_t a = 0, b = 0;
+            while (a < nt || b < nc) {
+                const uint32_t ta = a < nt ? __ldg(Tt + a) : 0xFFFFFFFFu;
+                const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
+                if (ta < cb) { J.ids[w++] = ta; ++a; }
+                else { if (S.pass[qb[k] + b]) J.ids[w++] = cb; ++b; }
+            }
+        }
+    }
+    if (base + 32 * PPT >= J.n && lane == 0) {
+        J.offsets[J.n] = (uint32_t)(prefix + run);
+        J.status[0] = prefix + run;
+        const uint64_t g = *S.scan_err;
+        if (g) atomicOr((unsigned long long*)&J.status[1], (unsigned long long)g);
+    }
+}
+
+template <int PPT, class Src, int MODE>
+__global__ void __launch_bounds__(kJoinBlock) k_emit(const Src src, uint64_t T, const JoinScratch S) {
+    uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if constexpr (Src::kSingle) {
+        if (wt < T) emit_tile<PPT, MODE>(src, 0, wt, S);
+    } else if ((uint64_t)gridDim.x * kWarpsPerBlock >= T) {     // one warp per tile
+        if (wt < T) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S);
+    } else {                                                     // persistent grid
+        for (; wt < T; wt += (uint64_t)gridDim.x * kWarpsPerBlock) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S);
+    }
+}
+
+}  // namespace agj

@@ -62,6 +62,11 @@ class Requirements(C.Structure):
     _fields_ = [("ids_capacity", C.c_uint64), ("scratch_bytes", C.c_uint64)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("points_per_lane", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("no_graph", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -96,6 +101,11 @@ def lib():
             "agj_cell_ids_host": (i32, [P, u64, P]),
             "agj_fast_ids_host": (i32, [P, P, u64, P, P]),
             "agj_covers_certified_host": (i32, [P, P, P, u64, P]),
+            "agj_batch_create": (i32, [P, P, u32, P, P]),
+            "agj_batch_run": (i32, [P, P, P, P]),
+            "agj_batch_device_bytes": (u64, [P]),
+            "agj_batch_free": (None, [P]),
+            "agj_join_batched": (i32, [P, P, P, u32, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -304,6 +314,70 @@ def join_host(index: Index, points: np.ndarray, pairs: Pairs, staging, h_offsets
                              int(h_ids.shape[0]), C.byref(nnz), _stream_ptr(stream))
     _check(rc, "agj_join_host")
     return int(nnz.value)
+
+
+class Batch:
+    """A batched-join plan (agj_batch_create) for fixed (index, point count)
+    jobs; run() joins one point batch per job into one Pairs per job."""
+
+    def __init__(self, indexes, ns, points_per_lane: int = 0, ctas_per_sm: int = 0, graph: bool = True):
+        m = len(indexes)
+        assert len(ns) == m
+        self.indexes = list(indexes)
+        self.ns = [int(x) for x in ns]
+        self.opts = (int(points_per_lane), int(ctas_per_sm), bool(graph))
+        hs = (C.c_void_p * max(m, 1))(*[ix.handle for ix in self.indexes])
+        nn = (C.c_uint64 * max(m, 1))(*self.ns)
+        o = BatchOpts(int(points_per_lane), int(ctas_per_sm), 0 if graph else 1, 0)
+        h = C.c_void_p()
+        _check(lib().agj_batch_create(hs, nn, m, C.byref(o), C.byref(h)), "agj_batch_create")
+        self._h = h
+
+    def device_bytes(self) -> int:
+        return int(lib().agj_batch_device_bytes(self._h))
+
+    def pairs(self, device=None) -> list:
+        """One Pairs per job, sized for that job."""
+        return [Pairs(ix, n, device=device) for ix, n in zip(self.indexes, self.ns)]
+
+    def run(self, points, pairs: list, stream=None) -> list:
+        import torch
+        m = len(self.indexes)
+        assert len(points) == m and len(pairs) == m
+        for p, n in zip(points, self.ns):
+            assert p.is_cuda and p.dtype == torch.float64 and p.is_contiguous() and p.shape[0] == n
+        pp = (C.c_void_p * max(m, 1))(*[C.c_void_p(p.data_ptr()) for p in points])
+        arr = (PairsC * max(m, 1))(*[q.c for q in pairs])
+        for q, n in zip(pairs, self.ns):
+            q.n = n
+        _check(lib().agj_batch_run(self._h, pp, _stream_ptr(stream), arr), "agj_batch_run")
+        return pairs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().agj_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def join_batched(indexes, points, pairs: list | None = None, stream=None) -> list:
+    """One-shot batched join (agj_join_batched): synchronises the stream."""
+    m = len(indexes)
+    if pairs is None:
+        pairs = [Pairs(ix, p.shape[0], device=p.device) for ix, p in zip(indexes, points)]
+    hs = (C.c_void_p * max(m, 1))(*[ix.handle for ix in indexes])
+    pp = (C.c_void_p * max(m, 1))(*[C.c_void_p(p.data_ptr()) for p in points])
+    nn = (C.c_uint64 * max(m, 1))(*[int(p.shape[0]) for p in points])
+    arr = (PairsC * max(m, 1))(*[q.c for q in pairs])
+    for q, p in zip(pairs, points):
+        q.n = int(p.shape[0])
+    _check(lib().agj_join_batched(hs, pp, nn, m, _stream_ptr(stream), arr), "agj_join_batched")
+    return pairs
 
 
 def supercover(cells, refs):

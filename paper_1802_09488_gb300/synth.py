@@ -318,3 +318,85 @@ def c2_city(n_points: int = 100_000_000, n_train: int | None = None) -> Workload
         n_train = max(n_points // 100, 1000)
     train = points_mixture(n_train, BOX_CITY, seed=4, dist_seed=3)
     return Workload("c2-city-300polys", polys, pts, 4.0, train)
+
+
+def scale_about_centroid(polys: list, seed: int, lo: float, hi: float) -> list:
+    """Each polygon scaled about its vertex centroid (in local metres) by a
+    factor drawn from U[lo, hi]: a homothety keeps a simple ring simple, and
+    factors above 1 make neighbours of a tiling overlap, below 1 open gaps."""
+    rng = np.random.default_rng([seed, 3])
+    f = rng.uniform(lo, hi, len(polys))
+    out = []
+    for k, p in enumerate(polys):
+        c = p.mean(axis=0)
+        out.append(np.ascontiguousarray(c + f[k] * (p - c)))
+    return out
+
+
+def c3_fine_polygons(n_polys: int = 40_000, seed: int = 5) -> list:
+    """n_polys small polygons (4-60 vertices) from a Voronoi tessellation of
+    the city box over a density-skewed seed field (the mixture), each scaled
+    about its centroid by U[0.85, 1.25] so that a point hits 0-3 polygons."""
+    box = BOX_CITY
+    rng = np.random.default_rng([seed, 2])
+    seeds = mixture_xy(n_polys, box, mixture_params(box, seed), rng)
+    polys = voronoi_tiling(n_polys, box, seed=seed, vmin=4, vmax=60, seeds_xy=seeds)
+    return scale_about_centroid(polys, seed, 0.85, 1.25)
+
+
+def c3_fine(n_points: int = 100_000_000, n_polys: int = 40_000, n_train: int | None = None) -> Workload:
+    """Fine polygons (c3_fine_polygons) with mixture points (seed 6, the
+    polygon field's clusters); eps = 1 m (also run at 10 m); exact index
+    trained on a 1 % sample (seed 7)."""
+    polys = c3_fine_polygons(n_polys)
+    pts = points_mixture(n_points, BOX_CITY, seed=6, dist_seed=5)
+    if n_train is None:
+        n_train = max(n_points // 100, 1000)
+    train = points_mixture(n_train, BOX_CITY, seed=7, dist_seed=5)
+    return Workload(f"c3-fine-{n_polys}polys", polys, pts, 1.0, train)
+
+
+@dataclass
+class Job:
+    """One (polygon set, point batch) job of the batched form."""
+    polygons: list
+    points: np.ndarray
+    exact: bool
+    eps_m: float
+    train: np.ndarray | None
+
+
+def batched_jobs(m: int = 64, seed: int = 11, polys: tuple[int, int] = (5, 40_000),
+                 points: tuple[int, int] = (1_000, 10_000_000), exact_every: int = 2) -> list:
+    """m jobs with polygon counts and point counts drawn log-uniform from the
+    given ranges (per-job seeds).  A set of at most 16 polygons is built as
+    the tiny workload (8-64 vertices, 40 km box, uniform points), one of at
+    most 1000 as the city one (20-400 vertices, mixture points), a larger one
+    as the fine one (4-60 vertices, skewed seed field, overlaps).  Every
+    exact_every-th job is exact (trained on 1 % of its own points' field),
+    the others approximate with eps 4 m."""
+    rng = np.random.default_rng([seed, 4])
+    n_polys = np.exp(rng.uniform(math.log(polys[0]), math.log(polys[1]), m)).round().astype(int)
+    n_pts = np.exp(rng.uniform(math.log(points[0]), math.log(points[1]), m)).round().astype(int)
+    jobs = []
+    for j in range(m):
+        s = 1000 * seed + j
+        k = int(n_polys[j])
+        if k <= 16:
+            box = BOX_C1
+            pl = voronoi_tiling(k, box, seed=s, vmin=8, vmax=64)
+            pts = points_uniform(int(n_pts[j]), box, seed=s + 1)
+            tr = points_uniform(max(int(n_pts[j]) // 100, 100), box, seed=s + 2)
+        elif k <= 1000:
+            box = BOX_CITY
+            pl = voronoi_tiling(k, box, seed=s, vmin=20, vmax=400)
+            pts = points_mixture(int(n_pts[j]), box, seed=s + 1)
+            tr = points_mixture(max(int(n_pts[j]) // 100, 100), box, seed=s + 2, dist_seed=s + 1)
+        else:
+            box = BOX_CITY
+            pl = c3_fine_polygons(k, seed=s)
+            pts = points_mixture(int(n_pts[j]), box, seed=s + 1, dist_seed=s)
+            tr = points_mixture(max(int(n_pts[j]) // 100, 100), box, seed=s + 2, dist_seed=s)
+        exact = exact_every > 0 and j % exact_every == exact_every - 1
+        jobs.append(Job(pl, pts, exact, 4.0, tr if exact else None))
+    return jobs
