@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "points joined/sec at 1 GB300 (approx eps and exact) vs plain join; p50/p99 latency"
 # approx: k_zero, k_probe_approx, k_scan_counts, k_emit_approx
 # exact:  k_zero, k_probe_exact, k_poly_scan, k_scatter, k_pip, k_scan_counts, k_emit_exact
-LAUNCHES_PER_STEP = {"approx": 4, "exact": 7}
+LAUNCHES_PER_STEP = {"approx": 4, "exact": 8}
 
 
 def parse():
@@ -264,7 +264,7 @@ def main():
                    "k_scan_counts": [ev[0][1].elapsed_time(ev[0][2]) for ev in stage_ev],
                    "k_emit_approx": [ev[0][2].elapsed_time(ev[0][3]) for ev in stage_ev]},
         "exact": {"k_probe_exact": [ev[1][0].elapsed_time(ev[1][1]) for ev in stage_ev],
-                  "refine (k_poly_scan + k_scatter + k_pip)": [ev[1][1].elapsed_time(ev[1][2]) for ev in stage_ev],
+                  "refine (k_count + k_poly_scan + k_scatter + k_pip)": [ev[1][1].elapsed_time(ev[1][2]) for ev in stage_ev],
                   "csr (k_scan_counts + k_emit_exact)": [ev[1][2].elapsed_time(ev[1][3]) for ev in stage_ev]},
     }
     total_ms = step_ev[0][0].elapsed_time(step_ev[-1][1])

@@ -123,7 +123,8 @@ int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, 
     if (ctas_per_sm < 0 || ctas_per_sm > 8) return AGJ_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
-    uint64_t T = 0, P = 0, Q = 0;
+    uint64_t T = 0, P = 0;
+    uint32_t mcr = 1;    // most candidate references of a point over the exact jobs
     bool any_exact = false;
     Batch* B = new (std::nothrow) Batch();
     if (!B) return AGJ_ENOMEM;
@@ -141,17 +142,23 @@ int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, 
         if (ids >= 0xFFFFFFFFull) { delete B; return AGJ_ECAPACITY; }
         B->tile0.push_back(T);
         B->poly0.push_back((uint32_t)P);
+        // whole CTAs per job: a CTA's tiles share one job
         T += (n[j] + 32 * ppt - 1) / (32 * ppt);
+        T = (T + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
         if (x->mode == AGJ_EXACT) {
             any_exact = true;
             P += x->n_polys;
-            Q += n[j] * std::max<uint64_t>(x->stats.max_cand_refs, 1);
+            mcr = std::max<uint32_t>(mcr, x->stats.max_cand_refs);
         }
     }
-    if (P >= 0xFFFFFFFFull || Q >= 0xFFFFFFFFull || T >= (1ull << 36)) { delete B; return AGJ_ECAPACITY; }
+    const uint32_t slots = 32u * (uint32_t)ppt * mcr;
+    if (P >= 0xFFFFFFFFull || (any_exact && T * slots >= 0xFFFFFFFFull) || T >= (1ull << 36)) {
+        delete B;
+        return AGJ_ECAPACITY;
+    }
     B->tile0.push_back(T);
     B->poly0.push_back((uint32_t)P);
-    B->L = join_layout(T * 32 * ppt, T, any_exact, Q, P);
+    B->L = join_layout(T * 32 * ppt, T, any_exact, any_exact ? slots : 0u, P);
     std::vector<uint16_t> tile_job(T);
     for (uint32_t j = 0; j < m; ++j)
         std::fill(tile_job.begin() + B->tile0[j], tile_job.begin() + B->tile0[j + 1], (uint16_t)j);

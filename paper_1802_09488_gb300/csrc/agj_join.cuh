@@ -24,20 +24,22 @@ JobDesc make_job(const Index& X, const double* d_points, uint64_t n, agj_pairs* 
 inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 // Work space of one join launch sequence, as byte offsets into one buffer:
-//   [header 256 B: u32 tile-scan chunk counter, u32 queue length,
+//   [header 256 B: u32 tile-scan chunk counter, u32 unused,
 //    u32 refine chunks, u32 polygon-scan chunk counter,
 //    u64 FP64 cell-id fallbacks, u64 FP64 refine fallbacks, u64 scan errors]
 //   [tile-scan chunk states] [exact: polygon-scan chunk states,
 //    per-polygon candidate counts]
 //   -- the part zeroed before every launch sequence --
 //   [entries u64 per point] [tile counts u32] [tile prefixes u32]
-//   then, with exact jobs, the queue bases, the candidate queue, its pass
-//   bytes, its polygon order and the per-polygon segments
+//   then, with exact jobs, the per-tile candidate counts, the candidate
+//   queue (a region of tile_slots per tile), its pass bytes, its polygon
+//   order and the per-polygon segments
 struct JoinLayout {
     uint64_t chunks = 0, pchunks = 0, pcount = 0, zero_end = 0;
     uint64_t entries = 0, tcount = 0, tprefix = 0;
-    uint64_t qbase = 0, queue = 0, pass = 0, sorted = 0, pstart = 0, cursor = 0, cstart = 0, total = 0;
+    uint64_t tcand = 0, queue = 0, pass = 0, sorted = 0, pstart = 0, cursor = 0, cstart = 0, total = 0;
     uint64_t n_points = 0, n_tiles = 0, n_chunks = 0, n_pchunks = 0, queue_cap = 0, n_polys = 0;
+    uint32_t tile_slots = 0;
     bool exact = false;
 };
 
@@ -47,10 +49,9 @@ constexpr uint64_t kHdrScanErr = 4;
 constexpr uint64_t kPolyScanPerCta = 256 * 4;
 
 // n_points / n_tiles: sizes of the (tile-padded) global point space and of
-// the tile space; exact: some
-// job refines; queue_cap: candidate queue slots; n_polys: polygons of the
-// exact jobs.
-inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, uint64_t queue_cap, uint64_t n_polys) {
+// the tile space; exact: some job refines; tile_slots: queue slots per tile;
+// n_polys: polygons of the exact jobs.
+inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, uint32_t tile_slots, uint64_t n_polys) {
     JoinLayout L;
     L.n_points = n_points;
     L.n_tiles = n_tiles;
@@ -61,7 +62,8 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
     o += align256(std::max<uint64_t>(L.n_chunks, 1) * 8);
     if (exact) {
         L.n_polys = n_polys;
-        L.queue_cap = queue_cap;
+        L.tile_slots = tile_slots;
+        L.queue_cap = n_tiles * tile_slots;
         L.n_pchunks = (n_polys + kPolyScanPerCta - 1) / kPolyScanPerCta;
         L.pchunks = o;
         o += align256(std::max<uint64_t>(L.n_pchunks, 1) * 8);
@@ -73,10 +75,10 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
     L.tcount = o; o += align256(n_tiles * 4 + 4);
     L.tprefix = o; o += align256(n_tiles * 4 + 4);
     if (exact) {
-        L.qbase = o; o += align256(n_points * 4 + 4);
-        L.queue = o; o += align256(queue_cap * 8 + 8);
-        L.pass = o; o += align256(queue_cap + 1);
-        L.sorted = o; o += align256(queue_cap * 4 + 4);
+        L.tcand = o; o += align256(n_tiles * 4 + 4);
+        L.queue = o; o += align256(L.queue_cap * 8 + 8);
+        L.pass = o; o += align256(L.queue_cap + 1);
+        L.sorted = o; o += align256(L.queue_cap * 4 + 4);
         L.pstart = o; o += align256((n_polys + 1) * 4);
         L.cursor = o; o += align256((n_polys + 1) * 4);
         L.cstart = o; o += align256((n_polys + 1) * 4);
@@ -87,16 +89,14 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
 
 inline JoinScratch join_scratch(const JoinLayout& L, char* sc) {
     JoinScratch S;
-    uint32_t* hdr = reinterpret_cast<uint32_t*>(sc);
     S.entries = reinterpret_cast<uint64_t*>(sc + L.entries);
     S.tile_count = reinterpret_cast<uint32_t*>(sc + L.tcount);
     S.tile_prefix = reinterpret_cast<uint32_t*>(sc + L.tprefix);
-    S.qbase = L.exact ? reinterpret_cast<uint32_t*>(sc + L.qbase) : nullptr;
     S.queue = L.exact ? reinterpret_cast<uint2*>(sc + L.queue) : nullptr;
     S.pass = L.exact ? reinterpret_cast<uint8_t*>(sc + L.pass) : nullptr;
-    S.queue_len = hdr + 1;
+    S.tile_cand = L.exact ? reinterpret_cast<uint32_t*>(sc + L.tcand) : nullptr;
     S.poly_count = L.exact ? reinterpret_cast<uint32_t*>(sc + L.pcount) : nullptr;
-    S.queue_cap = L.queue_cap;
+    S.tile_slots = L.tile_slots;
     S.scan_err = reinterpret_cast<const uint64_t*>(sc) + kHdrScanErr;
     return S;
 }
@@ -132,13 +132,15 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
     mark(1);
     const bool refine = MODE != kModeApprox && L.exact && L.n_polys;
     if (refine && L.n_tiles) {
+        k_count<<<G.sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, S.poly_count,
+                                          (uint32_t)L.n_polys);
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
             S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.pstart),
             reinterpret_cast<uint32_t*>(sc + L.cursor), reinterpret_cast<uint32_t*>(sc + L.cstart), hdr + 2,
             reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3, reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
-        k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.queue_len, reinterpret_cast<uint32_t*>(sc + L.cursor),
-                                            reinterpret_cast<uint32_t*>(sc + L.sorted), L.queue_cap,
-                                            (uint32_t)L.n_polys);
+        k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots,
+                                            reinterpret_cast<uint32_t*>(sc + L.cursor),
+                                            reinterpret_cast<uint32_t*>(sc + L.sorted), (uint32_t)L.n_polys);
         k_pip<Src><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, (uint32_t)L.n_polys, S.queue,
                                                     reinterpret_cast<const uint32_t*>(sc + L.sorted),
                                                     reinterpret_cast<const uint32_t*>(sc + L.pstart),

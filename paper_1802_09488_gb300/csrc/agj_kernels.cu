@@ -141,42 +141,108 @@ __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ 
     }
 }
 
-// Each CTA takes chunks of kScatterChunk queue items, counts them per polygon
-// with shared-memory atomics, reserves each polygon's slots with one global
-// atomic per polygon and chunk, and writes the items' queue indices there.
-// With more polygons than shared counters, every item reserves its slot
-// globally.
-constexpr int kScatterChunk = 4096;
+// The candidates queued by a chunk of kChunkTiles tiles (tile t holds
+// tile_cand[t] items from slot t x tile_slots) are numbered densely: the
+// chunk's counts are scanned into s_off, and item i lives in the last tile
+// whose offset is <= i.  Returns the chunk's item count (after a barrier).
+constexpr int kChunkTiles = 512;
+__device__ __forceinline__ uint32_t chunk_number(const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
+                                                 uint32_t tile_slots, uint64_t c0, uint32_t* s_off, uint32_t* s_warp) {
+    constexpr int kPer = kChunkTiles / 256;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint64_t t = c0 + (uint64_t)threadIdx.x * kPer + k;
+        v[k] = t < n_tiles ? min(tile_cand[t], tile_slots) : 0u;
+        sum += v[k];
+    }
+    uint32_t total;
+    uint32_t o = block_excl_scan<256>(sum, &total, s_warp);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        s_off[threadIdx.x * kPer + k] = o;
+        o += v[k];
+    }
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ uint64_t chunk_slot(const uint32_t* s_off, uint64_t c0, uint32_t tile_slots, uint32_t i) {
+    uint32_t lo = 0, hi = kChunkTiles;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return (c0 + lo) * tile_slots + (i - s_off[lo]);
+}
+
+// Candidates per polygon: a shared-memory histogram per chunk, added to the
+// global counts with one atomic per polygon and chunk (global atomics per
+// item beyond kCountMaxPolys polygons, where they rarely collide).
+constexpr int kCountMaxPolys = 8192;
+__global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand,
+                                               uint64_t n_tiles, uint32_t tile_slots, uint32_t* __restrict__ poly_count,
+                                               uint32_t n_polys) {
+    __shared__ uint32_t s_cnt[kCountMaxPolys];
+    __shared__ uint32_t s_off[kChunkTiles];
+    __shared__ uint32_t s_warp[8];
+    const bool shared_counts = n_polys <= (uint32_t)kCountMaxPolys;
+    if (shared_counts)
+        for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) s_cnt[p] = 0;
+    for (uint64_t c0 = (uint64_t)blockIdx.x * kChunkTiles; c0 < n_tiles; c0 += (uint64_t)gridDim.x * kChunkTiles) {
+        const uint32_t total = chunk_number(tile_cand, n_tiles, tile_slots, c0, s_off, s_warp);
+        for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+            const uint32_t poly = queue[chunk_slot(s_off, c0, tile_slots, i)].y;
+            if (shared_counts) atomicAdd(&s_cnt[poly], 1u);
+            else atomicAdd(&poly_count[poly], 1u);
+        }
+        __syncthreads();
+    }
+    if (shared_counts) {
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x)
+            if (s_cnt[p]) atomicAdd(&poly_count[p], s_cnt[p]);
+    }
+}
+
+// Groups the queued candidates by polygon (counting-sort scatter of queue
+// slots): per chunk, the items are counted per polygon in shared memory,
+// each polygon's slots are reserved with one global atomic, and the items
+// are written there.  With more polygons than shared counters, every item
+// reserves its slot globally.
 constexpr int kScatterMaxPolys = 4096;
-__global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ queue_len,
-                                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted,
-                                                 uint64_t queue_cap, uint32_t n_polys) {
+__global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand,
+                                                 uint64_t n_tiles, uint32_t tile_slots, uint32_t* __restrict__ cursor,
+                                                 uint32_t* __restrict__ sorted, uint32_t n_polys) {
     __shared__ uint32_t s_cnt[kScatterMaxPolys];
     __shared__ uint32_t s_base[kScatterMaxPolys];
-    const uint64_t len = min((uint64_t)*queue_len, queue_cap);
-    if (n_polys > (uint32_t)kScatterMaxPolys) {
-        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-        for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < len; q += stride) {
-            const uint32_t pos = atomicAdd(&cursor[queue[q].y], 1u);
-            sorted[pos] = (uint32_t)q;
-        }
-        return;
-    }
-    for (uint64_t c0 = (uint64_t)blockIdx.x * kScatterChunk; c0 < len; c0 += (uint64_t)gridDim.x * kScatterChunk) {
-        const uint64_t c1 = min(c0 + kScatterChunk, len);
-        for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) s_cnt[p] = 0;
-        __syncthreads();
-        for (uint64_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) atomicAdd(&s_cnt[queue[q].y], 1u);
-        __syncthreads();
-        for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) {
-            const uint32_t c = s_cnt[p];
-            if (c) s_base[p] = atomicAdd(&cursor[p], c);
-            s_cnt[p] = 0;
-        }
-        __syncthreads();
-        for (uint64_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
-            const uint32_t poly = queue[q].y;
-            sorted[s_base[poly] + atomicAdd(&s_cnt[poly], 1u)] = (uint32_t)q;
+    __shared__ uint32_t s_off[kChunkTiles];
+    __shared__ uint32_t s_warp[8];
+    const bool shared_counts = n_polys <= (uint32_t)kScatterMaxPolys;
+    for (uint64_t c0 = (uint64_t)blockIdx.x * kChunkTiles; c0 < n_tiles; c0 += (uint64_t)gridDim.x * kChunkTiles) {
+        if (shared_counts)
+            for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) s_cnt[p] = 0;
+        const uint32_t total = chunk_number(tile_cand, n_tiles, tile_slots, c0, s_off, s_warp);
+        if (shared_counts) {
+            for (uint32_t i = threadIdx.x; i < total; i += blockDim.x)
+                atomicAdd(&s_cnt[queue[chunk_slot(s_off, c0, tile_slots, i)].y], 1u);
+            __syncthreads();
+            for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) {
+                const uint32_t c = s_cnt[p];
+                if (c) s_base[p] = atomicAdd(&cursor[p], c);
+                s_cnt[p] = 0;
+            }
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+                const uint64_t q = chunk_slot(s_off, c0, tile_slots, i);
+                const uint32_t poly = queue[q].y;
+                sorted[s_base[poly] + atomicAdd(&s_cnt[poly], 1u)] = (uint32_t)q;
+            }
+        } else {
+            for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+                const uint64_t q = chunk_slot(s_off, c0, tile_slots, i);
+                sorted[atomicAdd(&cursor[queue[q].y], 1u)] = (uint32_t)q;
+            }
         }
         __syncthreads();
     }
@@ -331,7 +397,8 @@ namespace {
 JoinLayout plain_layout(const Index& X, uint64_t n) {
     const uint64_t tiles = (n + 32 * kJoinPPT - 1) / (32 * kJoinPPT);
     const bool exact = X.mode == AGJ_EXACT;
-    return join_layout(tiles * 32 * kJoinPPT, tiles, exact, exact ? n * std::max<uint64_t>(X.stats.max_cand_refs, 1) : 0,
+    return join_layout(tiles * 32 * kJoinPPT, tiles, exact,
+                       exact ? 32u * kJoinPPT * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
                        exact ? X.n_polys : 0);
 }
 

@@ -334,23 +334,12 @@ __device__ __forceinline__ void emit_all(const DevIndex& X, uint64_t e, uint32_t
 }
 
 
-// Number of output pairs of one point of the exact join (true references
-// plus the candidates that passed the PIP); 0xFFFFFFFF flags a corrupt queue
-// position.
-__device__ __forceinline__ uint32_t exact_count(const DevIndex& X, uint64_t e, const uint32_t* qbase, uint64_t g,
-                                                const uint8_t* pass, uint64_t queue_cap, uint32_t* qb,
-                                                uint64_t* status) {
-    uint32_t nt, nc;
-    entry_counts(X, e, &nt, &nc);
-    *qb = 0;
-    if (!nc) return nt;
-    *qb = qbase[g];
-    if ((uint64_t)*qb + nc > queue_cap) {   // cannot happen: the queue holds every candidate
-        atomicOr((unsigned long long*)&status[1], (unsigned long long)kErrQueueOverflow);
-        return 0xFFFFFFFFu;
-    }
+// Number of output pairs of one point of the exact join: its true
+// references plus those of its nc candidates (queue slots qb .. qb + nc - 1)
+// that passed the PIP.
+__device__ __forceinline__ uint32_t exact_count(uint32_t nt, uint32_t nc, const uint8_t* pass, uint64_t qb) {
     uint32_t c = nt;
-    for (uint32_t t = 0; t < nc; ++t) c += pass[*qb + t];
+    for (uint32_t t = 0; t < nc; ++t) c += pass[qb + t];
     return c;
 }
 
@@ -388,12 +377,13 @@ __device__ __forceinline__ bool covers_fp64(const DevIndex& X, uint32_t poly, do
 // ---------------------------------------------------------------------------
 
 // One (index, points, output) job.  Its warp tiles are tile0 .. tile0 +
-// ceil(n / (32 PPT)) - 1 of the global tile space, and in exact mode its
+// ceil(n / (32 PPT)) - 1 of the global tile space (in the batched form its
+// range is padded to whole CTAs with tiles of no points), and in exact mode its
 // polygons poly0 .. poly0 + n_polys - 1 of the global polygon space of the
 // refine step.  Per-point work space (stored entries, queue bases) is
 // indexed by the tile-padded global point index wt * 32 PPT + lane + 32 k,
 // which needs no job lookup.
-struct JobDesc {
+struct __align__(16) JobDesc {
     DevIndex X;
     const double2* pts;
     uint32_t* offsets;        // n + 1
@@ -454,12 +444,11 @@ struct JoinScratch {
     uint64_t* entries;        // tagged trie entry per point
     uint32_t* tile_count;     // pairs per warp tile (exact: true hits, then + passing candidates)
     uint32_t* tile_prefix;    // exclusive scan of tile_count (mod 2^32)
-    uint32_t* qbase;          // exact: first queue slot of each point with candidates
-    uint2* queue;             // exact: (job-local point, global polygon) candidates
+    uint2* queue;             // exact: (job-local point, global polygon) candidates, tile_slots per tile
     uint8_t* pass;            // exact: PIP result per queue slot
-    uint32_t* queue_len;
-    uint32_t* poly_count;     // exact: candidates per global polygon
-    uint64_t queue_cap;
+    uint32_t* tile_cand;      // exact: candidates queued by each tile
+    uint32_t* poly_count;     // exact: candidates per global polygon (k_count)
+    uint32_t tile_slots;      // exact: queue slots per tile (32 PPT x most candidates of a point)
     const uint64_t* scan_err; // error bits of the scans, merged into each job's status
 };
 
@@ -511,22 +500,25 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(kFull, tsum, o);
     if (lane == 0) S.tile_count[wt] = tsum;
-    if (MODE == kModeApprox || !exact) return;
+    if (MODE == kModeApprox || S.tile_cand == nullptr) return;   // no exact job in the launch
+    // exact: the tile's candidates go to its own queue region, in point
+    // order (lane-major, then k), so no reservation is shared between tiles
     const uint32_t x = warp_incl_scan(csum);
     const uint32_t wtotal = __shfl_sync(kFull, x, 31);
-    if (wtotal == 0) return;
-    uint32_t wbase = 0;
     if (lane == 0) {
-        wbase = atomicAdd(S.queue_len, wtotal);
-        atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
+        S.tile_cand[wt] = wtotal;
+        if (wtotal) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
     }
-    wbase = __shfl_sync(kFull, wbase, 0);
-    uint64_t q = (uint64_t)wbase + x - csum;
+    if (wtotal == 0) return;
+    if (wtotal > S.tile_slots) {    // cannot happen: a point has at most the index's candidate references
+        if (lane == 0) atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrQueueOverflow);
+        return;
+    }
+    uint64_t q = wt * S.tile_slots + x - csum;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (!nc[k]) continue;
         const uint32_t p = (uint32_t)(base + lane + 32 * k);
-        S.qbase[gbase + lane + 32 * k] = (uint32_t)q;
         const uint64_t ek = e[k];
         const uint32_t tag = (uint32_t)(ek & 3ull);
         const uint32_t* Cc = nullptr;
@@ -544,41 +536,69 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
                 poly = pl >> 1;
             }
             ++t;
-            const uint32_t gp = gpoly0 + poly;
-            if (q < S.queue_cap) {
-                S.queue[q] = make_uint2(p, gp);
-                atomicAdd(&S.poly_count[gp], 1u);
-            } else {
-                atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrQueueOverflow);
-            }
-            ++q;
+            S.queue[q++] = make_uint2(p, gpoly0 + poly);
         }
     }
 }
 
+// Stages job J's face table and (with the fast model) the model face's root
+// node in shared memory.  Called by the whole CTA for a CTA-uniform job.
+// (The descriptor itself stays in global memory: read through the cache, its
+// fields are reloaded where needed instead of being held in registers.)
+__device__ __forceinline__ const uint64_t* cta_stage_job(const JobDesc& J, DevFace* s_faces, uint64_t* s_root) {
+    __syncthreads();   // the previous job's tiles are done with the staged copy
+    const DevIndex& X = J.X;
+    if (threadIdx.x < 6) s_faces[threadIdx.x] = X.faces[threadIdx.x];
+    const uint64_t* root = nullptr;
+    if (X.model.enabled && X.faces[X.model.face].root != kNoRootDev) {
+        const ulonglong2* r = reinterpret_cast<const ulonglong2*>(X.nodes + (uint64_t)X.faces[X.model.face].root * 256);
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) reinterpret_cast<ulonglong2*>(s_root)[t] = __ldg(r + t);
+        root = s_root;
+    }
+    __syncthreads();
+    return root;
+}
+
 // The plain join runs one warp per tile of its single job (job offsets are
-// compile-time zero).  The batched form runs one warp per tile of the global
-// tile space, or a persistent grid striding over it.
+// compile-time zero).  The batched form aligns every job's tile range to
+// whole CTAs, so the 8 tiles a CTA takes at a time belong to one job, whose
+// face table and root node the CTA stages in shared memory when the job
+// changes; the grid either covers the tile space (one warp per tile) or is
+// persistent and strides over it.
 template <int PPT, class Src, int MODE>
 __global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
     k_probe(const Src src, uint64_t T, const JoinScratch S) {
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
-    const uint64_t* s_root = cta_setup(Src::kSingle ? &src.job(0).X : nullptr, s_hlut, s_faces, s_rootbuf);
-    __syncthreads();
-    uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const uint32_t warp = threadIdx.x >> 5;
     if constexpr (Src::kSingle) {
+        const uint64_t* s_root = cta_setup(&src.job(0).X, s_hlut, s_faces, s_rootbuf);
+        __syncthreads();
+        const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
         if (wt < T) probe_tile<PPT, MODE>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S);
-    } else if ((uint64_t)gridDim.x * kWarpsPerBlock >= T) {     // one warp per tile
-        if (wt < T) {
-            const JobDesc& J = src.job(src.find_tile(wt));
-            probe_tile<PPT, MODE>(J, J.X.faces, s_hlut, nullptr, wt, wt - J.tile0, J.poly0, S);
-        }
-    } else {                                                     // persistent grid
-        for (; wt < T; wt += (uint64_t)gridDim.x * kWarpsPerBlock) {
-            const JobDesc& J = src.job(src.find_tile(wt));
-            probe_tile<PPT, MODE>(J, J.X.faces, s_hlut, nullptr, wt, wt - J.tile0, J.poly0, S);
+    } else {
+        cta_setup(nullptr, s_hlut, s_faces, s_rootbuf);
+        if ((uint64_t)gridDim.x * kWarpsPerBlock >= T) {            // one CTA per 8 tiles
+            const uint64_t g = blockIdx.x;
+            if (g * kWarpsPerBlock >= T) return;
+            const JobDesc& J = src.job(src.find_tile(g * kWarpsPerBlock));
+            const uint64_t* s_root = cta_stage_job(J, s_faces, s_rootbuf);
+            const uint64_t wt = g * kWarpsPerBlock + warp;
+            probe_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S);
+        } else {                                                    // persistent grid
+            uint32_t cur = 0xFFFFFFFFu;
+            const uint64_t* s_root = nullptr;
+            for (uint64_t g = blockIdx.x; g * kWarpsPerBlock < T; g += gridDim.x) {
+                const uint32_t j = src.find_tile(g * kWarpsPerBlock);
+                const JobDesc& J = src.job(j);
+                if (j != cur) {
+                    s_root = cta_stage_job(J, s_faces, s_rootbuf);
+                    cur = j;
+                }
+                const uint64_t wt = g * kWarpsPerBlock + warp;
+                probe_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S);
+            }
         }
     }
 }
@@ -604,9 +624,15 @@ __global__ void k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_
                             uint64_t* __restrict__ chunks, uint32_t* __restrict__ chunk_counter,
                             uint64_t* __restrict__ err);
 
-// Groups the candidate queue by polygon (counting-sort scatter).
-__global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ queue_len,
-                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted, uint64_t queue_cap,
+// Candidates per polygon of the queue (tile_cand[t] items from slot
+// t x tile_slots of each tile t).
+__global__ void k_count(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
+                        uint32_t tile_slots, uint32_t* __restrict__ poly_count, uint32_t n_polys);
+
+// Groups the queued candidates by polygon: a counting-sort scatter of slot
+// indices.
+__global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
+                          uint32_t tile_slots, uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted,
                           uint32_t n_polys);
 
 // Refine (Listing "Join" step 3 on candidate references): ST_Covers of
@@ -684,17 +710,32 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
     const bool exact = job_exact<MODE>(J);
     const uint64_t base = (wt - J.tile0) * (32 * PPT);
     uint32_t cnt[PPT], qb[PPT], ex[PPT], run = 0;
+    if (exact) {
+        // the queue slots of this tile's candidates, in the order the probe wrote them
+        uint32_t nt[PPT], nc[PPT], csum = 0;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        qb[k] = 0;
-        if (exact) {
-            cnt[k] = exact_count(J.X, e[k], S.qbase, gbase + lane + 32 * k, S.pass, S.queue_cap, &qb[k], J.status);
-            if (cnt[k] == 0xFFFFFFFFu) { cnt[k] = 0; e[k] = 0; }
-        } else {
+        for (int k = 0; k < PPT; ++k) {
+            entry_counts(J.X, e[k], &nt[k], &nc[k]);
+            csum += nc[k];
+        }
+        uint32_t q = warp_incl_scan(csum) - csum;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            qb[k] = q;
+            q += nc[k];
+            cnt[k] = exact_count(nt[k], nc[k], S.pass, wt * S.tile_slots + qb[k]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
             uint32_t nt, nc;
             entry_counts(J.X, e[k], &nt, &nc);
             cnt[k] = nt + nc;
+            qb[k] = 0;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
         const uint32_t incl = warp_incl_scan(cnt[k]);
         ex[k] = run + incl - cnt[k];
         run += __shfl_sync(kFull, incl, 31);
@@ -717,13 +758,14 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
         }
         const uint64_t ek = e[k];
         const uint32_t tag = (uint32_t)(ek & 3ull);
+        const uint8_t* ps = S.pass + wt * S.tile_slots + qb[k];
         uint64_t w = o;
         uint32_t ci = 0;
         if (tag == 1 || tag == 2) {
             for (int t = 0; t < (int)tag; ++t) {
                 const uint32_t pl = payload_of(ek, t);
                 if (pl & 1u) J.ids[w++] = pl >> 1;
-                else if (S.pass[qb[k] + ci++]) J.ids[w++] = pl >> 1;
+                else if (ps[ci++]) J.ids[w++] = pl >> 1;
             }
         } else if (tag == 3) {
             const uint32_t off = payload_of(ek, 0);
@@ -736,11 +778,12 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
                 const uint32_t ta = a < nt ? __ldg(Tt + a) : 0xFFFFFFFFu;
                 const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
                 if (ta < cb) { J.ids[w++] = ta; ++a; }
-                else { if (S.pass[qb[k] + b]) J.ids[w++] = cb; ++b; }
+                else { if (ps[b]) J.ids[w++] = cb; ++b; }
             }
         }
     }
-    if (base + 32 * PPT >= J.n && lane == 0) {
+    if (base < J.n && base + 32 * PPT >= J.n && lane == 0) {     // the job's last point
+
         J.offsets[J.n] = (uint32_t)(prefix + run);
         J.status[0] = prefix + run;
         const uint64_t g = *S.scan_err;

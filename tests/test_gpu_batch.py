@@ -125,3 +125,17 @@ def test_batch_rejects_small_outputs(torch, agj, jobs, indexes):
     pairs[1].c.ids_capacity = 0
     with pytest.raises(agj.AgjError):
         b.run([_dev(torch, jobs[6].points), _dev(torch, jobs[7].points)], pairs)
+
+
+@pytest.mark.parametrize("which", ["approx", "exact"])
+def test_batch_single_mode_plans(torch, agj, jobs, indexes, expected, which):
+    """Plans whose jobs are all approximate (no refine step, no candidate
+    work space) or all exact."""
+    sel = [j for j, jb in enumerate(jobs) if jb.exact == (which == "exact")]
+    for ppt, ctas in ((2, 0), (4, 3)):
+        b = agj.Batch([indexes[j] for j in sel], [len(jobs[j].points) for j in sel], points_per_lane=ppt,
+                      ctas_per_sm=ctas)
+        pr = b.run([_dev(torch, jobs[j].points) for j in sel], b.pairs())
+        torch.cuda.synchronize()
+        _check(pr, [expected[j] for j in sel])
+        b.close()
