@@ -336,6 +336,113 @@ void agj_batch_free(agj_batch* batch);
 int agj_join_batched(const agj_index* const* indexes, const double* const* d_points, const uint64_t* n,
                      uint32_t m, void* stream, agj_pairs* outs);
 
+/* ---------------------------------------------------------------------- */
+/* served form (no counterpart in the paper)                                */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * A request loop over resident indexes.  The paper motivates low-latency
+ * joins for streaming points but measures none; this form serves many small
+ * point requests by continuous batching: a scheduler thread forms a launch
+ * from the requests waiting whenever one of its n_slots slots is free and
+ * runs it as one batched join (see agj_batch_create) on that slot's stream
+ * while other slots' launches are in flight.  Each slot owns device and
+ * pinned host buffers sized at creation: a launch admits requests while
+ * their points (max_step_points), output ids and work space fit the slot.
+ * Each request's result is exactly what agj_join computes for its points.
+ *
+ * agj_server_create: indexes (built on the current device) are borrowed and
+ * must outlive the server; requests name them by position.  opts may be
+ * NULL.  With hbm_budget_bytes set, fewer slots are made to fit it
+ * (AGJ_EBUDGET if one slot does not fit).  Errors: AGJ_EINVAL, AGJ_EBUDGET,
+ * AGJ_ENOMEM, AGJ_ECUDA.
+ */
+typedef struct agj_server agj_server;
+typedef struct {
+    uint32_t n_slots;            /* launches in flight, 0 = 4 */
+    uint32_t max_step_requests;  /* requests per launch (<= 65535), 0 = 4096 */
+    uint64_t max_step_points;    /* points per launch (and per request), 0 = 2^20 */
+    uint64_t hbm_budget_bytes;   /* device memory for all slots, 0 = no limit */
+    uint64_t max_pending;        /* queued requests before submit answers AGJ_EBUSY, 0 = 2^20 */
+    uint32_t points_per_lane;    /* as agj_batch_opts, 0 = 2 */
+    uint32_t ctas_per_sm;        /* as agj_batch_opts */
+} agj_server_opts;
+int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const agj_server_opts* opts,
+                      agj_server** out);
+
+/*
+ * Queues a request: h_points (host, n x {lat, lng}) is borrowed until the
+ * request completes.  With h_offsets (host, n + 1) and h_ids (host,
+ * ids_capacity) the result is written there and kept until
+ * agj_server_poll; with both NULL the result is discarded and only counted
+ * in the statistics.  *ticket names the request.  Errors: AGJ_EINVAL,
+ * AGJ_ECAPACITY (n > max_step_points), AGJ_EBUSY (max_pending queued).
+ */
+int agj_server_submit(agj_server* server, uint32_t index_id, const double* h_points, uint64_t n,
+                      uint32_t* h_offsets, uint32_t* h_ids, uint64_t ids_capacity, uint64_t* ticket);
+
+typedef struct {
+    int32_t  status;             /* AGJ_OK, or the request's error */
+    uint32_t reserved;
+    uint64_t nnz;                /* pairs of the request */
+    uint64_t t_submit_ns, t_start_ns, t_done_ns;   /* steady clock */
+    uint64_t step;               /* launch that served it (1, 2, ...) */
+} agj_request_result;
+
+/* Result of a kept request (wait != 0 blocks until it completes; else
+ * AGJ_EBUSY while it runs).  A polled result is released. */
+int agj_server_poll(agj_server* server, uint64_t ticket, int wait, agj_request_result* out);
+/* Blocks until every submitted request has completed. */
+int agj_server_drain(agj_server* server);
+
+typedef struct {
+    uint64_t submitted, completed, rejected, points, steps, step_requests_max;
+    uint32_t n_slots, reserved;
+    uint64_t device_bytes;       /* device memory of the slots */
+    double p50_us, p99_us, mean_us, max_us;   /* submit-to-done latency of completed requests */
+} agj_server_stats;
+/* Statistics since creation or the last reset (reset != 0 clears them). */
+int agj_server_get_stats(agj_server* server, int reset, agj_server_stats* out);
+/* Drains, stops the scheduler and frees the server. */
+void agj_server_destroy(agj_server* server);
+
+/*
+ * Poisson load for the served form: n_requests arrivals at `rate` per
+ * second; sizes 1..max_points with P(k) proportional to k^-zipf_alpha; each
+ * addresses a uniformly drawn set, its exact index with probability
+ * exact_fraction (when exact_index[set] != 0xFFFFFFFF), else its approximate
+ * index; its points are a random contiguous slice of the set's host pool
+ * (pool_points[set] >= max_points).  The first warmup_requests are left
+ * out of the statistics.
+ */
+typedef struct {
+    double rate;
+    uint64_t n_requests;
+    double zipf_alpha;
+    uint32_t max_points;
+    uint32_t n_sets;
+    double exact_fraction;
+    const uint32_t* approx_index;
+    const uint32_t* exact_index;
+    const double* const* pools;
+    const uint64_t* pool_points;
+    uint64_t seed;
+    uint64_t warmup_requests;
+} agj_load_spec;
+typedef struct {
+    uint64_t requests, points, rejected;
+    double seconds, offered_rate, achieved_rate, points_per_s;
+    double p50_us, p99_us, mean_us, max_us;   /* arrival-to-done latency */
+} agj_load_result;
+/* Drives `server` with the spec's arrivals (submitting at arrival times
+ * from the calling thread) and waits for all of them. */
+int agj_server_load(agj_server* server, const agj_load_spec* spec, agj_load_result* out);
+/* The same arrivals served one at a time by agj_join_host (the plain join
+ * of a host request) in arrival order, for comparison; index ids name
+ * positions in `indexes`. */
+int agj_plain_load(const agj_index* const* indexes, uint32_t n_indexes, const agj_load_spec* spec,
+                   agj_load_result* out);
+
 /* Synchronises `stream`, reads out->status and returns AGJ_OK, or the first
  * device-side error as a status code; *nnz receives the pair count. */
 int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz);

@@ -28,7 +28,7 @@ NVCCFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", *ARCH, "-Xcompiler
              f"-I{ROOT}/include", "--expt-relaxed-constexpr"]
 
 CU_SOURCES = ["agj_kernels.cu", "agj_batch.cu"]
-CXX_SOURCES = ["agj_build.cpp", "agj_model.cpp", "agj_capi.cpp"]
+CXX_SOURCES = ["agj_build.cpp", "agj_model.cpp", "agj_capi.cpp", "agj_server.cpp"]
 
 
 def _sources():

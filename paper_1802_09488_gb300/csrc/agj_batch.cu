@@ -1,10 +1,17 @@
 // agj_batch.cu — the batched form of the probe (no counterpart in the paper):
 // many (index, point batch) jobs of uneven sizes joined by one launch
-// sequence whose probe and emit kernels are persistent grids striding over
-// the jobs' warp tiles laid end to end, and whose refine step covers the
-// candidate polygons of every exact job at once.  The sequence is captured
-// once into a CUDA graph; a run uploads the job descriptors (only when a
-// pointer changed) and launches the graph.
+// sequence.  The jobs' warp tiles are laid end to end in one tile space
+// (each job padded to whole CTAs, so a CTA's tiles share a job), their exact
+// indexes' polygons in one polygon space (one range per distinct index), and
+// the probe, refine, scan and emit kernels run once over all of it.
+//
+// Two users share the code here:
+//   * Batch (agj_batch_*): a plan for fixed (index, point count) jobs, with
+//     its own device memory and a CUDA graph captured once; a run uploads
+//     the job descriptors (only when a pointer changed) and replays the graph;
+//   * step_enqueue (the served form): one launch for a set of jobs formed on
+//     the fly, into a caller's device work space, with its tables staged
+//     through a caller's pinned buffer.
 //
 // Each job computes what the plain join computes for it, bit for bit: the
 // same probe per point, the same candidate set and refine test, the same
@@ -15,6 +22,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "agj_index.h"
@@ -41,22 +49,154 @@ __global__ void __launch_bounds__(256) k_jobs_init(const JobDesc* __restrict__ j
     }
 }
 
-struct Batch {
+// The shape of one batched launch: where each job sits in the tile and
+// polygon spaces, and the device memory it needs, as offsets from a base:
+//   [job descriptors][job of each tile u16]   <- the tables a launch uploads
+//   [job bases u32][per-job counters 2 x u64][join work space]
+struct Shape {
     uint32_t m = 0;
     int ppt = 2;
+    uint64_t T = 0, P = 0;
+    std::vector<uint64_t> tile0;   // m + 1
+    std::vector<uint32_t> poly0;   // m
+    JoinLayout L;
+    uint64_t off_jobs = 0, off_tile_job = 0, table_bytes = 0;
+    uint64_t off_job_base = 0, off_counters = 0, off_scratch = 0, bytes = 0;
+};
+
+namespace {
+
+int make_shape(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, int dev, Shape* S) {
+    if (m > kMaxBatchJobs) return AGJ_EUNSUPPORTED;
+    S->m = m;
+    S->ppt = ppt;
+    S->tile0.clear();
+    S->poly0.clear();
+    uint64_t T = 0, P = 0;
+    uint32_t mcr = 1;    // most candidate references of a point over the exact jobs
+    bool any_exact = false;
+    std::vector<std::pair<const Index*, uint32_t>> poly_base;   // exact indexes and their polygon ranges
+    for (uint32_t j = 0; j < m; ++j) {
+        const Index* x = X[j];
+        if (!x || !x->d_blob || x->device != dev || n[j] >= 0xFFFFFFFFull) return AGJ_EINVAL;
+        if (n[j] * std::max<uint64_t>(x->stats.max_refs, 1) >= 0xFFFFFFFFull) return AGJ_ECAPACITY;
+        S->tile0.push_back(T);
+        uint32_t pb = 0;
+        if (x->mode == AGJ_EXACT) {
+            any_exact = true;
+            mcr = std::max<uint32_t>(mcr, x->stats.max_cand_refs);
+            auto it = std::find_if(poly_base.begin(), poly_base.end(), [&](const auto& e) { return e.first == x; });
+            if (it == poly_base.end()) {
+                poly_base.emplace_back(x, (uint32_t)P);
+                pb = (uint32_t)P;
+                P += x->n_polys;
+            } else {
+                pb = it->second;
+            }
+        }
+        S->poly0.push_back(pb);
+        // whole CTAs per job: a CTA's tiles share one job
+        T += (n[j] + 32 * ppt - 1) / (32 * ppt);
+        T = (T + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
+    }
+    const uint32_t slots = 32u * (uint32_t)ppt * mcr;
+    if (P >= 0xFFFFFFFFull || T * 32 * ppt >= 0xFFFFFFFFull || (any_exact && T * slots >= 0xFFFFFFFFull))
+        return AGJ_ECAPACITY;   // 32-bit point, polygon and queue indices
+    S->tile0.push_back(T);
+    S->T = T;
+    S->P = P;
+    S->L = join_layout(T * 32 * ppt, T, any_exact, any_exact ? slots : 0u, P);
+    uint64_t o = 0;
+    S->off_jobs = o; o += align256((uint64_t)std::max<uint32_t>(m, 1) * sizeof(JobDesc));
+    S->off_tile_job = o; o += align256(T * 2 + 2);
+    S->table_bytes = o;
+    S->off_job_base = o; o += align256((uint64_t)std::max<uint32_t>(m, 1) * 4);
+    S->off_counters = o; o += align256((uint64_t)std::max<uint32_t>(m, 1) * 16);
+    S->off_scratch = o; o += S->L.total;
+    S->bytes = o;
+    return AGJ_OK;
+}
+
+void fill_tile_job(const Shape& S, uint16_t* tile_job) {
+    for (uint32_t j = 0; j < S.m; ++j)
+        std::fill(tile_job + S.tile0[j], tile_job + S.tile0[j + 1], (uint16_t)j);
+}
+
+// Job descriptors of one launch; counters: the per-job diagnostic words in
+// device memory (used where the caller passes no work space).
+int fill_jobs(const Shape& S, const Index* const* X, const uint64_t* n, const double* const* d_points,
+              agj_pairs* outs, uint64_t* counters, JobDesc* jobs) {
+    for (uint32_t j = 0; j < S.m; ++j) {
+        agj_pairs* o = &outs[j];
+        const Index& x = *X[j];
+        if (!o->offsets || !o->status || (n[j] && !d_points[j])) return AGJ_EINVAL;
+        if ((reinterpret_cast<uintptr_t>(d_points[j]) & 15u) != 0) return AGJ_EINVAL;
+        const uint64_t need = n[j] * std::max<uint64_t>(x.stats.max_refs, 1);
+        if (o->ids_capacity < need || (need && !o->ids)) return AGJ_ECAPACITY;
+        // diagnostics go where the plain join puts them when the caller
+        // passes a work space
+        uint64_t* c = (o->scratch && o->scratch_bytes >= 32) ? static_cast<uint64_t*>(o->scratch) + 2 : counters + 2 * j;
+        JobDesc J = make_job(x, d_points[j], n[j], o, c);
+        J.tile0 = S.tile0[j];
+        J.poly0 = S.poly0[j];
+        memcpy(&jobs[j], &J, sizeof J);
+    }
+    return AGJ_OK;
+}
+
+template <int PPT>
+cudaError_t enqueue_kernels(const Shape& S, char* base, int ctas_per_sm, cudaStream_t s) {
+    ManyJobs src;
+    src.d = reinterpret_cast<const JobDesc*>(base + S.off_jobs);
+    src.tile_job = reinterpret_cast<const uint16_t*>(base + S.off_tile_job);
+    src.base = reinterpret_cast<const uint32_t*>(base + S.off_job_base);
+    src.m = S.m;
+    k_jobs_init<<<(S.m + 255) / 256, 256, 0, s>>>(src.d, S.m);
+    JoinLaunch G;
+    G.sms = sm_count();
+    const uint64_t need = (S.L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (ctas_per_sm == 0) {            // one warp per tile
+        G.probe_grid = (int)std::max<uint64_t>(1, need);
+        G.emit_grid = G.probe_grid;
+    } else {                           // persistent grids
+        G.probe_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)G.sms * ctas_per_sm));
+        // the emit is short and latency-bound: a full-occupancy grid
+        G.emit_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)G.sms * 8));
+    }
+    G.pip_grid = G.sms * 4;
+    G.tile_job = src.tile_job;
+    G.job_base = reinterpret_cast<uint32_t*>(base + S.off_job_base);
+    return enqueue_join<PPT, ManyJobs, kModeAny>(src, S.L, base + S.off_scratch, G, nullptr, 0, s, nullptr);
+}
+
+cudaError_t enqueue(const Shape& S, char* base, int ctas_per_sm, cudaStream_t s) {
+    switch (S.ppt) {
+        case 1: return enqueue_kernels<1>(S, base, ctas_per_sm, s);
+        case 4: return enqueue_kernels<4>(S, base, ctas_per_sm, s);
+        default: return enqueue_kernels<2>(S, base, ctas_per_sm, s);
+    }
+}
+
+int check_options(int* ppt, int ctas_per_sm) {
+    if (*ppt == 0) *ppt = 2;
+    if (*ppt != 1 && *ppt != 2 && *ppt != 4) return AGJ_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 8) return AGJ_EINVAL;
+    return AGJ_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+
+struct Batch {
+    Shape S;
     int ctas_per_sm = 0;                // 0: one warp per tile, else persistent grids
-    bool use_graph = true;
     int device = 0;
     std::vector<const Index*> X;
     std::vector<uint64_t> n;
-    std::vector<uint64_t> tile0;
-    std::vector<uint32_t> poly0;
-    JoinLayout L;
-    // device: [job descriptors][job of each tile u16][job bases u32]
-    // [poly0 u32 m+1][per-job counters 2 x u64][join work space]
     char* d_mem = nullptr;
-    uint64_t off_jobs = 0, off_tile_job = 0, off_job_base = 0, off_poly0 = 0, off_counters = 0, off_scratch = 0,
-             bytes = 0;
     JobDesc* h_jobs = nullptr;          // pinned staging of the descriptors
     std::vector<JobDesc> last;          // descriptors of the last upload
     bool uploaded = false;
@@ -64,44 +204,6 @@ struct Batch {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
-
-namespace {
-
-template <int PPT>
-cudaError_t enqueue_batch(Batch* B, cudaStream_t s) {
-    ManyJobs src;
-    src.d = reinterpret_cast<const JobDesc*>(B->d_mem + B->off_jobs);
-    src.tile_job = reinterpret_cast<const uint16_t*>(B->d_mem + B->off_tile_job);
-    src.base = reinterpret_cast<const uint32_t*>(B->d_mem + B->off_job_base);
-    src.poly0 = reinterpret_cast<const uint32_t*>(B->d_mem + B->off_poly0);
-    src.m = B->m;
-    k_jobs_init<<<(B->m + 255) / 256, 256, 0, s>>>(src.d, B->m);
-    JoinLaunch G;
-    G.sms = sm_count();
-    const uint64_t need = (B->L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (B->ctas_per_sm == 0) {            // one warp per tile
-        G.probe_grid = (int)std::max<uint64_t>(1, need);
-        G.emit_grid = G.probe_grid;
-    } else {                              // persistent grids
-        G.probe_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)G.sms * B->ctas_per_sm));
-        // the emit is short and latency-bound: a full-occupancy grid
-        G.emit_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)G.sms * 8));
-    }
-    G.pip_grid = G.sms * 4;
-    G.tile_job = src.tile_job;
-    G.job_base = reinterpret_cast<uint32_t*>(B->d_mem + B->off_job_base);
-    return enqueue_join<PPT, ManyJobs, kModeAny>(src, B->L, B->d_mem + B->off_scratch, G, nullptr, 0, s, nullptr);
-}
-
-cudaError_t enqueue(Batch* B, cudaStream_t s) {
-    switch (B->ppt) {
-        case 1: return enqueue_batch<1>(B, s);
-        case 4: return enqueue_batch<4>(B, s);
-        default: return enqueue_batch<2>(B, s);
-    }
-}
-
-}  // namespace
 
 void batch_free(Batch* B) {
     if (!B) return;
@@ -117,60 +219,20 @@ int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, 
                  Batch** out) {
     if (!out || (m && (!X || !n))) return AGJ_EINVAL;
     *out = nullptr;
-    if (m > kMaxBatchJobs) return AGJ_EUNSUPPORTED;
-    if (ppt == 0) ppt = 2;
-    if (ppt != 1 && ppt != 2 && ppt != 4) return AGJ_EINVAL;
-    if (ctas_per_sm < 0 || ctas_per_sm > 8) return AGJ_EINVAL;
+    int rc = check_options(&ppt, ctas_per_sm);
+    if (rc != AGJ_OK) return rc;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
-    uint64_t T = 0, P = 0;
-    uint32_t mcr = 1;    // most candidate references of a point over the exact jobs
-    bool any_exact = false;
     Batch* B = new (std::nothrow) Batch();
     if (!B) return AGJ_ENOMEM;
-    B->m = m;
-    B->ppt = ppt;
+    rc = make_shape(X, n, m, ppt, dev, &B->S);
+    if (rc != AGJ_OK) { delete B; return rc; }
     B->ctas_per_sm = ctas_per_sm;
-    B->use_graph = use_graph;
     B->device = dev;
     B->X.assign(X, X + m);
     B->n.assign(n, n + m);
-    for (uint32_t j = 0; j < m; ++j) {
-        const Index* x = X[j];
-        if (!x || !x->d_blob || x->device != dev || n[j] >= 0xFFFFFFFFull) { delete B; return AGJ_EINVAL; }
-        const uint64_t ids = n[j] * std::max<uint64_t>(x->stats.max_refs, 1);
-        if (ids >= 0xFFFFFFFFull) { delete B; return AGJ_ECAPACITY; }
-        B->tile0.push_back(T);
-        B->poly0.push_back((uint32_t)P);
-        // whole CTAs per job: a CTA's tiles share one job
-        T += (n[j] + 32 * ppt - 1) / (32 * ppt);
-        T = (T + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
-        if (x->mode == AGJ_EXACT) {
-            any_exact = true;
-            P += x->n_polys;
-            mcr = std::max<uint32_t>(mcr, x->stats.max_cand_refs);
-        }
-    }
-    const uint32_t slots = 32u * (uint32_t)ppt * mcr;
-    if (P >= 0xFFFFFFFFull || (any_exact && T * slots >= 0xFFFFFFFFull) || T >= (1ull << 36)) {
-        delete B;
-        return AGJ_ECAPACITY;
-    }
-    B->tile0.push_back(T);
-    B->poly0.push_back((uint32_t)P);
-    B->L = join_layout(T * 32 * ppt, T, any_exact, any_exact ? slots : 0u, P);
-    std::vector<uint16_t> tile_job(T);
-    for (uint32_t j = 0; j < m; ++j)
-        std::fill(tile_job.begin() + B->tile0[j], tile_job.begin() + B->tile0[j + 1], (uint16_t)j);
-    uint64_t o = 0;
-    B->off_jobs = o; o += align256((uint64_t)std::max<uint32_t>(m, 1) * sizeof(JobDesc));
-    B->off_tile_job = o; o += align256(T * 2 + 2);
-    B->off_job_base = o; o += align256((uint64_t)std::max<uint32_t>(m, 1) * 4);
-    B->off_poly0 = o; o += align256((uint64_t)(m + 1) * 4);
-    B->off_counters = o; o += align256((uint64_t)std::max<uint32_t>(m, 1) * 16);
-    B->off_scratch = o; o += B->L.total;
-    B->bytes = o;
-    if (cudaMalloc(&B->d_mem, o) != cudaSuccess) { cudaGetLastError(); B->d_mem = nullptr; batch_free(B); return AGJ_ENOMEM; }
+    const Shape& S = B->S;
+    if (cudaMalloc(&B->d_mem, S.bytes) != cudaSuccess) { cudaGetLastError(); B->d_mem = nullptr; batch_free(B); return AGJ_ENOMEM; }
     if (cudaMallocHost(&B->h_jobs, (uint64_t)std::max<uint32_t>(m, 1) * sizeof(JobDesc)) != cudaSuccess) {
         cudaGetLastError();
         B->h_jobs = nullptr;
@@ -183,20 +245,19 @@ int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, 
         batch_free(B);
         return AGJ_ECUDA;
     }
-    // the job-space tables never change for a plan
+    // the tile-to-job table never changes for a plan
+    std::vector<uint16_t> tile_job(S.T);
+    fill_tile_job(S, tile_job.data());
     cudaError_t e = cudaSuccess;
-    if (T)
-        e = cudaMemcpyAsync(B->d_mem + B->off_tile_job, tile_job.data(), T * 2, cudaMemcpyHostToDevice, B->cap_stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(B->d_mem + B->off_poly0, B->poly0.data(), (m + 1) * 4ull, cudaMemcpyHostToDevice,
-                            B->cap_stream);
+    if (S.T)
+        e = cudaMemcpyAsync(B->d_mem + S.off_tile_job, tile_job.data(), S.T * 2, cudaMemcpyHostToDevice, B->cap_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(B->cap_stream);
     if (e != cudaSuccess) { cudaGetLastError(); batch_free(B); return AGJ_ECUDA; }
     if (use_graph && m) {
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t e1 = enqueue(B, B->cap_stream);
+            const cudaError_t e1 = enqueue(S, B->d_mem, ctas_per_sm, B->cap_stream);
             e = cudaStreamEndCapture(B->cap_stream, &g);
             if (e1 != cudaSuccess) e = e1;
         }
@@ -208,46 +269,92 @@ int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, 
     return AGJ_OK;
 }
 
-uint64_t batch_device_bytes(const Batch* B) { return B ? B->bytes : 0; }
+uint64_t batch_device_bytes(const Batch* B) { return B ? B->S.bytes : 0; }
 
 int batch_run(Batch* B, const double* const* d_points, cudaStream_t s, agj_pairs* outs) {
     if (!B) return AGJ_EINVAL;
-    if (B->m == 0) return AGJ_OK;
+    const Shape& S = B->S;
+    if (S.m == 0) return AGJ_OK;
     if (!d_points || !outs) return AGJ_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != B->device) { cudaGetLastError(); return AGJ_EINVAL; }
-    std::vector<JobDesc> jobs(B->m);
-    uint64_t* counters = reinterpret_cast<uint64_t*>(B->d_mem + B->off_counters);
-    for (uint32_t j = 0; j < B->m; ++j) {
-        agj_pairs* o = &outs[j];
-        const uint64_t n = B->n[j];
-        const Index& x = *B->X[j];
-        if (!o->offsets || !o->status || (n && !d_points[j])) return AGJ_EINVAL;
-        if ((reinterpret_cast<uintptr_t>(d_points[j]) & 15u) != 0) return AGJ_EINVAL;
-        const uint64_t need = n * std::max<uint64_t>(x.stats.max_refs, 1);
-        if (o->ids_capacity < need || (need && !o->ids)) return AGJ_ECAPACITY;
-        // diagnostics go where the plain join puts them when the caller
-        // passes a work space, else to the plan's own words
-        uint64_t* c = (o->scratch && o->scratch_bytes >= 32) ? static_cast<uint64_t*>(o->scratch) + 2 : counters + 2 * j;
-        JobDesc J = make_job(x, d_points[j], n, o, c);
-        J.tile0 = B->tile0[j];
-        J.poly0 = B->poly0[j];
-        jobs[j] = J;
-    }
+    std::vector<JobDesc> jobs(S.m);
+    const int rc = fill_jobs(S, B->X.data(), B->n.data(), d_points, outs,
+                             reinterpret_cast<uint64_t*>(B->d_mem + S.off_counters), jobs.data());
+    if (rc != AGJ_OK) return rc;
     const bool same = B->uploaded && memcmp(jobs.data(), B->last.data(), jobs.size() * sizeof(JobDesc)) == 0;
     if (!same) {
         // the staging buffer may still feed the previous upload
         if (B->uploaded && cudaEventSynchronize(B->upload_done) != cudaSuccess) return AGJ_ECUDA;
         memcpy(B->h_jobs, jobs.data(), jobs.size() * sizeof(JobDesc));
-        if (cudaMemcpyAsync(B->d_mem + B->off_jobs, B->h_jobs, jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice,
+        if (cudaMemcpyAsync(B->d_mem + S.off_jobs, B->h_jobs, jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice,
                             s) != cudaSuccess ||
             cudaEventRecord(B->upload_done, s) != cudaSuccess)
             return AGJ_ECUDA;
         B->last = jobs;
         B->uploaded = true;
     }
-    const cudaError_t e = B->exec ? cudaGraphLaunch(B->exec, s) : enqueue(B, s);
+    const cudaError_t e = B->exec ? cudaGraphLaunch(B->exec, s) : enqueue(S, B->d_mem, B->ctas_per_sm, s);
     return e == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// one launch for jobs formed on the fly (the served form)
+// ---------------------------------------------------------------------------
+
+int step_bytes(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, uint64_t* device_bytes,
+               uint64_t* table_bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
+    int rc = check_options(&ppt, 0);
+    if (rc != AGJ_OK) return rc;
+    Shape S;
+    rc = make_shape(X, n, m, ppt, dev, &S);
+    if (rc != AGJ_OK) return rc;
+    *device_bytes = S.bytes;
+    *table_bytes = S.table_bytes;
+    return AGJ_OK;
+}
+
+int step_bound(uint64_t max_points, uint32_t max_jobs, int ppt, uint32_t max_cand_refs, uint64_t max_polys,
+               bool exact, uint64_t* device_bytes, uint64_t* table_bytes) {
+    int rc = check_options(&ppt, 0);
+    if (rc != AGJ_OK) return rc;
+    if (max_jobs > kMaxBatchJobs) return AGJ_EUNSUPPORTED;
+    // every job adds at most one partial tile and the padding to a whole CTA
+    const uint64_t T = (max_points + 32 * ppt - 1) / (32 * ppt) + (uint64_t)max_jobs * kWarpsPerBlock;
+    const uint32_t slots = 32u * (uint32_t)ppt * std::max<uint32_t>(max_cand_refs, 1);
+    if (max_polys >= 0xFFFFFFFFull || T * 32 * ppt >= 0xFFFFFFFFull || (exact && T * slots >= 0xFFFFFFFFull))
+        return AGJ_ECAPACITY;
+    const JoinLayout L = join_layout(T * 32 * ppt, T, exact, exact ? slots : 0u, exact ? max_polys : 0);
+    const uint64_t m = std::max<uint32_t>(max_jobs, 1);
+    *table_bytes = align256(m * sizeof(JobDesc)) + align256(T * 2 + 2);
+    *device_bytes = *table_bytes + align256(m * 4) + align256(m * 16) + L.total;
+    return AGJ_OK;
+}
+
+int step_enqueue(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, int ctas_per_sm,
+                 const double* const* d_points, agj_pairs* outs, void* d_work, uint64_t work_bytes, void* h_stage,
+                 uint64_t stage_bytes, cudaStream_t s) {
+    if (m == 0) return AGJ_OK;
+    if (!X || !n || !d_points || !outs || !d_work || !h_stage) return AGJ_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_work) & 255u) != 0) return AGJ_EINVAL;
+    int rc = check_options(&ppt, ctas_per_sm);
+    if (rc != AGJ_OK) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
+    Shape S;
+    rc = make_shape(X, n, m, ppt, dev, &S);
+    if (rc != AGJ_OK) return rc;
+    if (S.bytes > work_bytes || S.table_bytes > stage_bytes) return AGJ_ECAPACITY;
+    char* base = static_cast<char*>(d_work);
+    char* stage = static_cast<char*>(h_stage);
+    rc = fill_jobs(S, X, n, d_points, outs, reinterpret_cast<uint64_t*>(base + S.off_counters),
+                   reinterpret_cast<JobDesc*>(stage + S.off_jobs));
+    if (rc != AGJ_OK) return rc;
+    fill_tile_job(S, reinterpret_cast<uint16_t*>(stage + S.off_tile_job));
+    if (cudaMemcpyAsync(base, stage, S.table_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return AGJ_ECUDA;
+    return enqueue(S, base, ctas_per_sm, s) == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
 
 }  // namespace agj

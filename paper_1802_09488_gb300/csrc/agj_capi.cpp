@@ -10,12 +10,9 @@
 
 #include "../../include/agj.h"
 #include "agj_geom.cuh"
+#include "agj_handle.h"
 #include "agj_index.h"
 #include "agj_launch.h"
-
-struct agj_index {
-    agj::Index X;
-};
 
 struct agj_batch {
     agj::Batch* B;

@@ -27,5 +27,19 @@ int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, 
 int batch_run(Batch* B, const double* const* d_points, cudaStream_t s, agj_pairs* outs);
 uint64_t batch_device_bytes(const Batch* B);
 void batch_free(Batch* B);
+// One batched launch for jobs formed on the fly (the served form): device
+// work space (256-byte aligned) and pinned staging sizes for the jobs, and
+// the launch itself on stream s (the staging buffer must stay untouched
+// until the stream passes the launch).
+int step_bytes(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, uint64_t* device_bytes,
+               uint64_t* table_bytes);
+// Work space and staging that suffice for any step of at most max_points
+// points in max_jobs jobs over indexes with at most max_cand_refs candidate
+// references per cell and max_polys polygons over the exact indexes.
+int step_bound(uint64_t max_points, uint32_t max_jobs, int ppt, uint32_t max_cand_refs, uint64_t max_polys,
+               bool exact, uint64_t* device_bytes, uint64_t* table_bytes);
+int step_enqueue(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, int ctas_per_sm,
+                 const double* const* d_points, agj_pairs* outs, void* d_work, uint64_t work_bytes, void* h_stage,
+                 uint64_t stage_bytes, cudaStream_t s);
 
 }  // namespace agj

@@ -378,9 +378,9 @@ __device__ __forceinline__ bool covers_fp64(const DevIndex& X, uint32_t poly, do
 
 // One (index, points, output) job.  Its warp tiles are tile0 .. tile0 +
 // ceil(n / (32 PPT)) - 1 of the global tile space (in the batched form its
-// range is padded to whole CTAs with tiles of no points), and in exact mode its
-// polygons poly0 .. poly0 + n_polys - 1 of the global polygon space of the
-// refine step.  Per-point work space (stored entries, queue bases) is
+// range is padded to whole CTAs with tiles of no points), and in exact mode
+// its index's polygons are poly0 .. poly0 + n_polys - 1 of the global
+// polygon space of the refine step (shared by the jobs of one index).  Per-point work space (stored entries, queue bases) is
 // indexed by the tile-padded global point index wt * 32 PPT + lane + 32 k,
 // which needs no job lookup.
 struct __align__(16) JobDesc {
@@ -402,7 +402,6 @@ struct OneJob {
     JobDesc d;
     static constexpr bool kSingle = true;
     __device__ __forceinline__ uint32_t find_tile(uint64_t) const { return 0; }
-    __device__ __forceinline__ uint32_t find_poly(uint32_t) const { return 0; }
     __device__ __forceinline__ const JobDesc& job(uint32_t) const { return d; }
     __device__ __forceinline__ uint32_t job_base(uint32_t) const { return 0; }
 };
@@ -412,21 +411,9 @@ struct ManyJobs {
     const JobDesc* d;
     const uint16_t* tile_job; // job of each global tile
     const uint32_t* base;     // per job: tile prefix (mod 2^32) at its first tile, written by the scan
-    const uint32_t* poly0;    // m + 1: first global polygon of each job, then the total
     uint32_t m;
     static constexpr bool kSingle = false;
-    // the last j with start[j] <= x (jobs with empty ranges are skipped over)
-    template <class T>
-    __device__ __forceinline__ uint32_t last_le(const T* start, T x) const {
-        uint32_t lo = 0, hi = m;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(start + mid) <= x) lo = mid; else hi = mid;
-        }
-        return lo;
-    }
     __device__ __forceinline__ uint32_t find_tile(uint64_t wt) const { return __ldg(tile_job + wt); }
-    __device__ __forceinline__ uint32_t find_poly(uint32_t gp) const { return last_le(poly0, gp); }
     __device__ __forceinline__ const JobDesc& job(uint32_t j) const { return d[j]; }
     __device__ __forceinline__ uint32_t job_base(uint32_t j) const { return base[j]; }
 };
@@ -444,7 +431,7 @@ struct JoinScratch {
     uint64_t* entries;        // tagged trie entry per point
     uint32_t* tile_count;     // pairs per warp tile (exact: true hits, then + passing candidates)
     uint32_t* tile_prefix;    // exclusive scan of tile_count (mod 2^32)
-    uint2* queue;             // exact: (job-local point, global polygon) candidates, tile_slots per tile
+    uint2* queue;             // exact: (global point, global polygon) candidates, tile_slots per tile
     uint8_t* pass;            // exact: PIP result per queue slot
     uint32_t* tile_cand;      // exact: candidates queued by each tile
     uint32_t* poly_count;     // exact: candidates per global polygon (k_count)
@@ -518,7 +505,7 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (!nc[k]) continue;
-        const uint32_t p = (uint32_t)(base + lane + 32 * k);
+        const uint32_t g = (uint32_t)(gbase + lane + 32 * k);     // global point index
         const uint64_t ek = e[k];
         const uint32_t tag = (uint32_t)(ek & 3ull);
         const uint32_t* Cc = nullptr;
@@ -536,7 +523,7 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
                 poly = pl >> 1;
             }
             ++t;
-            S.queue[q++] = make_uint2(p, gpoly0 + poly);
+            S.queue[q++] = make_uint2(g, gpoly0 + poly);
         }
     }
 }
@@ -643,7 +630,9 @@ __global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __res
 // one (covers_certified); an undecided candidate (within the error bounds of
 // a vertex or an edge) is recomputed in FP64 (covers_fp64), as is every
 // candidate of a polygon too large for the FP32 local frame.  A passing
-// candidate adds one to its tile's pair count.
+// candidate adds one to its tile's pair count.  The polygon's data comes
+// from the job of the chunk's first candidate (every job sharing a polygon
+// range probes the same index); each candidate's point from its own job.
 template <class Src>
 __global__ void __launch_bounds__(kPipBlock) k_pip(const Src src, uint32_t tile_points, uint32_t P,
                                                    const uint2* __restrict__ queue, const uint32_t* __restrict__ sorted,
@@ -661,32 +650,34 @@ __global__ void __launch_bounds__(kPipBlock) k_pip(const Src src, uint32_t tile_
             if (chunk_start[mid] <= c) lo = mid; else hi = mid;
         }
         const uint32_t gp = lo;
-        const JobDesc& J = src.job(src.find_poly(gp));
-        const uint32_t poly = gp - J.poly0;
         const uint32_t q0 = poly_start[gp] + (c - chunk_start[gp]) * kPipBlock;
         const uint32_t q1 = min(q0 + kPipBlock, poly_start[gp + 1]);
+        const JobDesc& JP = src.job(src.find_tile(queue[sorted[q0]].x / tile_points));
+        const uint32_t poly = gp - JP.poly0;
         const uint32_t item = q0 + threadIdx.x;
-        const uint32_t v0 = J.X.poly_off[poly], V = J.X.poly_off[poly + 1] - v0;
-        const PolyLocal L = J.X.poly_local[poly];
-        const bool certified = J.X.model.uv_enabled && L.ok && V <= (uint32_t)kPipSmemVerts;
+        const uint32_t v0 = JP.X.poly_off[poly], V = JP.X.poly_off[poly + 1] - v0;
+        const PolyLocal L = JP.X.poly_local[poly];
+        const bool certified = JP.X.model.uv_enabled && L.ok && V <= (uint32_t)kPipSmemVerts;
         __syncthreads();
         if (certified)
-            for (uint32_t t = threadIdx.x; t < V; t += blockDim.x) s_lv[t] = J.X.poly_luv[v0 + t];
+            for (uint32_t t = threadIdx.x; t < V; t += blockDim.x) s_lv[t] = JP.X.poly_luv[v0 + t];
         __syncthreads();
         if (item < q1) {
             const uint32_t qi = sorted[item];
             const uint2 qp = queue[qi];
-            const double2 pt = J.pts[qp.x];
+            const uint32_t wt = qp.x / tile_points;
+            const JobDesc& J = src.job(src.find_tile(wt));
+            const double2 pt = J.pts[qp.x - J.tile0 * tile_points];
             int r = -1;
             float pu, pv, dp;
-            if (certified && model_uv_local(J.X.model, pt.x, pt.y, L, &pu, &pv, &dp))
+            if (certified && model_uv_local(JP.X.model, pt.x, pt.y, L, &pu, &pv, &dp))
                 r = covers_certified(s_lv, V, L, pu, pv, dp);
             if (r < 0) {
-                r = covers_fp64(J.X, poly, pt.x, pt.y) ? 1 : 0;
+                r = covers_fp64(JP.X, poly, pt.x, pt.y) ? 1 : 0;
                 atomicAdd((unsigned long long*)&J.counters[1], 1ull);
             }
             pass[qi] = (uint8_t)r;
-            if (r) atomicAdd(&tile_count[J.tile0 + qp.x / tile_points], 1u);
+            if (r) atomicAdd(&tile_count[wt], 1u);
         }
     }
 }

@@ -62,6 +62,44 @@ class Requirements(C.Structure):
     _fields_ = [("ids_capacity", C.c_uint64), ("scratch_bytes", C.c_uint64)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("n_slots", C.c_uint32), ("max_step_requests", C.c_uint32), ("max_step_points", C.c_uint64),
+                ("hbm_budget_bytes", C.c_uint64), ("max_pending", C.c_uint64), ("points_per_lane", C.c_uint32),
+                ("ctas_per_sm", C.c_uint32)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("reserved", C.c_uint32), ("nnz", C.c_uint64), ("t_submit_ns", C.c_uint64),
+                ("t_start_ns", C.c_uint64), ("t_done_ns", C.c_uint64), ("step", C.c_uint64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("points", C.c_uint64), ("steps", C.c_uint64), ("step_requests_max", C.c_uint64),
+                ("n_slots", C.c_uint32), ("reserved", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class LoadSpec(C.Structure):
+    _fields_ = [("rate", C.c_double), ("n_requests", C.c_uint64), ("zipf_alpha", C.c_double),
+                ("max_points", C.c_uint32), ("n_sets", C.c_uint32), ("exact_fraction", C.c_double),
+                ("approx_index", C.c_void_p), ("exact_index", C.c_void_p), ("pools", C.c_void_p),
+                ("pool_points", C.c_void_p), ("seed", C.c_uint64), ("warmup_requests", C.c_uint64)]
+
+
+class LoadResult(C.Structure):
+    _fields_ = [("requests", C.c_uint64), ("points", C.c_uint64), ("rejected", C.c_uint64),
+                ("seconds", C.c_double), ("offered_rate", C.c_double), ("achieved_rate", C.c_double),
+                ("points_per_s", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double),
+                ("mean_us", C.c_double), ("max_us", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class BatchOpts(C.Structure):
     _fields_ = [("points_per_lane", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("no_graph", C.c_uint32),
                 ("reserved", C.c_uint32)]
@@ -106,6 +144,14 @@ def lib():
             "agj_batch_device_bytes": (u64, [P]),
             "agj_batch_free": (None, [P]),
             "agj_join_batched": (i32, [P, P, P, u32, P, P]),
+            "agj_server_create": (i32, [P, u32, P, P]),
+            "agj_server_submit": (i32, [P, u32, P, u64, P, P, u64, P]),
+            "agj_server_poll": (i32, [P, u64, i32, P]),
+            "agj_server_drain": (i32, [P]),
+            "agj_server_get_stats": (i32, [P, i32, P]),
+            "agj_server_destroy": (None, [P]),
+            "agj_server_load": (i32, [P, P, P]),
+            "agj_plain_load": (i32, [P, u32, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -378,6 +424,103 @@ def join_batched(indexes, points, pairs: list | None = None, stream=None) -> lis
         q.n = int(p.shape[0])
     _check(lib().agj_join_batched(hs, pp, nn, m, _stream_ptr(stream), arr), "agj_join_batched")
     return pairs
+
+
+class Server:
+    """The served form (agj_server_*): continuous batching of host point
+    requests over resident indexes."""
+
+    def __init__(self, indexes, n_slots: int = 0, max_step_requests: int = 0, max_step_points: int = 0,
+                 hbm_budget_bytes: int = 0, max_pending: int = 0, points_per_lane: int = 0, ctas_per_sm: int = 0):
+        self.indexes = list(indexes)
+        hs = (C.c_void_p * len(self.indexes))(*[ix.handle for ix in self.indexes])
+        o = ServerOpts(n_slots, max_step_requests, max_step_points, hbm_budget_bytes, max_pending, points_per_lane,
+                       ctas_per_sm)
+        h = C.c_void_p()
+        _check(lib().agj_server_create(hs, len(self.indexes), C.byref(o), C.byref(h)), "agj_server_create")
+        self._h = h
+        self._live = {}
+
+    def submit(self, index_id: int, points: np.ndarray, keep: bool = True) -> int:
+        """Queues a request; with keep, its CSR is returned by poll()."""
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 2)
+        n = pts.shape[0]
+        t = C.c_uint64()
+        if keep:
+            cap = n * max(self.indexes[index_id].stats()["max_refs"], 1)
+            off = np.empty(n + 1, dtype=np.uint32)
+            ids = np.empty(max(cap, 1), dtype=np.uint32)
+            rc = lib().agj_server_submit(self._h, index_id, _np_ptr(pts), n, _np_ptr(off), _np_ptr(ids), cap,
+                                         C.byref(t))
+        else:
+            off = ids = None
+            rc = lib().agj_server_submit(self._h, index_id, _np_ptr(pts), n, None, None, 0, C.byref(t))
+        _check(rc, "agj_server_submit")
+        self._live[int(t.value)] = (pts, off, ids)
+        return int(t.value)
+
+    def poll(self, ticket: int, wait: bool = True):
+        """(offsets, ids, result dict) of a kept request, or None while it runs."""
+        r = RequestResult()
+        rc = lib().agj_server_poll(self._h, ticket, 1 if wait else 0, C.byref(r))
+        if rc == 7 and not wait:      # AGJ_EBUSY
+            return None
+        _check(rc, "agj_server_poll")
+        pts, off, ids = self._live.pop(ticket)
+        res = {k: getattr(r, k) for k, _ in r._fields_ if k != "reserved"}
+        _check(r.status, "served request")
+        return off, ids[: r.nnz].copy(), res
+
+    def drain(self):
+        _check(lib().agj_server_drain(self._h), "agj_server_drain")
+        for t in [t for t, v in self._live.items() if v[1] is None]:
+            self._live.pop(t)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(lib().agj_server_get_stats(self._h, 1 if reset else 0, C.byref(st)), "agj_server_get_stats")
+        return st.as_dict()
+
+    def load(self, spec: "LoadSpecPy") -> dict:
+        res = LoadResult()
+        _check(lib().agj_server_load(self._h, C.byref(spec.c), C.byref(res)), "agj_server_load")
+        return res.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().agj_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LoadSpecPy:
+    """agj_load_spec with the arrays it points to kept alive."""
+
+    def __init__(self, rate: float, n_requests: int, pools, approx_index, exact_index=None, zipf_alpha: float = 1.2,
+                 max_points: int = 65536, exact_fraction: float = 0.0, seed: int = 0, warmup_requests: int = 0):
+        self.pools = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 2) for p in pools]
+        n_sets = len(self.pools)
+        self._ptrs = (C.c_void_p * n_sets)(*[p.ctypes.data for p in self.pools])
+        self._counts = (C.c_uint64 * n_sets)(*[p.shape[0] for p in self.pools])
+        self._approx = (C.c_uint32 * n_sets)(*approx_index)
+        self._exact = (C.c_uint32 * n_sets)(*(exact_index if exact_index is not None else [0xFFFFFFFF] * n_sets))
+        self.c = LoadSpec(rate, n_requests, zipf_alpha, max_points, n_sets, exact_fraction,
+                          C.cast(self._approx, C.c_void_p), C.cast(self._exact, C.c_void_p),
+                          C.cast(self._ptrs, C.c_void_p), C.cast(self._counts, C.c_void_p), seed, warmup_requests)
+
+
+def plain_load(indexes, spec: LoadSpecPy) -> dict:
+    """The spec's arrivals served one request at a time by agj_join_host."""
+    hs = (C.c_void_p * len(indexes))(*[ix.handle for ix in indexes])
+    res = LoadResult()
+    _check(lib().agj_plain_load(hs, len(indexes), C.byref(spec.c), C.byref(res)), "agj_plain_load")
+    return res.as_dict()
 
 
 def supercover(cells, refs):

@@ -1,0 +1,139 @@
+"""GPU tests of the served form: requests served by continuous batching
+(many requests per launch, several launches in flight) give exactly the
+plain join's CSR for their points - alone and in the mix - and the CPU
+oracle's; the Poisson load generator and the plain per-request baseline
+run and account for every request."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def agj(torch):
+    import paper_1802_09488_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def sets(agj):
+    """Two polygon sets, each with an approximate (eps 4 m) and an exact
+    index, and a point pool per set."""
+    from paper_1802_09488_gb300 import synth
+    out = []
+    for k, (n_polys, box) in enumerate([(5, synth.BOX_C1), (60, synth.BOX_CITY)]):
+        polys = synth.voronoi_tiling(n_polys, box, seed=50 + k, vmin=8 if n_polys <= 16 else 20,
+                                     vmax=64 if n_polys <= 16 else 200)
+        pool = synth.points_mixture(200_000, box, seed=60 + k)
+        ax = agj.Index(polys, agj.APPROX, 4.0)
+        ex = agj.Index(polys, agj.EXACT, 0, train=pool[:2000])
+        out.append((polys, pool, ax, ex))
+    return out
+
+
+def _indexes(sets):
+    return [s[2] for s in sets] + [s[3] for s in sets]   # ids: approx 0..S-1, exact S..2S-1
+
+
+def _requests(sets, count, seed, max_points=4000):
+    rng = np.random.default_rng(seed)
+    S = len(sets)
+    reqs = []
+    for i in range(count):
+        s = int(rng.integers(0, S))
+        exact = bool(rng.random() < 0.3)
+        n = int(min(max_points, np.floor(rng.pareto(1.2)) + 1))
+        if i % 50 == 7:
+            n = 0 if i % 100 == 7 else 1
+        start = int(rng.integers(0, sets[s][1].shape[0] - max(n, 1)))
+        reqs.append((s + (S if exact else 0), sets[s][1][start:start + n]))
+    return reqs
+
+
+def _plain(torch, agj, ix, pts):
+    if len(pts) == 0:
+        return np.zeros(1, np.uint32), np.zeros(0, np.uint32)
+    pr = agj.join(ix, torch.from_numpy(np.ascontiguousarray(pts)).cuda())
+    off, ids = pr.to_host()
+    return off.copy(), ids.copy()
+
+
+def test_server_mix_equals_alone_and_plain(torch, agj, oracle, sets):
+    idx = _indexes(sets)
+    reqs = _requests(sets, 600, seed=1)
+    srv = agj.Server(idx, n_slots=3, max_step_requests=256, max_step_points=1 << 16)
+    tickets = [srv.submit(i, p) for i, p in reqs]          # a burst: many requests per launch
+    mixed = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["steps"] < len(reqs) and st["step_requests_max"] > 1
+    steps = np.array([m[2]["step"] for m in mixed])
+    assert len(np.unique(steps)) < len(reqs)
+    for k in range(0, len(reqs), 7):                       # alone: one request per launch
+        i, p = reqs[k]
+        off, ids, res = srv.poll(srv.submit(i, p))
+        assert np.array_equal(off, mixed[k][0]) and np.array_equal(ids, mixed[k][1]), k
+    for k, (i, p) in enumerate(reqs):
+        off, ids = _plain(torch, agj, idx[i], p)
+        assert np.array_equal(mixed[k][0], off), k
+        assert np.array_equal(mixed[k][1], ids), k
+        assert mixed[k][2]["nnz"] == len(ids)
+        r = mixed[k][2]
+        assert r["t_submit_ns"] <= r["t_start_ns"] <= r["t_done_ns"]
+    # a few requests against the oracle directly
+    S = len(sets)
+    for k in range(0, len(reqs), 97):
+        i, p = reqs[k]
+        polys = sets[i % S][0]
+        if len(p) == 0:
+            continue
+        if i >= S:
+            eo, ei = oracle.PolySet(polys).join_exact(p)
+        else:
+            cells, ro, refs = idx[i].logical()
+            eo, ei = oracle.join_approx_logical(cells, ro, refs, p)
+        assert np.array_equal(np.asarray(mixed[k][0], np.int64), np.asarray(eo, np.int64))
+        assert np.array_equal(np.asarray(mixed[k][1], np.int64), np.asarray(ei, np.int64))
+    srv.close()
+
+
+def test_server_limits(torch, agj, sets):
+    idx = _indexes(sets)
+    srv = agj.Server(idx, n_slots=1, max_step_requests=4, max_step_points=1000)
+    with pytest.raises(agj.AgjError):
+        srv.submit(0, sets[0][1][:1001])                   # larger than a launch
+    # more requests than a launch takes: served over several launches
+    ts = [srv.submit(1, sets[1][1][k * 300:(k + 1) * 300]) for k in range(10)]
+    outs = [srv.poll(t) for t in ts]
+    assert len({o[2]["step"] for o in outs}) >= 3
+    for k, o in enumerate(outs):
+        off, ids = _plain(torch, agj, idx[1], sets[1][1][k * 300:(k + 1) * 300])
+        assert np.array_equal(o[0], off) and np.array_equal(o[1], ids)
+    srv.close()
+
+
+def test_server_and_plain_load(torch, agj, sets):
+    idx = _indexes(sets)
+    S = len(sets)
+    spec = agj.LoadSpecPy(rate=20_000, n_requests=3000, pools=[s[1] for s in sets], approx_index=list(range(S)),
+                          exact_index=list(range(S, 2 * S)), zipf_alpha=1.2, max_points=8192, exact_fraction=0.1,
+                          seed=5, warmup_requests=300)
+    srv = agj.Server(idx, n_slots=4, max_step_points=1 << 17)
+    r = srv.load(spec)
+    assert r["requests"] == 2700 and r["rejected"] == 0
+    assert 0 < r["p50_us"] <= r["p99_us"] <= r["max_us"]
+    assert r["points_per_s"] > 0
+    srv.close()
+    spec_small = agj.LoadSpecPy(rate=20_000, n_requests=500, pools=[s[1] for s in sets], approx_index=list(range(S)),
+                                exact_index=list(range(S, 2 * S)), zipf_alpha=1.2, max_points=8192,
+                                exact_fraction=0.1, seed=5, warmup_requests=50)
+    p = agj.plain_load(idx, spec_small)
+    assert p["requests"] == 450 and p["p50_us"] > 0
