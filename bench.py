@@ -32,8 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "points joined/sec at 1 GB300 (approx eps and exact) vs plain join; p50/p99 latency"
-# approx: k_zero, k_probe_approx, k_scan_counts, k_emit_approx
-# exact:  k_zero, k_probe_exact, k_poly_scan, k_scatter, k_pip, k_scan_counts, k_emit_exact
+# approx: k_zero, k_probe<approx>, k_scan_counts, k_emit<approx>
+# exact:  k_zero, k_probe<exact>, k_count, k_poly_scan, k_scatter, k_pip, k_scan_counts, k_emit<exact>
 LAUNCHES_PER_STEP = {"approx": 4, "exact": 8}
 
 
@@ -46,7 +46,117 @@ def parse():
     ap.add_argument("--n-points", type=int, default=100_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
     return ap.parse_args()
+
+
+# Batched form: 64 (polygon set, point batch) jobs, polygon counts and batch
+# sizes log-uniform (per-job seeds), every second job exact.  The polygon
+# range is cut from 5-40 000 to 5-300 so that generating and indexing the
+# 64 sets stays within the bench's time budget.
+C4 = {"m": 64, "seed": 11, "polys": (5, 300), "points": (1_000, 10_000_000)}
+# Served form: 16 resident sets (approximate eps = 4 m and exact index each),
+# Poisson arrivals at 2e5 requests/s, sizes 1-65 536 Zipf(1.2), 10 % exact.
+# Set sizes cut from 300-40 000 to 300-1 500 polygons for the same reason.
+C5 = {"sets": 16, "polys": (300, 1500), "rate": 2e5, "requests": 300_000, "warmup": 50_000, "zipf": 1.2,
+      "max_points": 65536, "exact_fraction": 0.1, "plain_requests": 5_000, "saturate_rate": 1e6}
+
+
+def batched_form(agj, torch, reps: int = 10) -> dict:
+    """64 plain joins in sequence vs one batched plan (graph replay) over the
+    same jobs, with the autotuned tiling; outputs compared job by job."""
+    import numpy as np
+    from paper_1802_09488_gb300 import autotune, synth
+    t0 = time.perf_counter()
+    jobs = synth.batched_jobs(m=C4["m"], seed=C4["seed"], polys=C4["polys"], points=C4["points"])
+    idx = [agj.Index(j.polygons, agj.EXACT, 0, train=j.train) if j.exact else agj.Index(j.polygons, agj.APPROX, j.eps_m)
+           for j in jobs]
+    prep_s = time.perf_counter() - t0
+    pts = [torch.from_numpy(j.points).cuda() for j in jobs]
+    ns = [len(j.points) for j in jobs]
+    N = sum(ns)
+    s = torch.cuda.current_stream()
+    plain_pairs = [agj.Pairs(ix, n) for ix, n in zip(idx, ns)]
+
+    def time_it(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sorted(ts)[len(ts) // 2]
+
+    def plain():
+        for ix, p, pr in zip(idx, pts, plain_pairs):
+            agj.join(ix, p, pr)
+
+    plain_ms = time_it(plain)
+    ref = [pr.to_host() for pr in plain_pairs]
+    tuned = autotune.tune(idx, pts, use_cache=False)
+    plan = agj.Batch(idx, ns, points_per_lane=tuned["points_per_lane"], ctas_per_sm=tuned["ctas_per_sm"])
+    bp = plan.pairs()
+    batch_ms = time_it(lambda: plan.run(pts, bp))
+    same = all(np.array_equal(a[0], b.to_host()[0]) and np.array_equal(a[1], b.to_host()[1]) for a, b in zip(ref, bp))
+    out = {"workload": (f"c4-reduced: {C4['m']} jobs, polygons log-uniform {C4['polys'][0]}-{C4['polys'][1]}, "
+                        f"points log-uniform {C4['points'][0]:.0e}-{C4['points'][1]:.0e}, every 2nd job exact"),
+           "points": N, "plain_ms": plain_ms, "batched_ms": batch_ms,
+           "plain_points_per_s": N / (plain_ms / 1e3), "batched_points_per_s": N / (batch_ms / 1e3),
+           "speedup_vs_plain": plain_ms / batch_ms, "identical_output": bool(same),
+           "tiling": {"points_per_lane": tuned["points_per_lane"], "ctas_per_sm": tuned["ctas_per_sm"],
+                      "sweep": tuned["sweep"]},
+           "graph": True, "prep_s": prep_s}
+    plan.close()
+    return out
+
+
+def served_form(agj) -> dict:
+    """Poisson requests through the server (continuous batching) vs the same
+    arrivals served one plain join per request."""
+    import numpy as np
+    from paper_1802_09488_gb300 import synth
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(21)
+    lo, hi = C5["polys"]
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), C5["sets"])).round().astype(int)
+    pools, idx_a, idx_e = [], [], []
+    for k, npl in enumerate(sizes):
+        polys = synth.voronoi_tiling(int(npl), synth.BOX_CITY, seed=300 + k, vmin=20, vmax=400) if npl <= 1000 \
+            else synth.c3_fine_polygons(int(npl), seed=300 + k)
+        pools.append(synth.points_mixture(1 << 20, synth.BOX_CITY, seed=400 + k, dist_seed=300 + k))
+        idx_a.append(agj.Index(polys, agj.APPROX, 4.0))
+        idx_e.append(agj.Index(polys, agj.EXACT, 0, train=pools[-1][:10_000]))
+    idx = idx_a + idx_e
+    S = C5["sets"]
+    prep_s = time.perf_counter() - t0
+
+    def spec(rate, n, warm):
+        return agj.LoadSpecPy(rate=rate, n_requests=n, pools=pools, approx_index=list(range(S)),
+                              exact_index=list(range(S, 2 * S)), zipf_alpha=C5["zipf"], max_points=C5["max_points"],
+                              exact_fraction=C5["exact_fraction"], seed=7, warmup_requests=warm)
+
+    srv = agj.Server(idx, n_slots=4, max_step_points=1 << 20)
+    r = srv.load(spec(C5["rate"], C5["requests"], C5["warmup"]))
+    st = srv.stats()
+    sat = srv.load(spec(C5["saturate_rate"], int(C5["saturate_rate"]), int(C5["saturate_rate"] // 4)))
+    srv.close()
+    p = agj.plain_load(idx, spec(C5["rate"], C5["plain_requests"], C5["plain_requests"] // 10))
+    keys = ("achieved_rate", "points_per_s", "p50_us", "p99_us", "mean_us", "max_us", "requests", "rejected")
+    return {"workload": (f"c5-reduced: {S} resident sets of {lo}-{hi} polygons (approx eps 4 m + exact index each), "
+                         f"Poisson {C5['rate']:.0e} req/s, Zipf({C5['zipf']}) sizes 1-{C5['max_points']}, "
+                         f"{C5['exact_fraction']:.0%} exact"),
+            "served": {k: r[k] for k in keys} | {"steps": st["steps"], "max_requests_per_step": st["step_requests_max"],
+                                                 "slots": st["n_slots"], "slot_device_bytes": st["device_bytes"]},
+            "served_saturated": {k: sat[k] for k in keys} | {"offered_rate": sat["offered_rate"]},
+            "plain_per_request": {k: p[k] for k in keys},
+            "speedup_points_per_s_vs_plain": r["points_per_s"] / max(p["points_per_s"], 1e-9),
+            "capacity_vs_plain": sat["points_per_s"] / max(p["points_per_s"], 1e-9),
+            "index_device_bytes": sum(ix.stats()["device_bytes"] for ix in idx), "prep_s": prep_s}
 
 
 class ClockSampler:
@@ -353,6 +463,13 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cells, ro, refs = ia.logical()
         result["cpu_baseline"] = cpu_oracle_rate(polys, cells, ro, refs, pts_np)
+
+    if rank == 0 and not args.no_forms:
+        del pa, pe, d_pts
+        torch.cuda.empty_cache()
+        result["batched"] = batched_form(agj, torch)
+        torch.cuda.empty_cache()
+        result["served"] = served_form(agj)
 
     if dist is not None:
         dist.barrier()
