@@ -350,6 +350,10 @@ int agj_join_batched(const agj_index* const* indexes, const double* const* d_poi
  * pinned host buffers sized at creation: a launch admits requests while
  * their points (max_step_points), output ids and work space fit the slot.
  * Each request's result is exactly what agj_join computes for its points.
+ * Request points are read by the probe kernels from the client's host
+ * buffer where the device can read pageable host memory (see
+ * AGJ_SERVER_STAGE_POINTS), else staged; results come back through the
+ * slot's pinned buffers.
  *
  * agj_server_create: indexes (built on the current device) are borrowed and
  * must outlive the server; requests name them by position.  opts may be
@@ -366,7 +370,14 @@ typedef struct {
     uint64_t max_pending;        /* queued requests before submit answers AGJ_EBUSY, 0 = 2^20 */
     uint32_t points_per_lane;    /* as agj_batch_opts, 0 = 2 */
     uint32_t ctas_per_sm;        /* as agj_batch_opts */
+    uint32_t flags;              /* AGJ_SERVER_STAGE_POINTS */
+    uint32_t reserved;
 } agj_server_opts;
+/* Where the device can read pageable host memory (GB300: NVLink-C2C with
+ * the host's page tables), the probe reads each request's points straight
+ * from the client's buffer; this flag copies them through pinned staging
+ * buffers and one host-to-device copy per launch instead. */
+#define AGJ_SERVER_STAGE_POINTS 1u
 int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const agj_server_opts* opts,
                       agj_server** out);
 
@@ -397,7 +408,8 @@ int agj_server_drain(agj_server* server);
 
 typedef struct {
     uint64_t submitted, completed, rejected, points, steps, step_requests_max;
-    uint32_t n_slots, reserved;
+    uint32_t n_slots;
+    uint32_t host_reads;         /* 1: the probe reads request points from host memory */
     uint64_t device_bytes;       /* device memory of the slots */
     double p50_us, p99_us, mean_us, max_us;   /* submit-to-done latency of completed requests */
 } agj_server_stats;

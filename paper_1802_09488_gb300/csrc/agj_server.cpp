@@ -41,7 +41,6 @@ uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
 }
 
-uint64_t round16(uint64_t x) { return (x + 15) & ~15ull; }
 uint64_t round256(uint64_t x) { return (x + 255) & ~255ull; }
 
 struct Request {
@@ -76,6 +75,7 @@ struct agj_server {
     std::vector<const agj::Index*> X;
     int device = 0;
     int ppt = 2, ctas = 0;
+    bool host_reads = false;       // kernels read request points from host memory
     uint32_t n_slots = 4, max_req = 4096;
     uint64_t max_pts = 1ull << 20, max_ids = 0, max_pending = 1ull << 20;
     std::vector<Slot> slots;
@@ -183,15 +183,20 @@ bool launch_step(agj_server* S, Slot& sl) {
         sl.pofs[j] = po;
         sl.oofs[j] = oo;
         sl.iofs[j] = io;
-        memcpy(sl.h_mem + sl.h_off_pts + po, r->h_points, r->n * 16);
-        dp[j] = reinterpret_cast<const double*>(d_pts + po);
+        const bool direct = S->host_reads && (reinterpret_cast<uintptr_t>(r->h_points) & 15u) == 0;
+        if (direct) {
+            dp[j] = r->h_points;                 // read by the probe over the host link
+        } else {
+            memcpy(sl.h_mem + sl.h_off_pts + po, r->h_points, r->n * 16);
+            dp[j] = reinterpret_cast<const double*>(d_pts + po);
+            po += r->n * 16;
+        }
         agj_pairs& o = outs[j];
         memset(&o, 0, sizeof o);
         o.offsets = reinterpret_cast<uint32_t*>(sl.d_mem + sl.off_off) + oo;
         o.ids = reinterpret_cast<uint32_t*>(sl.d_mem + sl.off_ids) + io;
         o.ids_capacity = r->n * std::max<uint64_t>(xs[j]->stats.max_refs, 1);
         o.status = reinterpret_cast<uint64_t*>(sl.d_mem + sl.off_status) + 4 * j;
-        po += round16(r->n * 16);
         oo += r->n + 1;
         io += o.ids_capacity;
     }
@@ -306,6 +311,14 @@ int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const
     if (o.max_pending) S->max_pending = o.max_pending;
     S->ppt = o.points_per_lane ? (int)o.points_per_lane : 2;
     S->ctas = (int)o.ctas_per_sm;
+    {
+        int pageable = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+            cudaGetLastError();
+            pageable = 0;
+        }
+        S->host_reads = pageable == 1 && !(o.flags & AGJ_SERVER_STAGE_POINTS);
+    }
     if (S->n_slots > 64 || S->max_req > 65535 || S->max_pts >= (1ull << 31)) { delete S; return AGJ_EINVAL; }
     S->max_ids = S->max_pts * max_refs;
     // work space of the largest step a slot admits
@@ -430,6 +443,7 @@ int agj_server_get_stats(agj_server* S, int reset, agj_server_stats* out) {
     out->steps = S->steps;
     out->step_requests_max = S->step_req_max;
     out->n_slots = S->n_slots;
+    out->host_reads = S->host_reads ? 1u : 0u;
     out->device_bytes = S->device_bytes;
     std::vector<double> v;
     v.reserve(S->latencies.size());

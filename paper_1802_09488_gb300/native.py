@@ -65,7 +65,7 @@ class Requirements(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("n_slots", C.c_uint32), ("max_step_requests", C.c_uint32), ("max_step_points", C.c_uint64),
                 ("hbm_budget_bytes", C.c_uint64), ("max_pending", C.c_uint64), ("points_per_lane", C.c_uint32),
-                ("ctas_per_sm", C.c_uint32)]
+                ("ctas_per_sm", C.c_uint32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class RequestResult(C.Structure):
@@ -76,7 +76,7 @@ class RequestResult(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
                 ("points", C.c_uint64), ("steps", C.c_uint64), ("step_requests_max", C.c_uint64),
-                ("n_slots", C.c_uint32), ("reserved", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("n_slots", C.c_uint32), ("host_reads", C.c_uint32), ("device_bytes", C.c_uint64),
                 ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -431,11 +431,12 @@ class Server:
     requests over resident indexes."""
 
     def __init__(self, indexes, n_slots: int = 0, max_step_requests: int = 0, max_step_points: int = 0,
-                 hbm_budget_bytes: int = 0, max_pending: int = 0, points_per_lane: int = 0, ctas_per_sm: int = 0):
+                 hbm_budget_bytes: int = 0, max_pending: int = 0, points_per_lane: int = 0, ctas_per_sm: int = 0,
+                 stage_points: bool = False):
         self.indexes = list(indexes)
         hs = (C.c_void_p * len(self.indexes))(*[ix.handle for ix in self.indexes])
         o = ServerOpts(n_slots, max_step_requests, max_step_points, hbm_budget_bytes, max_pending, points_per_lane,
-                       ctas_per_sm)
+                       ctas_per_sm, 1 if stage_points else 0, 0)
         h = C.c_void_p()
         _check(lib().agj_server_create(hs, len(self.indexes), C.byref(o), C.byref(h)), "agj_server_create")
         self._h = h

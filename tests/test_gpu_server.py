@@ -67,10 +67,16 @@ def _plain(torch, agj, ix, pts):
     return off.copy(), ids.copy()
 
 
-def test_server_mix_equals_alone_and_plain(torch, agj, oracle, sets):
+@pytest.mark.parametrize("stage_points", [False, True])
+def test_server_mix_equals_alone_and_plain(torch, agj, oracle, sets, stage_points):
+    """Points read by the kernels from the client's host buffers (where the
+    device reads pageable memory) or staged through pinned buffers."""
     idx = _indexes(sets)
     reqs = _requests(sets, 600, seed=1)
-    srv = agj.Server(idx, n_slots=3, max_step_requests=256, max_step_points=1 << 16)
+    srv = agj.Server(idx, n_slots=3, max_step_requests=256, max_step_points=1 << 16, stage_points=stage_points)
+    assert srv.stats()["host_reads"] in (0, 1)
+    if stage_points:
+        assert srv.stats()["host_reads"] == 0
     tickets = [srv.submit(i, p) for i, p in reqs]          # a burst: many requests per launch
     mixed = [srv.poll(t) for t in tickets]
     st = srv.stats()
@@ -128,6 +134,13 @@ def test_server_and_plain_load(torch, agj, sets):
                           seed=5, warmup_requests=300)
     srv = agj.Server(idx, n_slots=4, max_step_points=1 << 17)
     r = srv.load(spec)
+    # unaligned client buffers are staged, aligned ones read in place
+    raw = np.empty(2 * 5000 + 1, dtype=np.float64)
+    odd = raw[1:].reshape(-1, 2)
+    odd[:] = sets[1][1][:5000]
+    off, ids, _ = srv.poll(srv.submit(1, odd))
+    ref = _plain(torch, agj, idx[1], sets[1][1][:5000])
+    assert np.array_equal(off, ref[0]) and np.array_equal(ids, ref[1])
     assert r["requests"] == 2700 and r["rejected"] == 0
     assert 0 < r["p50_us"] <= r["p99_us"] <= r["max_us"]
     assert r["points_per_s"] > 0
