@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    ap.add_argument("--workload", choices=["c2", "c3", "c1"], default="c2",
+                    help="c2: city (default); c3: 40 000 fine overlapping polygons; c1: 5 polygons, uniform points")
+    ap.add_argument("--eps", type=float, default=None, help="approximate precision in metres (default per workload)")
     return ap.parse_args()
 
 
@@ -223,12 +226,27 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def workload(n: int, rank: int):
+WORKLOADS = {
+    "c2": {"name": "c2-city-300polys-mixture-points", "eps": 4.0},
+    "c3": {"name": "c3-fine-40000polys-overlapping-mixture-points", "eps": 10.0},
+    "c1": {"name": "c1-tiny-5polys-uniform-points", "eps": 10.0},
+}
+
+
+def workload(name: str, n: int, rank: int):
     from paper_1802_09488_gb300 import synth
-    polys = synth.c2_city_polygons()
-    seed = 3 + 1000 * rank
-    pts = synth.points_mixture(n, synth.BOX_CITY, seed=seed, dist_seed=3)
-    train = synth.points_mixture(max(n // 100, 1000), synth.BOX_CITY, seed=4, dist_seed=3)
+    if name == "c3":
+        polys = synth.c3_fine_polygons(40_000, seed=5)
+        pts = synth.points_mixture(n, synth.BOX_CITY, seed=6 + 1000 * rank, dist_seed=5)
+        train = synth.points_mixture(max(n // 100, 1000), synth.BOX_CITY, seed=7, dist_seed=5)
+    elif name == "c1":
+        polys = synth.voronoi_tiling(5, synth.BOX_C1, seed=1, vmin=8, vmax=64)
+        pts = synth.points_uniform(n, synth.BOX_C1, seed=0 + 1000 * rank)
+        train = synth.points_uniform(max(n // 100, 1000), synth.BOX_C1, seed=2)
+    else:
+        polys = synth.c2_city_polygons()
+        pts = synth.points_mixture(n, synth.BOX_CITY, seed=3 + 1000 * rank, dist_seed=3)
+        train = synth.points_mixture(max(n // 100, 1000), synth.BOX_CITY, seed=4, dist_seed=3)
     return polys, pts, train
 
 
@@ -267,8 +285,9 @@ def run_reference(args, rank: int):
         return
     import paper_1802_09488_gb300 as agj
     n = min(args.n_points, 20_000_000)
-    polys, pts, train = workload(n, 0)
-    ix = agj.Index(polys, agj.APPROX, 4.0, host_only=True)
+    polys, pts, train = workload(args.workload, n, 0)
+    eps = args.eps if args.eps is not None else WORKLOADS[args.workload]["eps"]
+    ix = agj.Index(polys, agj.APPROX, eps, host_only=True)
     cells, ro, refs = ix.logical()
     import oracle
     ps = oracle.PolySet(polys)
@@ -295,7 +314,7 @@ def run_reference(args, rank: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "c2-city-300polys-mixture-points", "eps_m": 4.0, "exact_train": "1% sample",
+            "config": {"workload": WORKLOADS[args.workload]["name"], "eps_m": eps, "exact_train": "1% sample",
                        "step": "approx join + exact join of the same points",
                        "reference": "CPU oracle (oracle/oracle.c) on the host cores, bounded sample per step"},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
@@ -329,9 +348,10 @@ def main():
         torch.cuda.synchronize()
 
     n = args.n_points
-    polys, pts_np, train = workload(n, rank)
+    polys, pts_np, train = workload(args.workload, n, rank)
+    eps = args.eps if args.eps is not None else WORKLOADS[args.workload]["eps"]
     t0 = time.perf_counter()
-    ia = agj.Index(polys, agj.APPROX, 4.0)
+    ia = agj.Index(polys, agj.APPROX, eps)
     ie = agj.Index(polys, agj.EXACT, 0.0, train=train)
     build_s = time.perf_counter() - t0
     d_pts = torch.from_numpy(pts_np).cuda()
@@ -417,9 +437,12 @@ def main():
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "c2-city-300polys-1e8-mixture-points", "n_points_per_gpu": n, "polygons": len(polys),
-                   "eps_m": 4.0, "exact_train_points": len(train), "step": "approx join + exact join of the same points",
-                   "l2": "inputs (16 B x 1e8 = 1.6 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"{WORKLOADS[args.workload]['name']}-{n:.0e}".replace("+", ""), "n_points_per_gpu": n,
+                   "polygons": len(polys), "eps_m": eps, "exact_train_points": len(train),
+                   "step": "approx join + exact join of the same points",
+                   "l2": f"inputs (16 B x {n:.0e} = {16 * n / 1e9:.2f} GB) " + ("larger than L2, no flush" if 16 * n > 2e8
+                                                                                 else "smaller than L2: warm-cache figure"),
+                   "parallelism": f"replicas x{world}"},
         "modes": {
             "approx": {"points_per_s": n / (statistics.mean(approx_ms) / 1000.0), "p50_ms": pct(approx_ms, 50),
                        "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_per_pt,
@@ -467,7 +490,7 @@ def main():
         cells, ro, refs = ia.logical()
         result["cpu_baseline"] = cpu_oracle_rate(polys, cells, ro, refs, pts_np)
 
-    if rank == 0 and not args.no_forms:
+    if rank == 0 and not args.no_forms and args.workload == "c2":
         del pa, pe, d_pts
         torch.cuda.empty_cache()
         result["batched"] = batched_form(agj, torch)

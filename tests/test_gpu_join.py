@@ -196,3 +196,31 @@ def test_fast_ids_match_fp64_path(torch, agj, oracle):
         os_, ids_ = ps_.to_host()
         assert ps_.fallbacks() == 0
         _csr_equal(of, idf, os_, ids_)
+
+
+@pytest.fixture(scope="module")
+def c3_small():
+    """The fine-polygon workload's structure at a tenth of its polygon count:
+    a Voronoi tessellation over a skewed seed field, each polygon scaled
+    about its centroid so that points hit 0-3 polygons."""
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c3_fine_polygons(4000, seed=5)
+    pts = synth.points_mixture(300_000, synth.BOX_CITY, seed=6, dist_seed=5)
+    train = synth.points_mixture(30_000, synth.BOX_CITY, seed=7, dist_seed=5)
+    return polys, pts, train
+
+
+@pytest.mark.parametrize("mode,eps", [("approx", 1.0), ("approx", 10.0), ("exact", 0.0)])
+def test_c3_fine_overlapping_polygons(torch, agj, oracle, c3_small, mode, eps):
+    polys, pts, train = c3_small
+    if mode == "exact":
+        ix = agj.Index(polys, agj.EXACT, 0, train=train)
+        eo, ei = oracle.PolySet(polys).join_exact(pts)
+    else:
+        ix = agj.Index(polys, agj.APPROX, eps)
+        cells, ro, refs = ix.logical()
+        eo, ei = oracle.join_approx_logical(cells, ro, refs, pts)
+    off, ids = agj.join(ix, _dev(torch, pts)).to_host()
+    _csr_equal(off, ids, eo, ei)
+    hits = np.diff(np.asarray(off, np.int64))
+    assert hits.max() >= 2 and (hits == 0).any()       # overlaps and gaps are exercised
