@@ -423,8 +423,8 @@ def main():
     t_pe = mean(stages["exact"]["k_probe_exact"])
     r_pa = roof("k_probe_approx", 16 + 8 * gathers_per_pt + 8, t_pa,
                 "16 B point + 8 B per trie entry read + 8 B entry written, per point")
-    r_pe = roof("k_probe_exact", 16 + 8 * gathers_per_pt + 8 + 12 * cands_per_pt, t_pe,
-                "16 B point + 8 B per trie entry read + 8 B entry + 12 B per candidate queued, per point")
+    r_pe = roof("k_probe_exact", 16 + 8 * gathers_per_pt + 8 + 8 * cands_per_pt, t_pe,
+                "16 B point + 8 B per trie entry read + 8 B entry + 8 B per candidate queued, per point")
     roofline = r_pa if t_pa >= t_pe else r_pe
     join_roof = roof("approx join (probe + scan + emit)", 16 + 8 * gathers_per_pt + 4 + 4 * k_pts, mean(approx_ms),
                      "the method's bytes: 16 B point + 8 B per trie entry + 4 B offset + 4 B per pair")

@@ -49,7 +49,7 @@ def up_to_date() -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Builds libagj.so; extra nvcc flags may come from $AGJ_NVCC_EXTRA (for
-    example -DAGJ_PROBE_MIN_BLOCKS=4)."""
+    example -DAGJ_PROBE_MIN_BLOCKS=6)."""
     if not force and up_to_date():
         return LIB
     if not os.path.exists(NVCC):

@@ -163,7 +163,7 @@ cudaError_t enqueue_kernels(const Shape& S, char* base, int ctas_per_sm, cudaStr
         // the emit is short and latency-bound: a full-occupancy grid
         G.emit_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)G.sms * 8));
     }
-    G.pip_grid = G.sms * 4;
+    G.pip_grid = G.sms * AGJ_PIP_MIN_BLOCKS;
     G.tile_job = src.tile_job;
     G.job_base = reinterpret_cast<uint32_t*>(base + S.off_job_base);
     return enqueue_join<PPT, ManyJobs, kModeAny>(src, S.L, base + S.off_scratch, G, nullptr, 0, s, nullptr);

@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue
 // on its own tile state, so no CTA barrier follows the setup.  Warp tiles are
 // numbered from the CTA's ticket (the order CTAs started), which keeps the
 // look-back free of deadlock.
+constexpr int kNoAllocMinBlocks = 3;   // its PPT = 4 walks need the registers of 3 CTAs per SM
 template <int PPT>
-__global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS) k_join_approx(
+__global__ void __launch_bounds__(kJoinBlock, kNoAllocMinBlocks) k_join_approx(
     DevIndex X, const double2* __restrict__ pts, uint32_t n, uint32_t* __restrict__ offsets,
     uint32_t* __restrict__ ids, uint64_t ids_cap, uint64_t* __restrict__ tiles, uint32_t* __restrict__ tile_counter,
     uint64_t* __restrict__ status, uint64_t* __restrict__ fallback_counter) {
@@ -458,7 +459,7 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
     G.probe_grid = (int)((L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);   // one warp per tile
     G.emit_grid = G.probe_grid;
     G.sms = sm_count();
-    G.pip_grid = G.sms * 4;
+    G.pip_grid = G.sms * AGJ_PIP_MIN_BLOCKS;
     const cudaError_t e =
         X.mode == AGJ_APPROX
             ? enqueue_join<kJoinPPT, OneJob, kModeApprox>(src, L, sc, G, out->status, 4, s, events)

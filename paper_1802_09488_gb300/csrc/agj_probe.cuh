@@ -23,8 +23,17 @@ namespace agj {
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 static __device__ const HilbertLut g_hilbert_lut = make_hilbert_lut();
 constexpr uint32_t kSpinLimit = 1u << 22;
+// Resident CTAs per SM the probe kernels are compiled for (a register cap:
+// 65536 / (256 x blocks) per thread).  The probe is latency-bound (dependent
+// trie gathers), so more resident warps pay while the registers last: at 5
+// CTAs (40 warps, 48 registers) both the single-job and the batched probe
+// beat 3 and 4 CTAs on the city workload although the batched one spills a
+// little; at 6 the single-job probe spills more and the exact probe slows.
 #ifndef AGJ_PROBE_MIN_BLOCKS
-#define AGJ_PROBE_MIN_BLOCKS 3   // resident CTAs per SM the probe kernels are compiled for
+#define AGJ_PROBE_MIN_BLOCKS 5
+#endif
+#ifndef AGJ_BATCH_PROBE_MIN_BLOCKS
+#define AGJ_BATCH_PROBE_MIN_BLOCKS 5
 #endif
 constexpr int kJoinBlock = 256;
 constexpr int kJoinPPT = 2;                    // points per lane of the plain join
@@ -553,7 +562,7 @@ __device__ __forceinline__ const uint64_t* cta_stage_job(const JobDesc& J, DevFa
 // changes; the grid either covers the tile space (one warp per tile) or is
 // persistent and strides over it.
 template <int PPT, class Src, int MODE>
-__global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kJoinBlock, Src::kSingle ? AGJ_PROBE_MIN_BLOCKS : AGJ_BATCH_PROBE_MIN_BLOCKS)
     k_probe(const Src src, uint64_t T, const JoinScratch S) {
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
@@ -633,8 +642,11 @@ __global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __res
 // candidate adds one to its tile's pair count.  The polygon's data comes
 // from the job of the chunk's first candidate (every job sharing a polygon
 // range probes the same index); each candidate's point from its own job.
+#ifndef AGJ_PIP_MIN_BLOCKS
+#define AGJ_PIP_MIN_BLOCKS 6
+#endif
 template <class Src>
-__global__ void __launch_bounds__(kPipBlock) k_pip(const Src src, uint32_t tile_points, uint32_t P,
+__global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src src, uint32_t tile_points, uint32_t P,
                                                    const uint2* __restrict__ queue, const uint32_t* __restrict__ sorted,
                                                    const uint32_t* __restrict__ poly_start,
                                                    const uint32_t* __restrict__ chunk_start,
