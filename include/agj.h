@@ -93,6 +93,9 @@ typedef struct {
                                      (for inspection; agj_join then returns AGJ_EINVAL) */
     uint32_t no_fast_ids;         /* 1: always compute cell ids in FP64 (no certified
                                      FP32 model); results are identical, only slower */
+    uint32_t no_pip_bands;        /* 1: the certified refine test scans every edge
+                                     instead of the point's band; identical results */
+    uint32_t reserved;
 } agj_build_opts;
 
 typedef struct agj_index agj_index;

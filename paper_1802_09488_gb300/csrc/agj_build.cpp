@@ -825,7 +825,7 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
         return AGJ_EBUDGET;
     }
     if (bp.fast_ids) fit_fast_model(&X, threads);
-    prepare_poly_local(&X);
+    prepare_poly_local(&X, bp.pip_bands);
     X.stats.fast_ids = (uint32_t)X.model.enabled;
     X.stats.fast_err_cells = X.model.enabled ? (double)X.model.err : 0.0;
     X.stats.mode = (uint32_t)bp.mode;

@@ -68,6 +68,7 @@ int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, ag
     bp.max_train_level = o.max_train_level ? std::min<uint32_t>(o.max_train_level, 30) : 24;
     bp.threads = o.n_threads;
     bp.fast_ids = !o.no_fast_ids;
+    bp.pip_bands = !o.no_pip_bands;
     agj_index* h = new (std::nothrow) agj_index();
     if (!h) return AGJ_ENOMEM;
     int rc;
@@ -342,7 +343,8 @@ int agj_covers_certified_host(const agj_index* index, const double* h_points, co
         float pu, pv, dp;
         int r = -1;
         if (L.ok && agj::model_uv_local(X.model, h_points[2 * k], h_points[2 * k + 1], L, &pu, &pv, &dp))
-            r = agj::covers_certified(X.poly_luv.data() + v0, V, L, pu, pv, dp);
+            r = agj::covers_certified(X.poly_luv.data() + v0, V, L, L.nb ? X.poly_band.data() + L.band : nullptr,
+                                      pu, pv, dp);
         h_out[k] = (int8_t)r;
     }
     return AGJ_OK;

@@ -27,6 +27,7 @@ struct DevIndex {
     const int8_t* poly_face;
     const PolyLocal* poly_local;  // certified refine: per-polygon reference, bound, bbox
     const F2* poly_luv;           // certified refine: FP32 local vertex coordinates
+    const uint16_t* poly_band;    // certified refine: per-polygon band tables
     uint64_t n_nodes;
     uint64_t n_lut;
     uint32_t n_polys;

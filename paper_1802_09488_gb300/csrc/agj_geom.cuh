@@ -516,37 +516,71 @@ struct PolyLocal {
     float dv;                       // bound on the rounding of any local vertex coordinate
     float bu0, bu1, bv0, bv1;       // local bbox (rounded values of the exact bbox)
     int32_t ok;                     // 0: polygon too large for 24-bit local coordinates
+    // horizontal bands over the bbox: band b (v in [bv0 + b h, bv0 + (b+1) h))
+    // lists every edge whose v-range comes within a margin of it, so a point
+    // tests only its band's edges (0 bands: every edge)
+    uint32_t band;                  // offset of the band table in the index's band array (uint16 words)
+    uint32_t nb;                    // bands
+    float inv_h;                    // 1 / h
+    uint32_t band_len;              // words of the table: nb + 1 edge offsets, then the edge indices
 };
 
 AGJ_HD float fabs_f(float x) { return x < 0.0f ? -x : x; }
 
 // 1 covered, 0 not covered, -1 undecided.  verts: the ring's local
 // coordinates (implicitly closed).
-AGJ_HD int covers_certified(const F2* verts, uint32_t nv, const PolyLocal& P, float pu, float pv, float dp) {
+// One edge (A, B) of the certified crossing test; returns false when the
+// point is too close to decide (a vertex within D in v, or the orientation
+// within its error bound), else toggles *inside on a crossing.
+AGJ_HD bool certified_edge(F2 A, F2 B, float dA, float dB, float pu, float ev, float ep, int* inside) {
+    if ((dA > 0.0f) != (dB > 0.0f)) {
+        const float d1 = B.x - A.x, d3 = B.y - A.y, d4 = pu - A.x;
+        const float t1 = d1 * dA, t2 = d3 * d4;
+        const float o = t1 - t2;
+        const float e1 = ev + fabs_f(d1) * 6.0e-8f, e3 = ev + fabs_f(d3) * 6.0e-8f;
+        const float e2 = ep + fabs_f(dA) * 6.0e-8f, e4 = ep + fabs_f(d4) * 6.0e-8f;
+        const float bound = (fabs_f(d1) * e2 + fabs_f(dA) * e1 + e1 * e2 + fabs_f(d3) * e4 + fabs_f(d4) * e3 +
+                             e3 * e4 + (fabs_f(t1) + fabs_f(t2)) * 2.4e-7f) * 1.0001f;
+        if (fabs_f(o) <= bound) return false;
+        // upward edge (a.v < p.v < b.v) crosses when o > 0, downward when o < 0
+        if ((dA > 0.0f) == (o > 0.0f)) *inside ^= 1;
+    }
+    return true;
+}
+
+// Certified ST_Covers in FP32 local coordinates: 1 covered, 0 not, -1
+// undecided (the caller recomputes in FP64).  With a band table (bands !=
+// null, P.nb > 0) only the point's band's edges are tested: every edge that
+// can straddle the point's v or bring a vertex within D of it is listed
+// there, so the answer is the same as over all edges.
+AGJ_HD int covers_certified(const F2* verts, uint32_t nv, const PolyLocal& P, const uint16_t* bands, float pu,
+                            float pv, float dp) {
     const float D = (dp + P.dv) * 1.000001f;
     if (pu < P.bu0 - D || pu > P.bu1 + D || pv < P.bv0 - D || pv > P.bv1 + D) return 0;
     if (!(pu > P.bu0 + D && pu < P.bu1 - D && pv > P.bv0 + D && pv < P.bv1 - D)) return -1;
     const float ev = 2.0f * P.dv, ep = dp + P.dv;
+    int inside = 0;
+    if (bands && P.nb) {
+        int b = (int)((pv - P.bv0) * P.inv_h);     // pv > bv0 here: truncation is floor
+        b = b < 0 ? 0 : (b >= (int)P.nb ? (int)P.nb - 1 : b);
+        const uint16_t* E = bands + P.nb + 1;
+        for (uint32_t t = bands[b]; t < bands[b + 1]; ++t) {
+            const uint32_t k = E[t];
+            const F2 A = verts[k], B = verts[k + 1 == nv ? 0 : k + 1];
+            const float dA = pv - A.y, dB = pv - B.y;
+            if (fabs_f(dA) <= D || fabs_f(dB) <= D) return -1;
+            if (!certified_edge(A, B, dA, dB, pu, ev, ep, &inside)) return -1;
+        }
+        return inside;
+    }
     F2 A = verts[0];
     float dA = pv - A.y;
     if (fabs_f(dA) <= D) return -1;
-    int inside = 0;
     for (uint32_t k = 0; k < nv; ++k) {
         const F2 B = verts[k + 1 == nv ? 0 : k + 1];
         const float dB = pv - B.y;
         if (fabs_f(dB) <= D) return -1;
-        if ((dA > 0.0f) != (dB > 0.0f)) {
-            const float d1 = B.x - A.x, d3 = B.y - A.y, d4 = pu - A.x;
-            const float t1 = d1 * dA, t2 = d3 * d4;
-            const float o = t1 - t2;
-            const float e1 = ev + fabs_f(d1) * 6.0e-8f, e3 = ev + fabs_f(d3) * 6.0e-8f;
-            const float e2 = ep + fabs_f(dA) * 6.0e-8f, e4 = ep + fabs_f(d4) * 6.0e-8f;
-            const float bound = (fabs_f(d1) * e2 + fabs_f(dA) * e1 + e1 * e2 + fabs_f(d3) * e4 + fabs_f(d4) * e3 +
-                                 e3 * e4 + (fabs_f(t1) + fabs_f(t2)) * 2.4e-7f) * 1.0001f;
-            if (fabs_f(o) <= bound) return -1;
-            // upward edge (a.v < p.v < b.v) crosses when o > 0, downward when o < 0
-            if ((dA > 0.0f) == (o > 0.0f)) inside ^= 1;
-        }
+        if (!certified_edge(A, B, dA, dB, pu, ev, ep, &inside)) return -1;
         A = B;
         dA = dB;
     }

@@ -60,12 +60,13 @@ struct Index {
     FastModel model{};                // certified fast cell ids (disabled: all zero)
     std::vector<PolyLocal> poly_local;   // per polygon: reference point, rounding bound, bbox
     std::vector<F2> poly_luv;            // per vertex: FP32 local coordinates
+    std::vector<uint16_t> poly_band;     // per polygon: band tables of the certified test
     agj_stats stats{};
     // device copies (owned)
     void* d_blob = nullptr;
     uint64_t blob_bytes = 0;
     uint64_t off_nodes = 0, off_lut = 0, off_uv = 0, off_vkey = 0, off_ukey = 0, off_poff = 0, off_bbox = 0,
-             off_face = 0, off_plocal = 0, off_pluv = 0;
+             off_face = 0, off_plocal = 0, off_pluv = 0, off_pband = 0;
     int device = 0;
 };
 
@@ -79,6 +80,7 @@ struct BuildParams {
     uint32_t max_train_level;
     uint32_t threads;
     bool fast_ids;
+    bool pip_bands;
 };
 
 // Host build of the logical and physical index (no CUDA calls).  Returns an
@@ -91,7 +93,12 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
 void fit_fast_model(Index* idx, unsigned threads);
 
 // Local FP32 coordinates of every polygon for the certified refine step.
-void prepare_poly_local(Index* idx);
+void prepare_poly_local(Index* idx, bool bands);
+// band tables of the certified refine test: at least kBandMinVerts vertices,
+// at most kBandMax bands and kBandMaxWords uint16 words per polygon
+constexpr uint32_t kBandMinVerts = 24;
+constexpr uint32_t kBandMax = 64;
+constexpr uint32_t kBandMaxWords = 4096;
 
 // The super-covering merge on given (cell, reference) pairs, in order.
 void supercover(const uint64_t* cells, const uint32_t* refs, uint64_t n, std::vector<uint64_t>* out_cells,

@@ -33,11 +33,11 @@ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 //   [entries u64 per point] [tile counts u32] [tile prefixes u32]
 //   then, with exact jobs, the per-tile candidate counts, the candidate
 //   queue (a region of tile_slots per tile), its pass bytes, its polygon
-//   order and the per-polygon segments
+//   order and the per-polygon segments and refine chunks
 struct JoinLayout {
     uint64_t chunks = 0, pchunks = 0, pcount = 0, zero_end = 0;
     uint64_t entries = 0, tcount = 0, tprefix = 0;
-    uint64_t tcand = 0, queue = 0, pass = 0, sorted = 0, pstart = 0, cursor = 0, cstart = 0, total = 0;
+    uint64_t tcand = 0, queue = 0, pass = 0, sorted = 0, pstart = 0, cursor = 0, cstart = 0, cpoly = 0, total = 0;
     uint64_t n_points = 0, n_tiles = 0, n_chunks = 0, n_pchunks = 0, queue_cap = 0, n_polys = 0;
     uint32_t tile_slots = 0;
     bool exact = false;
@@ -78,10 +78,12 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
         L.tcand = o; o += align256(n_tiles * 4 + 4);
         L.queue = o; o += align256(L.queue_cap * 8 + 8);
         L.pass = o; o += align256(L.queue_cap + 1);
-        L.sorted = o; o += align256(L.queue_cap * 4 + 4);
+        L.sorted = o; o += align256(L.queue_cap * 8 + 8);
         L.pstart = o; o += align256((n_polys + 1) * 4);
         L.cursor = o; o += align256((n_polys + 1) * 4);
         L.cstart = o; o += align256((n_polys + 1) * 4);
+        // refine chunks: one per kPipBlock candidates of a polygon, plus one partial per polygon
+        L.cpoly = o; o += align256((L.queue_cap / kPipBlock + n_polys + 1) * 4);
     }
     L.total = o;
     return L;
@@ -137,14 +139,15 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
             S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.pstart),
             reinterpret_cast<uint32_t*>(sc + L.cursor), reinterpret_cast<uint32_t*>(sc + L.cstart), hdr + 2,
-            reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3, reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
+            reinterpret_cast<uint32_t*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
+            reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
         k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots,
                                             reinterpret_cast<uint32_t*>(sc + L.cursor),
-                                            reinterpret_cast<uint32_t*>(sc + L.sorted), (uint32_t)L.n_polys);
-        k_pip<Src><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, (uint32_t)L.n_polys, S.queue,
-                                                    reinterpret_cast<const uint32_t*>(sc + L.sorted),
+                                            reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
+        k_pip<Src><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, reinterpret_cast<const uint2*>(sc + L.sorted),
                                                     reinterpret_cast<const uint32_t*>(sc + L.pstart),
-                                                    reinterpret_cast<const uint32_t*>(sc + L.cstart), hdr + 2, S.pass,
+                                                    reinterpret_cast<const uint32_t*>(sc + L.cstart),
+                                                    reinterpret_cast<const uint32_t*>(sc + L.cpoly), hdr + 2, S.pass,
                                                     S.tile_count);
     }
     if (MODE == kModeApprox) {

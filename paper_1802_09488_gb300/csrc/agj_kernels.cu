@@ -100,8 +100,8 @@ constexpr int kPolyScanItems = 4;
 __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_polys,
                                                    uint32_t* __restrict__ poly_start, uint32_t* __restrict__ cursor,
                                                    uint32_t* __restrict__ chunk_start, uint32_t* __restrict__ n_chunks,
-                                                   uint64_t* __restrict__ chunks, uint32_t* __restrict__ chunk_counter,
-                                                   uint64_t* __restrict__ err) {
+                                                   uint32_t* __restrict__ chunk_poly, uint64_t* __restrict__ chunks,
+                                                   uint32_t* __restrict__ chunk_counter, uint64_t* __restrict__ err) {
     __shared__ uint64_t s_warp[8];
     __shared__ uint32_t s_chunk;
     __shared__ uint64_t s_prefix;
@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ 
             poly_start[i0 + k] = (uint32_t)o;
             cursor[i0 + k] = (uint32_t)o;
             chunk_start[i0 + k] = (uint32_t)(o >> 32);
+            const uint32_t c0 = (uint32_t)(o >> 32), nch = (uint32_t)(v[k] >> 32);
+            for (uint32_t t = 0; t < nch; ++t) chunk_poly[c0 + t] = (uint32_t)(i0 + k);
         }
         o += v[k];
     }
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ queue, 
 constexpr int kScatterMaxPolys = 4096;
 __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand,
                                                  uint64_t n_tiles, uint32_t tile_slots, uint32_t* __restrict__ cursor,
-                                                 uint32_t* __restrict__ sorted, uint32_t n_polys) {
+                                                 uint2* __restrict__ sorted, uint32_t n_polys) {
     __shared__ uint32_t s_cnt[kScatterMaxPolys];
     __shared__ uint32_t s_base[kScatterMaxPolys];
     __shared__ uint32_t s_off[kChunkTiles];
@@ -235,13 +237,14 @@ __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
                 const uint64_t q = chunk_slot(s_off, c0, tile_slots, i);
-                const uint32_t poly = queue[q].y;
-                sorted[s_base[poly] + atomicAdd(&s_cnt[poly], 1u)] = (uint32_t)q;
+                const uint2 it = queue[q];
+                sorted[s_base[it.y] + atomicAdd(&s_cnt[it.y], 1u)] = make_uint2(it.x, (uint32_t)q);
             }
         } else {
             for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
                 const uint64_t q = chunk_slot(s_off, c0, tile_slots, i);
-                sorted[atomicAdd(&cursor[queue[q].y], 1u)] = (uint32_t)q;
+                const uint2 it = queue[q];
+                sorted[atomicAdd(&cursor[it.y], 1u)] = make_uint2(it.x, (uint32_t)q);
             }
         }
         __syncthreads();
@@ -342,6 +345,7 @@ DevIndex make_dev_index(const Index& X) {
     D.poly_face = reinterpret_cast<const int8_t*>(b + X.off_face);
     D.poly_local = reinterpret_cast<const PolyLocal*>(b + X.off_plocal);
     D.poly_luv = reinterpret_cast<const F2*>(b + X.off_pluv);
+    D.poly_band = reinterpret_cast<const uint16_t*>(b + X.off_pband);
     D.n_nodes = X.nodes.size() / 256;
     D.n_lut = X.lut.size();
     D.n_polys = X.n_polys;
@@ -364,6 +368,7 @@ int upload_index(Index* X, cudaStream_t s) {
     X->off_face = o; o += align256((uint64_t)X->n_polys + 1);
     X->off_plocal = o; o += align256((uint64_t)X->n_polys * sizeof(PolyLocal) + 16);
     X->off_pluv = o; o += align256(nv * sizeof(F2) + 16);
+    X->off_pband = o; o += align256(X->poly_band.size() * 2 + 16);
     X->blob_bytes = o;
     std::vector<unsigned char> host(o, 0);
     auto put = [&](uint64_t off, const void* src, size_t bytes) {
@@ -385,6 +390,7 @@ int upload_index(Index* X, cudaStream_t s) {
     put(X->off_face, X->poly_face.data(), X->poly_face.size());
     put(X->off_plocal, X->poly_local.data(), X->poly_local.size() * sizeof(PolyLocal));
     put(X->off_pluv, X->poly_luv.data(), X->poly_luv.size() * sizeof(F2));
+    put(X->off_pband, X->poly_band.data(), X->poly_band.size() * 2);
     if (cudaMalloc(&X->d_blob, o) != cudaSuccess) { cudaGetLastError(); X->d_blob = nullptr; return AGJ_ENOMEM; }
     if (cudaMemcpyAsync(X->d_blob, host.data(), o, cudaMemcpyHostToDevice, s) != cudaSuccess) return AGJ_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return AGJ_ECUDA;

@@ -347,10 +347,55 @@ void fit_fast_model(Index* idx, unsigned threads) {
     M = F;
 }
 
-void prepare_poly_local(Index* idx) {
+// Horizontal bands of polygon k's certified test.  Band b covers local v in
+// [bv0 + b h, bv0 + (b+1) h); it lists every edge whose v-range, widened by
+// a margin M, meets that interval.  M exceeds the test's closeness bound D
+// for any point that reaches the edge loop (D = (dp + dv) (1 + 1e-6), dp <=
+// err_uv + (|u| + |v|) 2.4e-7 + 1e-5 with |u|, |v| within the bbox plus
+// D), plus the rounding of the device's band index ((pv - bv0) / h in FP32:
+// at most a unit of pv and a relative 2.4e-7 of the band count).  So every
+// edge the all-edges loop could straddle, or whose vertex could come within
+// D, is in the point's band: the banded test gives the same answer.
+static void build_bands(Index* idx, uint32_t k, PolyLocal* L) {
+    const uint32_t a = idx->poly_off[k], V = idx->poly_off[k + 1] - a;
+    if (!L->ok || !idx->model.uv_enabled || V < kBandMinVerts) return;
+    const double lo = L->bv0, hi = L->bv1;
+    if (!(hi > lo)) return;
+    const uint32_t nb = std::min<uint32_t>(kBandMax, V / 4);
+    const double h = (hi - lo) / nb;
+    const double big = std::max(std::fabs((double)L->bu0), std::fabs((double)L->bu1)) +
+                       std::max(std::fabs((double)L->bv0), std::fabs((double)L->bv1));
+    const double M = 2.0 * ((double)idx->model.err_uv + (double)L->dv) + big * 5e-7 + 8.0 + h * 1e-3;
+    std::vector<std::vector<uint16_t>> lists(nb);
+    const F2* lv = idx->poly_luv.data() + a;
+    for (uint32_t e = 0; e < V; ++e) {
+        const F2 A = lv[e], B = lv[e + 1 == V ? 0 : e + 1];
+        const double ylo = std::min(A.y, B.y) - M, yhi = std::max(A.y, B.y) + M;
+        const int64_t b0 = std::max<int64_t>(0, (int64_t)std::floor((ylo - lo) / h));
+        const int64_t b1 = std::min<int64_t>(nb - 1, (int64_t)std::floor((yhi - lo) / h));
+        for (int64_t b = b0; b <= b1; ++b) lists[b].push_back((uint16_t)e);
+    }
+    uint64_t total = nb + 1;
+    for (auto& l : lists) total += l.size();
+    if (total > kBandMaxWords) return;          // too large to stage: test every edge
+    L->band = (uint32_t)idx->poly_band.size();
+    L->nb = nb;
+    L->inv_h = (float)((double)nb / (hi - lo));
+    L->band_len = (uint32_t)total;
+    uint32_t off = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        idx->poly_band.push_back((uint16_t)off);
+        off += (uint32_t)lists[b].size();
+    }
+    idx->poly_band.push_back((uint16_t)off);
+    for (auto& l : lists) idx->poly_band.insert(idx->poly_band.end(), l.begin(), l.end());
+}
+
+void prepare_poly_local(Index* idx, bool bands) {
     const uint32_t P = idx->n_polys;
     idx->poly_local.assign(P, PolyLocal{});
     idx->poly_luv.assign(idx->poly_uv.size() / 2, F2{0.0f, 0.0f});
+    idx->poly_band.clear();
     const double S = 1073741824.0;   // 2^30
     for (uint32_t k = 0; k < P; ++k) {
         const uint32_t a = idx->poly_off[k], b = idx->poly_off[k + 1];
@@ -359,7 +404,7 @@ void prepare_poly_local(Index* idx) {
             u0 = std::min(u0, idx->poly_uv[2 * t] * S); u1 = std::max(u1, idx->poly_uv[2 * t] * S);
             v0 = std::min(v0, idx->poly_uv[2 * t + 1] * S); v1 = std::max(v1, idx->poly_uv[2 * t + 1] * S);
         }
-        PolyLocal L{};
+        PolyLocal L{};      // no band table unless build_bands makes one
         L.ru = (int32_t)std::llround(0.5 * (u0 + u1));
         L.rv = (int32_t)std::llround(0.5 * (v0 + v1));
         // local coordinates must stay well inside 24-bit range
@@ -375,6 +420,7 @@ void prepare_poly_local(Index* idx) {
         if ((double)L.dv < dv) L.dv = std::nextafter(L.dv, 1.0f);
         L.bu0 = (float)(u0 - L.ru); L.bu1 = (float)(u1 - L.ru);
         L.bv0 = (float)(v0 - L.rv); L.bv1 = (float)(v1 - L.rv);
+        if (bands) build_bands(idx, k, &L);
         idx->poly_local[k] = L;
     }
 }

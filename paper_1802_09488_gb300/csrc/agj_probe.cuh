@@ -612,23 +612,24 @@ __global__ void k_scan_counts(const uint32_t* __restrict__ tile_count, uint64_t 
 
 // Exclusive scans of the per-polygon candidate counts and of the per-polygon
 // refine chunks (kPipBlock candidates each), as one packed 64-bit scan
-// (count in the low 32 bits, chunks above) chained by the look-back.  The
-// CTA that finishes last writes the totals.
+// (count in the low 32 bits, chunks above) chained by the look-back; each
+// refine chunk's polygon goes to chunk_poly.  The CTA that finishes last
+// writes the totals.
 __global__ void k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_polys,
                             uint32_t* __restrict__ poly_start, uint32_t* __restrict__ cursor,
                             uint32_t* __restrict__ chunk_start, uint32_t* __restrict__ n_chunks,
-                            uint64_t* __restrict__ chunks, uint32_t* __restrict__ chunk_counter,
-                            uint64_t* __restrict__ err);
+                            uint32_t* __restrict__ chunk_poly, uint64_t* __restrict__ chunks,
+                            uint32_t* __restrict__ chunk_counter, uint64_t* __restrict__ err);
 
 // Candidates per polygon of the queue (tile_cand[t] items from slot
 // t x tile_slots of each tile t).
 __global__ void k_count(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
                         uint32_t tile_slots, uint32_t* __restrict__ poly_count, uint32_t n_polys);
 
-// Groups the queued candidates by polygon: a counting-sort scatter of slot
-// indices.
+// Groups the queued candidates by polygon: a counting-sort scatter of
+// (global point, queue slot) pairs.
 __global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
-                          uint32_t tile_slots, uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted,
+                          uint32_t tile_slots, uint32_t* __restrict__ cursor, uint2* __restrict__ sorted,
                           uint32_t n_polys);
 
 // Refine (Listing "Join" step 3 on candidate references): ST_Covers of
@@ -645,50 +646,50 @@ __global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __res
 #ifndef AGJ_PIP_MIN_BLOCKS
 #define AGJ_PIP_MIN_BLOCKS 6
 #endif
+constexpr int kPipSmemBand = 4096;               // band-table words staged per CTA (uint16)
 template <class Src>
-__global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src src, uint32_t tile_points, uint32_t P,
-                                                   const uint2* __restrict__ queue, const uint32_t* __restrict__ sorted,
-                                                   const uint32_t* __restrict__ poly_start,
-                                                   const uint32_t* __restrict__ chunk_start,
-                                                   const uint32_t* __restrict__ n_chunks, uint8_t* __restrict__ pass,
-                                                   uint32_t* __restrict__ tile_count) {
+__global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src src, uint32_t tile_points,
+                                                                   const uint2* __restrict__ sorted,
+                                                                   const uint32_t* __restrict__ poly_start,
+                                                                   const uint32_t* __restrict__ chunk_start,
+                                                                   const uint32_t* __restrict__ chunk_poly,
+                                                                   const uint32_t* __restrict__ n_chunks,
+                                                                   uint8_t* __restrict__ pass,
+                                                                   uint32_t* __restrict__ tile_count) {
     __shared__ F2 s_lv[kPipSmemVerts];
+    __shared__ uint16_t s_band[kPipSmemBand];
     const uint32_t total = *n_chunks;
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
-        // global polygon of chunk c: the last with chunk_start <= c
-        uint32_t lo = 0, hi = P;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (chunk_start[mid] <= c) lo = mid; else hi = mid;
-        }
-        const uint32_t gp = lo;
+        const uint32_t gp = chunk_poly[c];
         const uint32_t q0 = poly_start[gp] + (c - chunk_start[gp]) * kPipBlock;
         const uint32_t q1 = min(q0 + kPipBlock, poly_start[gp + 1]);
-        const JobDesc& JP = src.job(src.find_tile(queue[sorted[q0]].x / tile_points));
+        const JobDesc& JP = src.job(src.find_tile(sorted[q0].x / tile_points));
         const uint32_t poly = gp - JP.poly0;
         const uint32_t item = q0 + threadIdx.x;
         const uint32_t v0 = JP.X.poly_off[poly], V = JP.X.poly_off[poly + 1] - v0;
         const PolyLocal L = JP.X.poly_local[poly];
         const bool certified = JP.X.model.uv_enabled && L.ok && V <= (uint32_t)kPipSmemVerts;
+        const bool banded = certified && L.nb && L.band_len <= (uint32_t)kPipSmemBand;
         __syncthreads();
         if (certified)
             for (uint32_t t = threadIdx.x; t < V; t += blockDim.x) s_lv[t] = JP.X.poly_luv[v0 + t];
+        if (banded)
+            for (uint32_t t = threadIdx.x; t < L.band_len; t += blockDim.x) s_band[t] = JP.X.poly_band[L.band + t];
         __syncthreads();
         if (item < q1) {
-            const uint32_t qi = sorted[item];
-            const uint2 qp = queue[qi];
-            const uint32_t wt = qp.x / tile_points;
+            const uint2 it = sorted[item];            // (global point, queue slot)
+            const uint32_t wt = it.x / tile_points;
             const JobDesc& J = src.job(src.find_tile(wt));
-            const double2 pt = J.pts[qp.x - J.tile0 * tile_points];
+            const double2 pt = J.pts[it.x - J.tile0 * tile_points];
             int r = -1;
             float pu, pv, dp;
             if (certified && model_uv_local(JP.X.model, pt.x, pt.y, L, &pu, &pv, &dp))
-                r = covers_certified(s_lv, V, L, pu, pv, dp);
+                r = covers_certified(s_lv, V, L, banded ? s_band : nullptr, pu, pv, dp);
             if (r < 0) {
                 r = covers_fp64(JP.X, poly, pt.x, pt.y) ? 1 : 0;
                 atomicAdd((unsigned long long*)&J.counters[1], 1ull);
             }
-            pass[qi] = (uint8_t)r;
+            pass[it.y] = (uint8_t)r;
             if (r) atomicAdd(&tile_count[wt], 1u);
         }
     }

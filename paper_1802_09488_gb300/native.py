@@ -39,7 +39,7 @@ class BuildOpts(C.Structure):
                 ("max_interior_cells", C.c_uint32), ("max_interior_level", C.c_uint32),
                 ("memory_budget_bytes", C.c_uint64), ("train_latlng", C.c_void_p), ("n_train", C.c_uint64),
                 ("max_train_level", C.c_uint32), ("n_threads", C.c_uint32), ("host_only", C.c_uint32),
-                ("no_fast_ids", C.c_uint32)]
+                ("no_fast_ids", C.c_uint32), ("no_pip_bands", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -182,7 +182,8 @@ class Index:
 
     def __init__(self, polygons, mode: int = APPROX, precision_m: float = 10.0, train=None,
                  budget_bytes: int = 0, threads: int = 0, max_cover_cells: int = 0, max_interior_cells: int = 0,
-                 max_interior_level: int = 0, host_only: bool = False, fast_ids: bool = True, stream=None):
+                 max_interior_level: int = 0, host_only: bool = False, fast_ids: bool = True, pip_bands: bool = True,
+                 stream=None):
         L = lib()
         self._polys = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 2) for p in polygons]
         arr = (Polygon * max(len(self._polys), 1))()
@@ -197,6 +198,7 @@ class Index:
         opts.max_interior_level = int(max_interior_level)
         opts.host_only = 1 if host_only else 0
         opts.no_fast_ids = 0 if fast_ids else 1
+        opts.no_pip_bands = 0 if pip_bands else 1
         self._train = None
         if train is not None:
             self._train = np.ascontiguousarray(train, dtype=np.float64).reshape(-1, 2)

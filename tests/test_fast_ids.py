@@ -114,3 +114,32 @@ def test_certified_refine_equals_oracle(agj, oracle):
     n_rand = n_random_pairs
     assert np.mean(decided[:n_rand]) > 0.999
     assert (~decided).sum() > 0          # the near-edge points exercise the fallback
+
+
+def test_banded_refine_equals_all_edges(agj):
+    """The band tables only skip edges that cannot change the certified
+    test's answer: with and without them every (point, polygon) pair gets
+    the same 1 / 0 / undecided answer, near edges and vertices included."""
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c2_city_polygons()
+    with_b = agj.Index(polys, agj.EXACT, 0, host_only=True)
+    without = agj.Index(polys, agj.EXACT, 0, host_only=True, pip_bands=False)
+    rng = np.random.default_rng(47)
+    pts, pid = [], []
+    cand = synth.points_mixture(30000, synth.BOX_CITY, seed=48, dist_seed=3)
+    for k in range(len(cand)):
+        pts.append(cand[k]); pid.append(int(rng.integers(0, len(polys))))
+    for q in rng.choice(len(polys), 80, replace=False):
+        P = polys[q]
+        lat0, lat1 = P[:, 0].min(), P[:, 0].max()
+        lng0, lng1 = P[:, 1].min(), P[:, 1].max()
+        for _ in range(200):     # inside the bbox: every band, near band edges too
+            pts.append(np.array([rng.uniform(lat0, lat1), rng.uniform(lng0, lng1)])); pid.append(q)
+        for t in range(len(P)):  # vertices and points just off them in latitude
+            for off in (0.0, 1e-12, -1e-12, 1e-9, -1e-9, 1e-7):
+                pts.append(P[t] + np.array([off, 0.0])); pid.append(q)
+    pts = np.array(pts); pid = np.array(pid, dtype=np.uint32)
+    a = with_b.covers_certified_host(pts, pid)
+    b = without.covers_certified_host(pts, pid)
+    assert np.array_equal(a, b)
+    assert (a == 1).sum() > 1000 and (a == -1).sum() > 0
