@@ -20,7 +20,7 @@ import math
 import os
 import threading
 
-CANDIDATES = [(1, 0), (2, 0), (4, 0), (1, 3), (2, 3), (4, 3), (2, 2)]
+CANDIDATES = [(1, 0), (2, 0), (4, 0), (2, 3), (4, 3), (2, 5), (4, 5)]
 _lock = threading.Lock()
 
 

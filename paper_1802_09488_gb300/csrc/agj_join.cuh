@@ -77,7 +77,7 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
     if (exact) {
         L.tcand = o; o += align256(n_tiles * 4 + 4);
         L.queue = o; o += align256(L.queue_cap * 8 + 8);
-        L.pass = o; o += align256(L.queue_cap + 1);
+        L.pass = o; o += align256(L.queue_cap + 32);
         L.sorted = o; o += align256(L.queue_cap * 8 + 8);
         L.pstart = o; o += align256((n_polys + 1) * 4);
         L.cursor = o; o += align256((n_polys + 1) * 4);

@@ -343,15 +343,6 @@ __device__ __forceinline__ void emit_all(const DevIndex& X, uint64_t e, uint32_t
 }
 
 
-// Number of output pairs of one point of the exact join: its true
-// references plus those of its nc candidates (queue slots qb .. qb + nc - 1)
-// that passed the PIP.
-__device__ __forceinline__ uint32_t exact_count(uint32_t nt, uint32_t nc, const uint8_t* pass, uint64_t qb) {
-    uint32_t c = nt;
-    for (uint32_t t = 0; t < nc; ++t) c += pass[qb + t];
-    return c;
-}
-
 // ST_Covers in FP64 exactly as the spec (the certified test's fallback):
 // same face, closed (u,v) bbox, ring rule with integer keys for the range
 // tests and FP64 orientation, vertices read from global memory.
@@ -454,6 +445,51 @@ struct JoinScratch {
 
 __global__ void k_zero(uint64_t* __restrict__ a, uint64_t na, uint64_t* __restrict__ b, uint64_t nb);
 
+// Exact jobs: the tile's candidate references (nc[k] of point k, csum of
+// the lane) go to the tile's own queue region, in point order (lane-major,
+// then k), so no reservation is shared between tiles.
+template <int PPT>
+__device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, const uint32_t* nc, uint32_t csum,
+                                           uint64_t wt, uint64_t gbase, uint32_t gpoly0, const JoinScratch& S) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t x = warp_incl_scan(csum);
+    const uint32_t wtotal = __shfl_sync(kFull, x, 31);
+    if (lane == 0) {
+        S.tile_cand[wt] = wtotal;
+        if (wtotal) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
+    }
+    if (wtotal == 0) return;
+    if (wtotal > S.tile_slots) {    // cannot happen: a point has at most the index's candidate references
+        if (lane == 0) atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrQueueOverflow);
+        return;
+    }
+    uint64_t q = wt * S.tile_slots + x - csum;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!nc[k]) continue;
+        const uint32_t g = (uint32_t)(gbase + lane + 32 * k);     // global point index
+        const uint64_t ek = e[k];
+        const uint32_t tag = (uint32_t)(ek & 3ull);
+        const uint32_t* Cc = nullptr;
+        if (tag == 3) {
+            const uint32_t off = payload_of(ek, 0);
+            Cc = J.X.lut + off + 2 + __ldg(J.X.lut + off);
+        }
+        for (uint32_t t = 0, r = 0; t < nc[k]; ++r) {
+            uint32_t poly;
+            if (tag == 3) {
+                poly = __ldg(Cc + r);
+            } else {
+                const uint32_t pl = payload_of(ek, (int)r);
+                if (pl & 1u) continue;          // a true reference
+                poly = pl >> 1;
+            }
+            ++t;
+            S.queue[q++] = make_uint2(g, gpoly0 + poly);
+        }
+    }
+}
+
 // Step 1 of the join (Listing "Probe Adaptive Cell Trie" per point) for
 // warp tile wt = tile lt of job J: cell id + walk for every point of the tile (32 lanes x PPT
 // points, point base + lane + 32 k, so the 16-byte loads coalesce), the
@@ -496,45 +532,8 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(kFull, tsum, o);
     if (lane == 0) S.tile_count[wt] = tsum;
-    if (MODE == kModeApprox || S.tile_cand == nullptr) return;   // no exact job in the launch
-    // exact: the tile's candidates go to its own queue region, in point
-    // order (lane-major, then k), so no reservation is shared between tiles
-    const uint32_t x = warp_incl_scan(csum);
-    const uint32_t wtotal = __shfl_sync(kFull, x, 31);
-    if (lane == 0) {
-        S.tile_cand[wt] = wtotal;
-        if (wtotal) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
-    }
-    if (wtotal == 0) return;
-    if (wtotal > S.tile_slots) {    // cannot happen: a point has at most the index's candidate references
-        if (lane == 0) atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrQueueOverflow);
-        return;
-    }
-    uint64_t q = wt * S.tile_slots + x - csum;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (!nc[k]) continue;
-        const uint32_t g = (uint32_t)(gbase + lane + 32 * k);     // global point index
-        const uint64_t ek = e[k];
-        const uint32_t tag = (uint32_t)(ek & 3ull);
-        const uint32_t* Cc = nullptr;
-        if (tag == 3) {
-            const uint32_t off = payload_of(ek, 0);
-            Cc = J.X.lut + off + 2 + __ldg(J.X.lut + off);
-        }
-        for (uint32_t t = 0, r = 0; t < nc[k]; ++r) {
-            uint32_t poly;
-            if (tag == 3) {
-                poly = __ldg(Cc + r);
-            } else {
-                const uint32_t pl = payload_of(ek, (int)r);
-                if (pl & 1u) continue;          // a true reference
-                poly = pl >> 1;
-            }
-            ++t;
-            S.queue[q++] = make_uint2(g, gpoly0 + poly);
-        }
-    }
+    if constexpr (MODE != kModeApprox)
+        if (S.tile_cand) queue_tile<PPT>(J, e, nc, csum, wt, gbase, gpoly0, S);
 }
 
 // Stages job J's face table and (with the fast model) the model face's root
@@ -701,7 +700,8 @@ __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src
 // per point (true and candidate references merged; exact jobs keep the
 // candidates that passed).  The job's last tile writes offsets[n] and nnz.
 template <int PPT, int MODE, class Src>
-__device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t wt, const JoinScratch& S) {
+__device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t wt, const JoinScratch& S,
+                                          uint8_t* s_pass) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t gbase = wt * (32 * PPT);
     // the stored entries and the tile prefix do not depend on the job, so
@@ -712,22 +712,56 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
     const uint32_t tprefix = S.tile_prefix[wt];
     const JobDesc& J = src.job(j);
     const bool exact = job_exact<MODE>(J);
+    // exact: the first 32 PIP results of the tile's queue region, one per
+    // lane, loaded beside the entries (the region's size is known only
+    // after them)
+    const uint32_t pb0 = (MODE != kModeApprox && exact) ? S.pass[wt * S.tile_slots + lane] : 0u;
     const uint64_t base = (wt - J.tile0) * (32 * PPT);
-    uint32_t cnt[PPT], qb[PPT], ex[PPT], run = 0;
+    uint32_t cnt[PPT], pm[PPT], qb[PPT], ex[PPT], run = 0;   // pm: bit t = candidate t of the point passed
+    bool direct = false;     // a point with more than 32 candidates: read its results from memory
     if (exact) {
-        // the queue slots of this tile's candidates, in the order the probe wrote them
-        uint32_t nt[PPT], nc[PPT], csum = 0;
+        // the queue slots of this tile's candidates, in the order the probe
+        // wrote them: lane-major, then k
+        uint32_t nt[PPT], nc[PPT], csum = 0, mx = 0;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             entry_counts(J.X, e[k], &nt[k], &nc[k]);
             csum += nc[k];
+            mx = nc[k] > mx ? nc[k] : mx;
+            pm[k] = 0;
         }
-        uint32_t q = warp_incl_scan(csum) - csum;
+        const uint32_t q0 = warp_incl_scan(csum) - csum;
+        mx = __reduce_max_sync(kFull, mx);
+        direct = mx > 32;
+        uint32_t qq = q0;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            qb[k] = q;
-            q += nc[k];
-            cnt[k] = exact_count(nt[k], nc[k], S.pass, wt * S.tile_slots + qb[k]);
+            qb[k] = qq;
+            qq += nc[k];
+        }
+        // the tile's first 32 results through the warp's shared bytes; the
+        // rest (rare) from memory
+        __syncwarp();                  // the warp's previous tile is done with its bytes
+        s_pass[threadIdx.x] = (uint8_t)pb0;
+        __syncwarp();
+        const uint8_t* sp = s_pass + (threadIdx.x & ~31u);
+        const uint8_t* gp = S.pass + wt * S.tile_slots;
+        if (!direct) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                for (uint32_t t = 0; t < nc[k]; ++t) {
+                    const uint32_t idx = qb[k] + t;
+                    if (idx < 32 ? sp[idx] : gp[idx]) pm[k] |= 1u << t;
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (!direct) {
+                cnt[k] = nt[k] + __popc(pm[k]);
+            } else {
+                cnt[k] = nt[k];
+                for (uint32_t t = 0; t < nc[k]; ++t) cnt[k] += S.pass[wt * S.tile_slots + qb[k] + t];
+            }
         }
     } else {
 #pragma unroll
@@ -735,6 +769,7 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
             uint32_t nt, nc;
             entry_counts(J.X, e[k], &nt, &nc);
             cnt[k] = nt + nc;
+            pm[k] = 0;
             qb[k] = 0;
         }
     }
@@ -762,14 +797,15 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
         }
         const uint64_t ek = e[k];
         const uint32_t tag = (uint32_t)(ek & 3ull);
-        const uint8_t* ps = S.pass + wt * S.tile_slots + qb[k];
+        const uint32_t ps = pm[k];
+        const uint8_t* pd = S.pass + wt * S.tile_slots + qb[k];     // the results themselves (direct)
         uint64_t w = o;
         uint32_t ci = 0;
         if (tag == 1 || tag == 2) {
             for (int t = 0; t < (int)tag; ++t) {
                 const uint32_t pl = payload_of(ek, t);
                 if (pl & 1u) J.ids[w++] = pl >> 1;
-                else if (ps[ci++]) J.ids[w++] = pl >> 1;
+                else if (direct ? pd[ci++] : (ps >> ci++) & 1u) J.ids[w++] = pl >> 1;
             }
         } else if (tag == 3) {
             const uint32_t off = payload_of(ek, 0);
@@ -782,7 +818,7 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
                 const uint32_t ta = a < nt ? __ldg(Tt + a) : 0xFFFFFFFFu;
                 const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
                 if (ta < cb) { J.ids[w++] = ta; ++a; }
-                else { if (ps[b]) J.ids[w++] = cb; ++b; }
+                else { if (direct ? pd[b] : (ps >> b) & 1u) J.ids[w++] = cb; ++b; }
             }
         }
     }
@@ -797,13 +833,14 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
 
 template <int PPT, class Src, int MODE>
 __global__ void __launch_bounds__(kJoinBlock) k_emit(const Src src, uint64_t T, const JoinScratch S) {
+    __shared__ uint8_t s_pass[kJoinBlock];
     uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if constexpr (Src::kSingle) {
-        if (wt < T) emit_tile<PPT, MODE>(src, 0, wt, S);
+        if (wt < T) emit_tile<PPT, MODE>(src, 0, wt, S, s_pass);
     } else if ((uint64_t)gridDim.x * kWarpsPerBlock >= T) {     // one warp per tile
-        if (wt < T) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S);
+        if (wt < T) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S, s_pass);
     } else {                                                     // persistent grid
-        for (; wt < T; wt += (uint64_t)gridDim.x * kWarpsPerBlock) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S);
+        for (; wt < T; wt += (uint64_t)gridDim.x * kWarpsPerBlock) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S, s_pass);
     }
 }
 
