@@ -35,6 +35,12 @@ METRIC = "points joined/sec at 1 GB300 (approx eps and exact) vs plain join; p50
 # approx: k_zero, k_probe<approx>, k_scan_counts, k_emit<approx>
 # exact:  k_zero, k_probe<exact>, k_count, k_poly_scan, k_scatter, k_pip, k_scan_counts, k_emit<exact>
 LAUNCHES_PER_STEP = {"approx": 4, "exact": 8}
+# DRAM bytes (read + write) per point of the probe kernels on the city workload,
+# from one `ncu --set full` capture of a 16e6-point join of the current kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum divided by the points); a full
+# launch's traffic scales with its points (the trie gathers per point do not
+# depend on n).  Must be re-captured whenever a probe kernel changes.
+PROBE_DRAM_BYTES_PER_POINT = {"k_probe_approx": 24.92, "k_probe_exact": 25.18}
 
 
 def parse():
@@ -50,6 +56,10 @@ def parse():
     ap.add_argument("--workload", choices=["c2", "c3", "c1"], default="c2",
                     help="c2: city (default); c3: 40 000 fine overlapping polygons; c1: 5 polygons, uniform points")
     ap.add_argument("--eps", type=float, default=None, help="approximate precision in metres (default per workload)")
+    ap.add_argument("--only", choices=["batched", "served"], default=None,
+                    help="run only that form and print its JSON object (for profiling)")
+    ap.add_argument("--form-reps", type=int, default=10, help="timed repetitions of the batched form")
+    ap.add_argument("--batched-tiling", default=None, help="points_per_lane,ctas_per_sm: skip the autotuner")
     return ap.parse_args()
 
 
@@ -65,7 +75,7 @@ C5 = {"sets": 16, "polys": (300, 1500), "rate": 2e5, "requests": 300_000, "warmu
       "max_points": 65536, "exact_fraction": 0.1, "plain_requests": 5_000, "saturate_rate": 4e6}
 
 
-def batched_form(agj, torch, reps: int = 10) -> dict:
+def batched_form(agj, torch, reps: int = 10, tiling=None) -> dict:
     """64 plain joins in sequence vs one batched plan (graph replay) over the
     same jobs, with the autotuned tiling; outputs compared job by job."""
     import numpy as np
@@ -82,7 +92,7 @@ def batched_form(agj, torch, reps: int = 10) -> dict:
     plain_pairs = [agj.Pairs(ix, n) for ix, n in zip(idx, ns)]
 
     def time_it(fn):
-        for _ in range(3):
+        for _ in range(1 if reps == 1 else 3):
             fn()
         torch.cuda.synchronize()
         ts = []
@@ -101,7 +111,10 @@ def batched_form(agj, torch, reps: int = 10) -> dict:
 
     plain_ms = time_it(plain)
     ref = [pr.to_host() for pr in plain_pairs]
-    tuned = autotune.tune(idx, pts, use_cache=False)
+    if tiling is None:
+        tuned = autotune.tune(idx, pts, use_cache=False)
+    else:
+        tuned = {"points_per_lane": tiling[0], "ctas_per_sm": tiling[1], "sweep": None}
     plan = agj.Batch(idx, ns, points_per_lane=tuned["points_per_lane"], ctas_per_sm=tuned["ctas_per_sm"])
     bp = plan.pairs()
     batch_ms = time_it(lambda: plan.run(pts, bp))
@@ -332,6 +345,16 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.only:
+        import torch
+        import paper_1802_09488_gb300 as agj
+        torch.cuda.set_device(local)
+        if args.only == "batched":
+            tiling = tuple(int(x) for x in args.batched_tiling.split(",")) if args.batched_tiling else None
+            print(json.dumps(batched_form(agj, torch, reps=args.form_reps, tiling=tiling)), flush=True)
+        else:
+            print(json.dumps(served_form(agj)), flush=True)
+        return
     import numpy as np
     import torch
     import paper_1802_09488_gb300 as agj
@@ -415,9 +438,12 @@ def main():
 
     def roof(kernel, bytes_per_pt, ms, note):
         achieved = bytes_per_pt * n / (ms / 1000.0) / 1e9
+        tb = PROBE_DRAM_BYTES_PER_POINT.get(kernel) if args.workload == "c2" else None
         return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
-                "algorithmic_bytes_per_point": bytes_per_pt, "ms_per_launch": ms, "note": note}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": tb * n if tb else None,
+                "traffic_unit": "DRAM bytes per launch (ncu capture of 16e6 points scaled by points)" if tb else None,
+                "peak_source": peaks["source"], "algorithmic_bytes_per_point": bytes_per_pt, "ms_per_launch": ms,
+                "note": note}
 
     t_pa = mean(stages["approx"]["k_probe_approx"])
     t_pe = mean(stages["exact"]["k_probe_exact"])
@@ -493,7 +519,7 @@ def main():
     if rank == 0 and not args.no_forms and args.workload == "c2":
         del pa, pe, d_pts
         torch.cuda.empty_cache()
-        result["batched"] = batched_form(agj, torch)
+        result["batched"] = batched_form(agj, torch, reps=args.form_reps)
         torch.cuda.empty_cache()
         result["served"] = served_form(agj)
 
