@@ -126,8 +126,8 @@ __device__ __forceinline__ uint64_t lookback(uint64_t* tiles, uint32_t tile, uin
 // a time from the 4-level Hilbert table as the walk consumes them (byte b
 // holds levels 4b+1 .. 4b+4).
 struct Walk {
-    uint32_t i32, j32;      // (i, j) << 2: levels 31-32 are zero padding
-    uint32_t o;             // Hilbert orientation before byte b
+    uint32_t i32, j32;      // (i, j) << (2 + 4 b): the next byte's 4 levels on top; 0 padding below
+    uint32_t o;             // Hilbert orientation before byte b, << 8 (the table's row)
     uint32_t b;             // next key byte
     uint32_t node;          // current trie node
     int32_t cert;           // key bytes whose levels are all certified
@@ -135,9 +135,10 @@ struct Walk {
 };
 
 __device__ __forceinline__ uint32_t next_byte(const uint16_t* lut, Walk& w) {
-    const uint32_t sh = 28u - 4u * w.b;
-    const uint32_t e = lut[(w.o << 8) | (((w.i32 >> sh) & 15u) << 4) | ((w.j32 >> sh) & 15u)];
-    w.o = e & 3u;
+    const uint32_t e = lut[w.o | ((w.i32 >> 24) & 0xF0u) | (w.j32 >> 28)];
+    w.i32 <<= 4;
+    w.j32 <<= 4;
+    w.o = (e & 3u) << 8;
     ++w.b;
     return e >> 2;
 }
@@ -169,7 +170,7 @@ __device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* fac
     if (fr.root == kNoRootDev) return;
     w.i32 = i << 2;
     w.j32 = j << 2;
-    w.o = (uint32_t)face & 1u;
+    w.o = ((uint32_t)face & 1u) << 8;
     w.b = 0;
     w.cert = lc >> 2;
     const uint32_t nb = fr.prefix_bits >> 3;
@@ -277,6 +278,18 @@ __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFac
         }
     }
     return gathers;
+}
+
+// Adds two per-thread counts (a < 2^15, b < 2^11 per thread) to two device
+// counters with one warp reduction and at most two atomics per warp.
+__device__ __forceinline__ void warp_count2(uint32_t a, uint32_t b, uint64_t* ca, uint64_t* cb) {
+    uint32_t v = a | (b << 20);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0) {
+        if (v & 0xFFFFFu) atomicAdd((unsigned long long*)ca, (unsigned long long)(v & 0xFFFFFu));
+        if (v >> 20) atomicAdd((unsigned long long*)cb, (unsigned long long)(v >> 20));
+    }
 }
 
 // Adds a per-thread count to a device counter with one atomic per warp.
@@ -516,9 +529,8 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
     }
     uint64_t e[PPT];
     uint32_t fallbacks = 0;
-    warp_count(probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, valid, e, &J.status[1], &fallbacks),
-               &J.status[3]);
-    warp_count(fallbacks, &J.counters[0]);
+    const uint32_t gathers = probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, valid, e, &J.status[1], &fallbacks);
+    warp_count2(gathers, fallbacks, &J.status[3], &J.counters[0]);
     const bool exact = job_exact<MODE>(J);
     uint32_t nc[PPT], csum = 0, tsum = 0;
 #pragma unroll
