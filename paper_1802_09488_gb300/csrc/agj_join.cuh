@@ -82,8 +82,8 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
         L.pstart = o; o += align256((n_polys + 1) * 4);
         L.cursor = o; o += align256((n_polys + 1) * 4);
         L.cstart = o; o += align256((n_polys + 1) * 4);
-        // refine chunks: one per kPipBlock candidates of a polygon, plus one partial per polygon
-        L.cpoly = o; o += align256((L.queue_cap / kPipBlock + n_polys + 1) * 4);
+        // refine chunk descriptors: one per kPipBlock candidates of a polygon, plus one partial per polygon
+        L.cpoly = o; o += align256((L.queue_cap / kPipBlock + n_polys + 1) * 16);
     }
     L.total = o;
     return L;
@@ -139,15 +139,13 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
             S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.pstart),
             reinterpret_cast<uint32_t*>(sc + L.cursor), reinterpret_cast<uint32_t*>(sc + L.cstart), hdr + 2,
-            reinterpret_cast<uint32_t*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
+            reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
             reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
         k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots,
                                             reinterpret_cast<uint32_t*>(sc + L.cursor),
                                             reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
         k_pip<Src><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, reinterpret_cast<const uint2*>(sc + L.sorted),
-                                                    reinterpret_cast<const uint32_t*>(sc + L.pstart),
-                                                    reinterpret_cast<const uint32_t*>(sc + L.cstart),
-                                                    reinterpret_cast<const uint32_t*>(sc + L.cpoly), hdr + 2, S.pass,
+                                                    reinterpret_cast<const uint4*>(sc + L.cpoly), hdr + 2, S.pass,
                                                     S.tile_count);
     }
     if (MODE == kModeApprox) {

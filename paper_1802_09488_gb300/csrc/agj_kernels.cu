@@ -100,7 +100,7 @@ constexpr int kPolyScanItems = 4;
 __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_polys,
                                                    uint32_t* __restrict__ poly_start, uint32_t* __restrict__ cursor,
                                                    uint32_t* __restrict__ chunk_start, uint32_t* __restrict__ n_chunks,
-                                                   uint32_t* __restrict__ chunk_poly, uint64_t* __restrict__ chunks,
+                                                   uint4* __restrict__ chunk_desc, uint64_t* __restrict__ chunks,
                                                    uint32_t* __restrict__ chunk_counter, uint64_t* __restrict__ err) {
     __shared__ uint64_t s_warp[8];
     __shared__ uint32_t s_chunk;
@@ -130,8 +130,12 @@ __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ 
             poly_start[i0 + k] = (uint32_t)o;
             cursor[i0 + k] = (uint32_t)o;
             chunk_start[i0 + k] = (uint32_t)(o >> 32);
+            // refine chunks of this polygon: (polygon, first candidate, candidates)
             const uint32_t c0 = (uint32_t)(o >> 32), nch = (uint32_t)(v[k] >> 32);
-            for (uint32_t t = 0; t < nch; ++t) chunk_poly[c0 + t] = (uint32_t)(i0 + k);
+            const uint32_t q = (uint32_t)o, cnt = (uint32_t)v[k];
+            for (uint32_t t = 0; t < nch; ++t)
+                chunk_desc[c0 + t] = make_uint4((uint32_t)(i0 + k), q + t * kPipBlock,
+                                                min((uint32_t)kPipBlock, cnt - t * kPipBlock), 0u);
         }
         o += v[k];
     }

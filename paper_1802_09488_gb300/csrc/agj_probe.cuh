@@ -624,12 +624,12 @@ __global__ void k_scan_counts(const uint32_t* __restrict__ tile_count, uint64_t 
 // Exclusive scans of the per-polygon candidate counts and of the per-polygon
 // refine chunks (kPipBlock candidates each), as one packed 64-bit scan
 // (count in the low 32 bits, chunks above) chained by the look-back; each
-// refine chunk's polygon goes to chunk_poly.  The CTA that finishes last
-// writes the totals.
+// refine chunk's (polygon, first candidate, candidates) goes to chunk_desc.
+// The CTA that finishes last writes the totals.
 __global__ void k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_polys,
                             uint32_t* __restrict__ poly_start, uint32_t* __restrict__ cursor,
                             uint32_t* __restrict__ chunk_start, uint32_t* __restrict__ n_chunks,
-                            uint32_t* __restrict__ chunk_poly, uint64_t* __restrict__ chunks,
+                            uint4* __restrict__ chunk_desc, uint64_t* __restrict__ chunks,
                             uint32_t* __restrict__ chunk_counter, uint64_t* __restrict__ err);
 
 // Candidates per polygon of the queue (tile_cand[t] items from slot
@@ -661,9 +661,7 @@ constexpr int kPipSmemBand = 4096;               // band-table words staged per 
 template <class Src>
 __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src src, uint32_t tile_points,
                                                                    const uint2* __restrict__ sorted,
-                                                                   const uint32_t* __restrict__ poly_start,
-                                                                   const uint32_t* __restrict__ chunk_start,
-                                                                   const uint32_t* __restrict__ chunk_poly,
+                                                                   const uint4* __restrict__ chunk_desc,
                                                                    const uint32_t* __restrict__ n_chunks,
                                                                    uint8_t* __restrict__ pass,
                                                                    uint32_t* __restrict__ tile_count) {
@@ -671,12 +669,20 @@ __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src
     __shared__ uint16_t s_band[kPipSmemBand];
     const uint32_t total = *n_chunks;
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
-        const uint32_t gp = chunk_poly[c];
-        const uint32_t q0 = poly_start[gp] + (c - chunk_start[gp]) * kPipBlock;
-        const uint32_t q1 = min(q0 + kPipBlock, poly_start[gp + 1]);
-        const JobDesc& JP = src.job(src.find_tile(sorted[q0].x / tile_points));
+        const uint4 cd = chunk_desc[c];                   // (polygon, first candidate, candidates)
+        const uint32_t gp = cd.x;
+        const bool have = threadIdx.x < cd.z;
+        // the candidate and its point do not depend on the polygon's data:
+        // their loads overlap the staging below
+        uint2 it = make_uint2(0u, 0u);
+        double2 pt = make_double2(0.0, 0.0);
+        if (have) {
+            it = sorted[cd.y + threadIdx.x];              // (global point, queue slot)
+            const JobDesc& J = src.job(src.find_tile(it.x / tile_points));
+            pt = J.pts[it.x - J.tile0 * tile_points];
+        }
+        const JobDesc& JP = src.job(src.find_tile(sorted[cd.y].x / tile_points));
         const uint32_t poly = gp - JP.poly0;
-        const uint32_t item = q0 + threadIdx.x;
         const uint32_t v0 = JP.X.poly_off[poly], V = JP.X.poly_off[poly + 1] - v0;
         const PolyLocal L = JP.X.poly_local[poly];
         const bool certified = JP.X.model.uv_enabled && L.ok && V <= (uint32_t)kPipSmemVerts;
@@ -687,18 +693,15 @@ __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src
         if (banded)
             for (uint32_t t = threadIdx.x; t < L.band_len; t += blockDim.x) s_band[t] = JP.X.poly_band[L.band + t];
         __syncthreads();
-        if (item < q1) {
-            const uint2 it = sorted[item];            // (global point, queue slot)
+        if (have) {
             const uint32_t wt = it.x / tile_points;
-            const JobDesc& J = src.job(src.find_tile(wt));
-            const double2 pt = J.pts[it.x - J.tile0 * tile_points];
             int r = -1;
             float pu, pv, dp;
             if (certified && model_uv_local(JP.X.model, pt.x, pt.y, L, &pu, &pv, &dp))
                 r = covers_certified(s_lv, V, L, banded ? s_band : nullptr, pu, pv, dp);
             if (r < 0) {
                 r = covers_fp64(JP.X, poly, pt.x, pt.y) ? 1 : 0;
-                atomicAdd((unsigned long long*)&J.counters[1], 1ull);
+                atomicAdd((unsigned long long*)&src.job(src.find_tile(wt)).counters[1], 1ull);
             }
             pass[it.y] = (uint8_t)r;
             if (r) atomicAdd(&tile_count[wt], 1u);

@@ -224,3 +224,18 @@ def test_c3_fine_overlapping_polygons(torch, agj, oracle, c3_small, mode, eps):
     _csr_equal(off, ids, eo, ei)
     hits = np.diff(np.asarray(off, np.int64))
     assert hits.max() >= 2 and (hits == 0).any()       # overlaps and gaps are exercised
+
+
+def test_c3_exact_many_polygons(torch, agj, oracle):
+    """More polygons than the shared-memory counters of the candidate
+    grouping hold (> 8192): counting and scattering use global atomics."""
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c3_fine_polygons(9000, seed=8)
+    pts = synth.points_mixture(200_000, synth.BOX_CITY, seed=9, dist_seed=8)
+    train = synth.points_mixture(20_000, synth.BOX_CITY, seed=10, dist_seed=8)
+    ix = agj.Index(polys, agj.EXACT, 0, train=train)
+    pr = agj.join(ix, _dev(torch, pts))
+    off, ids = pr.to_host()
+    eo, ei = oracle.PolySet(polys).join_exact(pts)
+    _csr_equal(off, ids, eo, ei)
+    assert pr.status.cpu().numpy()[2] > 10_000          # candidates were refined
