@@ -463,12 +463,15 @@ int agj_plain_load(const agj_index* const* indexes, uint32_t n_indexes, const ag
 int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz);
 
 /*
- * End-to-end join from host memory: copies h_points (n x {lat, lng}) to the
- * device, joins, and copies the CSR back (h_offsets: n + 1, h_ids: up to
- * h_ids_capacity).  Uses `work` (from agj_pairs_alloc or caller buffers for
- * n points) plus d_points_staging (device, n x 16 bytes).  Synchronises
- * `stream`.  *nnz receives the pair count; AGJ_ECAPACITY if h_ids is too
- * small (h_offsets is still filled).
+ * End-to-end join from host memory: h_points (n x {lat, lng}) are read by
+ * the probe where they are when the device can read them (pinned memory, or
+ * pageable memory on devices that read the host's page tables, as GB300 over
+ * NVLink-C2C; 16-byte aligned) and copied to d_points_staging (device, n x 16
+ * bytes; may be NULL when not needed) otherwise; the CSR comes back to
+ * h_offsets (n + 1) and h_ids (up to h_ids_capacity).  Uses `work` (from
+ * agj_pairs_alloc or caller buffers for n points).  Synchronises `stream`.
+ * *nnz receives the pair count; AGJ_ECAPACITY if h_ids is too small
+ * (h_offsets is still filled).
  */
 int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, double* d_points_staging,
                   agj_pairs* work, uint32_t* h_offsets, uint32_t* h_ids, uint64_t h_ids_capacity,

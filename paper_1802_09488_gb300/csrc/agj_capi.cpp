@@ -22,6 +22,28 @@ namespace {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+// The address kernels on the current device read host buffer p through, or
+// null: pinned (registered) memory through its device mapping, pageable
+// memory where the device reads the host's page tables; 16-byte aligned
+// buffers only (the probe loads 16-byte points).
+const void* device_view(const void* p) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) & 15u) != 0) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    int dev = 0, pageable = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return pageable == 1 ? p : nullptr;
+}
+
 thread_local std::string g_last_error;
 
 }  // namespace
@@ -286,12 +308,19 @@ int agj_join_batched(const agj_index* const* indexes, const double* const* d_poi
 int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, double* d_points_staging,
                   agj_pairs* work, uint32_t* h_offsets, uint32_t* h_ids, uint64_t h_ids_capacity, uint64_t* nnz,
                   void* stream) {
-    if (!index || !index->X.d_blob || !work || !h_offsets || (n && (!h_points || !d_points_staging)))
-        return AGJ_EINVAL;
+    if (!index || !index->X.d_blob || !work || !h_offsets || (n && !h_points)) return AGJ_EINVAL;
     cudaStream_t s = as_stream(stream);
-    if (n && cudaMemcpyAsync(d_points_staging, h_points, n * 16, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return AGJ_ECUDA;
-    int rc = agj::launch_join(index->X, d_points_staging, n, s, work);
+    // the probe reads the points where they are when the device can
+    // (pinned memory, or pageable memory read through the host's page
+    // tables); otherwise they are copied to the staging buffer first
+    const double* src = n ? static_cast<const double*>(device_view(h_points)) : nullptr;
+    if (n && !src) {
+        if (!d_points_staging) return AGJ_EINVAL;
+        if (cudaMemcpyAsync(d_points_staging, h_points, n * 16, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return AGJ_ECUDA;
+        src = d_points_staging;
+    }
+    int rc = agj::launch_join(index->X, src, n, s, work);
     if (rc != AGJ_OK) return rc;
     if (cudaMemcpyAsync(h_offsets, work->offsets, (n + 1) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return AGJ_ECUDA;

@@ -239,3 +239,22 @@ def test_c3_exact_many_polygons(torch, agj, oracle):
     eo, ei = oracle.PolySet(polys).join_exact(pts)
     _csr_equal(off, ids, eo, ei)
     assert pr.status.cpu().numpy()[2] > 10_000          # candidates were refined
+
+
+def test_join_host_pinned_pageable_and_unaligned(torch, agj, c1):
+    """The end-to-end host call gives the device join's CSR whether the
+    points are pinned, pageable, or unaligned (staged) host memory."""
+    ix = agj.Index(c1.polygons, agj.EXACT, 0, train=c1.points[:1000])
+    pts = np.ascontiguousarray(c1.points[:50_000])
+    ref_off, ref_ids = agj.join(ix, _dev(torch, pts)).to_host()
+    pairs = agj.Pairs(ix, len(pts))
+    staging = torch.empty((len(pts), 2), dtype=torch.float64, device="cuda")
+    raw = np.empty(2 * len(pts) + 1)
+    odd = raw[1:].reshape(-1, 2)
+    odd[:] = pts
+    for src in (torch.from_numpy(pts).pin_memory(), pts, odd):
+        off = np.empty(len(pts) + 1, dtype=np.uint32)
+        ids = np.empty(len(ref_ids) + 8, dtype=np.uint32)
+        nnz = agj.join_host(ix, src, pairs, staging, off, ids)
+        assert nnz == len(ref_ids)
+        assert np.array_equal(off, ref_off) and np.array_equal(ids[:nnz], ref_ids)
