@@ -477,6 +477,19 @@ int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, do
                   agj_pairs* work, uint32_t* h_offsets, uint32_t* h_ids, uint64_t h_ids_capacity,
                   uint64_t* nnz, void* stream);
 
+/*
+ * Self-test of the join's bounded device-side waits (no counterpart in the
+ * paper).  The tile scan chains CTA chunks by a look-back that waits for
+ * each predecessor's published state, with a bounded spin after which it
+ * sets the "scan wait timed out" bit of the join's status instead of
+ * hanging.  This runs the scan as the second chunk while the first never
+ * publishes: it returns AGJ_ETIMEOUT when the wait ran out and was
+ * reported (the expected outcome, after about a second), AGJ_OK if it was
+ * not, AGJ_ENOMEM / AGJ_ECUDA on setup errors.  The context stays usable.
+ * Synchronises `stream`.
+ */
+int agj_selftest_scan_timeout(void* stream);
+
 /* Cell ids of points with the device kernel (FP64 spec, bit-exact); for
  * checking the id step alone.  d_ids: device, n uint64. */
 int agj_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, void* stream);

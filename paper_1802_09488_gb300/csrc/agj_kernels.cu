@@ -478,6 +478,42 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
 }
 
 // ---------------------------------------------------------------------------
+// self-test of the bounded waits
+// ---------------------------------------------------------------------------
+// The tile scan's look-back waits for its predecessor chunks with a bounded
+// spin.  Here one CTA runs the scan as chunk 1 (its ticket counter starts
+// at 1) while chunk 0's state is never published: the wait must run out,
+// set kErrScanTimeout and return, leaving the context usable.
+int selftest_scan_timeout(cudaStream_t s) {
+    constexpr uint64_t kTiles = 2 * 256 * kScanItems;     // two chunks' worth of tiles
+    char* d = nullptr;
+    const uint64_t bytes = 256 + 256 + kTiles * 8;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) { cudaGetLastError(); return AGJ_ENOMEM; }
+    uint32_t* counter = reinterpret_cast<uint32_t*>(d);
+    uint64_t* err = reinterpret_cast<uint64_t*>(d) + 1;
+    uint64_t* chunks = reinterpret_cast<uint64_t*>(d + 256);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(d + 512);
+    uint32_t* prefix = counts + kTiles;
+    const uint32_t one = 1;
+    int rc = AGJ_OK;
+    if (cudaMemsetAsync(d, 0, bytes, s) != cudaSuccess ||
+        cudaMemcpyAsync(counter, &one, 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = AGJ_ECUDA;
+    if (rc == AGJ_OK) {
+        k_scan_counts<<<1, 256, 0, s>>>(counts, kTiles, prefix, chunks, counter, err, nullptr, nullptr);
+        uint64_t e = 0;
+        if (cudaMemcpyAsync(&e, err, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = AGJ_ECUDA;
+        else
+            rc = (e & kErrScanTimeout) ? AGJ_ETIMEOUT : AGJ_OK;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(d);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
 // approximate join without any allocation
 // ---------------------------------------------------------------------------
 // The one-pass approximate join needs work space for its tile scan: a

@@ -18,6 +18,8 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
 int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t n, uint32_t* d_offsets,
                                uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, cudaStream_t s);
 int launch_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, cudaStream_t s);
+// Runs the tile scan with a predecessor that never publishes (see agj.h).
+int selftest_scan_timeout(cudaStream_t s);
 
 // Batched form (agj_batch.cu): a plan for m (index, point count) jobs with
 // its own work space and, with use_graph, an instantiated CUDA graph.

@@ -258,3 +258,14 @@ def test_join_host_pinned_pageable_and_unaligned(torch, agj, c1):
         nnz = agj.join_host(ix, src, pairs, staging, off, ids)
         assert nnz == len(ref_ids)
         assert np.array_equal(off, ref_off) and np.array_equal(ids[:nnz], ref_ids)
+
+
+def test_scan_wait_is_bounded_and_reported(torch, agj, c1):
+    """A look-back whose predecessor never publishes runs out its bounded
+    wait, reports AGJ_ETIMEOUT, and leaves the device usable."""
+    import ctypes
+    rc = agj.lib().agj_selftest_scan_timeout(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 6                      # AGJ_ETIMEOUT
+    ix = agj.Index(c1.polygons, agj.APPROX, c1.eps_m)
+    off, ids = agj.join(ix, _dev(torch, c1.points[:10_000])).to_host()
+    assert off[-1] == len(ids) > 0
