@@ -211,17 +211,29 @@ __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFac
 #pragma unroll 1
     for (int d = 0; d < 8; ++d) {
         uint64_t v[PPT];
+        if (d == 0 && s_root) {
+            // with the fast model every walk starts at the model face's root,
+            // which each CTA holds in shared memory
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            v[k] = 0;
-            if (w[k].st == 1) {
-                if (w[k].b >= (uint32_t)w[k].cert) {
-                    w[k].st = 2;
-                } else {
-                    const uint32_t byte = next_byte(lut, w[k]);
-                    // with the fast model every walk starts at the model face's root,
-                    // which each CTA holds in shared memory
-                    v[k] = (d == 0 && s_root) ? s_root[byte] : __ldg(X.nodes + (((uint64_t)w[k].node) << 8) + byte);
+            for (int k = 0; k < PPT; ++k) {
+                v[k] = 0;
+                if (w[k].st == 1) {
+                    if (w[k].b >= (uint32_t)w[k].cert) w[k].st = 2;
+                    else v[k] = s_root[next_byte(lut, w[k])];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                v[k] = 0;
+                if (w[k].st == 1) {
+                    if (w[k].b >= (uint32_t)w[k].cert) {
+                        w[k].st = 2;
+                    } else {
+                        const uint32_t byte = next_byte(lut, w[k]);
+                        const uint64_t* row = X.nodes + (size_t)w[k].node * 256u;
+                        v[k] = __ldg(row + byte);
+                    }
                 }
             }
         }
