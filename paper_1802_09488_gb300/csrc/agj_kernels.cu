@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(kJoinBlock, kNoAllocMinBlocks) k_join_approx(
     }
     uint64_t e[PPT];
     uint32_t fallbacks = 0;
-    warp_count(probe_points<PPT>(X, s_faces, s_hlut, s_root, lat, lng, valid, e, &status[1], &fallbacks), &status[3]);
+    warp_count(probe_points<PPT>(X, s_faces, s_hlut, s_root, lat, lng, pts + base + lane, valid, e, &status[1],
+                                 &fallbacks),
+               &status[3]);
     warp_count(fallbacks, fallback_counter);
     uint32_t c[PPT], ex[PPT], run = 0;
 #pragma unroll

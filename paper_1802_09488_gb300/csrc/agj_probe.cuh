@@ -35,6 +35,9 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 #ifndef AGJ_BATCH_PROBE_MIN_BLOCKS
 #define AGJ_BATCH_PROBE_MIN_BLOCKS 5
 #endif
+#ifndef AGJ_APPROX_PROBE_MIN_BLOCKS
+#define AGJ_APPROX_PROBE_MIN_BLOCKS 6     // the single-job approximate probe: 40 registers pay there
+#endif
 constexpr int kJoinBlock = 256;
 constexpr int kJoinPPT = 2;                    // points per lane of the plain join
 constexpr int kWarpsPerBlock = kJoinBlock / 32;
@@ -189,12 +192,14 @@ __device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* fac
 // Walks of PPT points advance level by level together, so their gathers
 // (Listing "Probe Adaptive Cell Trie") are in flight at the same time.
 // Points whose walk needs an uncertified key byte get their FP64 id and walk
-// again alone (counted in *fallbacks).  Returns the trie entries read.
+// again alone (counted in *fallbacks); they reload their coordinates from
+// pts[32 k] (the lane's points), so lat/lng need no registers during the
+// walk.  Returns the trie entries read.
 template <int PPT>
 __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
                                                  const uint64_t* s_root, const double* lat, const double* lng,
-                                                 const bool* valid, uint64_t e[PPT], uint64_t* err,
-                                                 uint32_t* fallbacks) {
+                                                 const double2* pts, const bool* valid, uint64_t e[PPT],
+                                                 uint64_t* err, uint32_t* fallbacks) {
     uint32_t gathers = 0;
     Walk w[PPT];
 #pragma unroll
@@ -267,7 +272,8 @@ __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFac
         } else if (w[k].st == 2) {
             ++*fallbacks;
             Walk x;
-            begin_walk(X, faces, lut, lat[k], lng[k], true, x);
+            const double2 q = pts[32 * k];
+            begin_walk(X, faces, lut, q.x, q.y, true, x);
             e[k] = 0;
             while (x.st == 1) {
                 if (x.b >= 8u) {
@@ -541,7 +547,8 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
     }
     uint64_t e[PPT];
     uint32_t fallbacks = 0;
-    const uint32_t gathers = probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, valid, e, &J.status[1], &fallbacks);
+    const uint32_t gathers =
+        probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, J.pts + base + lane, valid, e, &J.status[1], &fallbacks);
     warp_count2(gathers, fallbacks, &J.status[3], &J.counters[0]);
     const bool exact = job_exact<MODE>(J);
     uint32_t nc[PPT], csum = 0, tsum = 0;
@@ -585,7 +592,9 @@ __device__ __forceinline__ const uint64_t* cta_stage_job(const JobDesc& J, DevFa
 // changes; the grid either covers the tile space (one warp per tile) or is
 // persistent and strides over it.
 template <int PPT, class Src, int MODE>
-__global__ void __launch_bounds__(kJoinBlock, Src::kSingle ? AGJ_PROBE_MIN_BLOCKS : AGJ_BATCH_PROBE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kJoinBlock, !Src::kSingle ? AGJ_BATCH_PROBE_MIN_BLOCKS
+                                                 : MODE == kModeApprox ? AGJ_APPROX_PROBE_MIN_BLOCKS
+                                                                       : AGJ_PROBE_MIN_BLOCKS)
     k_probe(const Src src, uint64_t T, const JoinScratch S) {
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
