@@ -33,11 +33,11 @@ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 //   [entries u64 per point] [tile counts u32] [tile prefixes u32]
 //   then, with exact jobs, the per-tile candidate counts, the candidate
 //   queue (a region of tile_slots per tile), its pass bytes, its polygon
-//   order and the per-polygon segments and refine chunks
+//   order, the per-polygon cursors and the refine chunk descriptors
 struct JoinLayout {
     uint64_t chunks = 0, pchunks = 0, pcount = 0, zero_end = 0;
     uint64_t entries = 0, tcount = 0, tprefix = 0;
-    uint64_t tcand = 0, queue = 0, pass = 0, sorted = 0, pstart = 0, cursor = 0, cstart = 0, cpoly = 0, total = 0;
+    uint64_t tcand = 0, queue = 0, pass = 0, sorted = 0, cursor = 0, cpoly = 0, total = 0;
     uint64_t n_points = 0, n_tiles = 0, n_chunks = 0, n_pchunks = 0, queue_cap = 0, n_polys = 0;
     uint32_t tile_slots = 0;
     bool exact = false;
@@ -79,9 +79,7 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
         L.queue = o; o += align256(L.queue_cap * 8 + 8);
         L.pass = o; o += align256(L.queue_cap + 32);
         L.sorted = o; o += align256(L.queue_cap * 8 + 8);
-        L.pstart = o; o += align256((n_polys + 1) * 4);
         L.cursor = o; o += align256((n_polys + 1) * 4);
-        L.cstart = o; o += align256((n_polys + 1) * 4);
         // refine chunk descriptors: one per kPipBlock candidates of a polygon, plus one partial per polygon
         L.cpoly = o; o += align256((L.queue_cap / kPipBlock + n_polys + 1) * 16);
     }
@@ -137,8 +135,7 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
         k_count<<<G.sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, S.poly_count,
                                           (uint32_t)L.n_polys);
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
-            S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.pstart),
-            reinterpret_cast<uint32_t*>(sc + L.cursor), reinterpret_cast<uint32_t*>(sc + L.cstart), hdr + 2,
+            S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.cursor), hdr + 2,
             reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
             reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
         k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots,

@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(256) k_scan_counts(const uint32_t* __restrict_
 
 constexpr int kPolyScanItems = 4;
 __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_polys,
-                                                   uint32_t* __restrict__ poly_start, uint32_t* __restrict__ cursor,
-                                                   uint32_t* __restrict__ chunk_start, uint32_t* __restrict__ n_chunks,
+                                                   uint32_t* __restrict__ cursor, uint32_t* __restrict__ n_chunks,
                                                    uint4* __restrict__ chunk_desc, uint64_t* __restrict__ chunks,
                                                    uint32_t* __restrict__ chunk_counter, uint64_t* __restrict__ err) {
     __shared__ uint64_t s_warp[8];
@@ -127,9 +126,7 @@ __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ 
 #pragma unroll
     for (int k = 0; k < kPolyScanItems; ++k) {
         if (i0 + k < n_polys) {
-            poly_start[i0 + k] = (uint32_t)o;
             cursor[i0 + k] = (uint32_t)o;
-            chunk_start[i0 + k] = (uint32_t)(o >> 32);
             // refine chunks of this polygon: (polygon, first candidate, candidates)
             const uint32_t c0 = (uint32_t)(o >> 32), nch = (uint32_t)(v[k] >> 32);
             const uint32_t q = (uint32_t)o, cnt = (uint32_t)v[k];
@@ -141,8 +138,6 @@ __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ 
     }
     if (chunk == gridDim.x - 1 && threadIdx.x == 0) {
         const uint64_t t = s_prefix + total;
-        poly_start[n_polys] = (uint32_t)t;
-        chunk_start[n_polys] = (uint32_t)(t >> 32);
         *n_chunks = (uint32_t)(t >> 32);
     }
 }

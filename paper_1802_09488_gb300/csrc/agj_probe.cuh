@@ -646,10 +646,10 @@ __global__ void k_scan_counts(const uint32_t* __restrict__ tile_count, uint64_t 
 // refine chunks (kPipBlock candidates each), as one packed 64-bit scan
 // (count in the low 32 bits, chunks above) chained by the look-back; each
 // refine chunk's (polygon, first candidate, candidates) goes to chunk_desc.
-// The CTA that finishes last writes the totals.
+// The CTA that finishes last writes the refine chunk count; cursor receives
+// each polygon's first slot in the grouped order (the scatter's cursors).
 __global__ void k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_polys,
-                            uint32_t* __restrict__ poly_start, uint32_t* __restrict__ cursor,
-                            uint32_t* __restrict__ chunk_start, uint32_t* __restrict__ n_chunks,
+                            uint32_t* __restrict__ cursor, uint32_t* __restrict__ n_chunks,
                             uint4* __restrict__ chunk_desc, uint64_t* __restrict__ chunks,
                             uint32_t* __restrict__ chunk_counter, uint64_t* __restrict__ err);
 
