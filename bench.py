@@ -263,6 +263,17 @@ def workload(name: str, n: int, rank: int):
     return polys, pts, train
 
 
+def step_config(args, n: int, n_polys: int, eps: float, n_train: int, world: int) -> dict:
+    """The workload both arms report: per-GPU point count, polygons, precision
+    and training sample of the exact index."""
+    return {"workload": f"{WORKLOADS[args.workload]['name']}-{n:.0e}".replace("+", ""), "n_points_per_gpu": n,
+            "polygons": n_polys, "eps_m": eps, "exact_train_points": n_train,
+            "step": "approx join + exact join of the same points",
+            "l2": f"inputs (16 B x {n:.0e} = {16 * n / 1e9:.2f} GB) " + ("larger than L2, no flush" if 16 * n > 2e8
+                                                                         else "smaller than L2: warm-cache figure"),
+            "parallelism": f"replicas x{world}"}
+
+
 def cpu_oracle_rate(polys, cells, ro, refs, pts, budget_s: float = 12.0):
     """Oracle points/s on the host cores for approx (sorted-vector probe of the
     logical covering) and exact (grid-prefiltered brute force), each on a
@@ -327,12 +338,11 @@ def run_reference(args, rank: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["name"], "eps_m": eps, "exact_train": "1% sample",
-                       "step": "approx join + exact join of the same points",
-                       "reference": "CPU oracle (oracle/oracle.c) on the host cores, bounded sample per step"},
+            "config": step_config(args, args.n_points, len(polys), eps, max(args.n_points // 100, 1000), args.gpus),
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{m} points per step (approx sorted-vector probe + exact brute force), "
-                                       f"{cores} threads"},
+                             "sample": f"{m} of the workload's points per step, drawn from the first {n} of its "
+                                       f"stream (approx sorted-vector probe + exact brute force by the CPU oracle, "
+                                       f"oracle/oracle.c), {cores} threads"},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -463,12 +473,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOADS[args.workload]['name']}-{n:.0e}".replace("+", ""), "n_points_per_gpu": n,
-                   "polygons": len(polys), "eps_m": eps, "exact_train_points": len(train),
-                   "step": "approx join + exact join of the same points",
-                   "l2": f"inputs (16 B x {n:.0e} = {16 * n / 1e9:.2f} GB) " + ("larger than L2, no flush" if 16 * n > 2e8
-                                                                                 else "smaller than L2: warm-cache figure"),
-                   "parallelism": f"replicas x{world}"},
+        "config": step_config(args, n, len(polys), eps, len(train), world),
         "modes": {
             "approx": {"points_per_s": n / (statistics.mean(approx_ms) / 1000.0), "p50_ms": pct(approx_ms, 50),
                        "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_per_pt,
