@@ -415,11 +415,19 @@ def main():
     step_ev = [(mk(), mk()) for _ in range(args.steps)]
     stage_ev = [([mk() for _ in range(4)], [mk() for _ in range(4)]) for _ in range(args.steps)]
     barrier()
+    # A GPU hold ahead of the first timed event lets the host enqueue every
+    # step before the device reaches them, so small joins are timed without
+    # host launch gaps between their kernels (the host's per-call cost is in
+    # `e2e`).  If the device still drains the queue first, the line says so.
+    hold_ms = 1.0 + 0.5 * args.steps
+    torch.cuda._sleep(int(hold_ms * 2.0e6))
+    hold_end = mk()
     for k in range(args.steps):
         step_ev[k][0].record(stream)
         agj.join_timed(ia, d_pts, pa, stage_ev[k][0])
         agj.join_timed(ie, d_pts, pe, stage_ev[k][1])
         step_ev[k][1].record(stream)
+    host_ahead = not hold_end.query()
     barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
@@ -473,7 +481,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": step_config(args, n, len(polys), eps, len(train), world),
+        "config": dict(step_config(args, n, len(polys), eps, len(train), world),
+                       enqueue=(f"all {args.steps} steps enqueued behind a {hold_ms:.0f} ms GPU hold before the first "
+                                f"timed event" if host_ahead else
+                                "host enqueue fell behind the device: timings include host launch gaps")),
         "modes": {
             "approx": {"points_per_s": n / (statistics.mean(approx_ms) / 1000.0), "p50_ms": pct(approx_ms, 50),
                        "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_per_pt,

@@ -53,11 +53,15 @@ __global__ void __launch_bounds__(256) k_jobs_init(const JobDesc* __restrict__ j
 // polygon spaces, and the device memory it needs, as offsets from a base:
 //   [job descriptors][job of each tile u16]   <- the tables a launch uploads
 //   [job bases u32][per-job counters 2 x u64][join work space]
+// The approximate jobs' tiles come first (tiles 0 .. Ta - 1), the exact
+// jobs' after them, each in the callers' order, so each mode's probe and emit
+// run as their own launch, compiled for that mode.
 struct Shape {
     uint32_t m = 0;
     int ppt = 2;
-    uint64_t T = 0, P = 0;
-    std::vector<uint64_t> tile0;   // m + 1
+    uint64_t T = 0, P = 0, Ta = 0;
+    std::vector<uint64_t> tile0;   // m: first tile of each job
+    std::vector<uint64_t> tile1;   // m: end of each job's tiles
     std::vector<uint32_t> poly0;   // m
     JoinLayout L;
     uint64_t off_jobs = 0, off_tile_job = 0, table_bytes = 0;
@@ -70,8 +74,9 @@ int make_shape(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, in
     if (m > kMaxBatchJobs) return AGJ_EUNSUPPORTED;
     S->m = m;
     S->ppt = ppt;
-    S->tile0.clear();
-    S->poly0.clear();
+    S->tile0.assign(m, 0);
+    S->tile1.assign(m, 0);
+    S->poly0.assign(m, 0);
     uint64_t T = 0, P = 0;
     uint32_t mcr = 1;    // most candidate references of a point over the exact jobs
     bool any_exact = false;
@@ -80,7 +85,21 @@ int make_shape(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, in
         const Index* x = X[j];
         if (!x || !x->d_blob || x->device != dev || n[j] >= 0xFFFFFFFFull) return AGJ_EINVAL;
         if (n[j] * std::max<uint64_t>(x->stats.max_refs, 1) >= 0xFFFFFFFFull) return AGJ_ECAPACITY;
-        S->tile0.push_back(T);
+    }
+    // tiles: the approximate jobs, then the exact ones; whole CTAs per job,
+    // so a CTA's tiles share one job
+    for (int exact = 0; exact < 2; ++exact) {
+        if (exact) S->Ta = T;
+        for (uint32_t j = 0; j < m; ++j) {
+            if ((X[j]->mode == AGJ_EXACT) != (exact == 1)) continue;
+            S->tile0[j] = T;
+            T += (n[j] + 32 * ppt - 1) / (32 * ppt);
+            T = (T + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
+            S->tile1[j] = T;
+        }
+    }
+    for (uint32_t j = 0; j < m; ++j) {
+        const Index* x = X[j];
         uint32_t pb = 0;
         if (x->mode == AGJ_EXACT) {
             any_exact = true;
@@ -94,15 +113,11 @@ int make_shape(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, in
                 pb = it->second;
             }
         }
-        S->poly0.push_back(pb);
-        // whole CTAs per job: a CTA's tiles share one job
-        T += (n[j] + 32 * ppt - 1) / (32 * ppt);
-        T = (T + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
+        S->poly0[j] = pb;
     }
     const uint32_t slots = 32u * (uint32_t)ppt * mcr;
     if (P >= 0xFFFFFFFFull || T * 32 * ppt >= 0xFFFFFFFFull || (any_exact && T * slots >= 0xFFFFFFFFull))
         return AGJ_ECAPACITY;   // 32-bit point, polygon and queue indices
-    S->tile0.push_back(T);
     S->T = T;
     S->P = P;
     S->L = join_layout(T * 32 * ppt, T, any_exact, any_exact ? slots : 0u, P);
@@ -119,7 +134,7 @@ int make_shape(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, in
 
 void fill_tile_job(const Shape& S, uint16_t* tile_job) {
     for (uint32_t j = 0; j < S.m; ++j)
-        std::fill(tile_job + S.tile0[j], tile_job + S.tile0[j + 1], (uint16_t)j);
+        std::fill(tile_job + S.tile0[j], tile_job + S.tile1[j], (uint16_t)j);
 }
 
 // Job descriptors of one launch; counters: the per-job diagnostic words in
@@ -151,22 +166,38 @@ cudaError_t enqueue_kernels(const Shape& S, char* base, int ctas_per_sm, cudaStr
     src.tile_job = reinterpret_cast<const uint16_t*>(base + S.off_tile_job);
     src.base = reinterpret_cast<const uint32_t*>(base + S.off_job_base);
     src.m = S.m;
+    src.t0 = 0;
+    src.ta = S.Ta;
     k_jobs_init<<<(S.m + 255) / 256, 256, 0, s>>>(src.d, S.m);
     JoinLaunch G;
     G.sms = sm_count();
-    const uint64_t need = (S.L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (ctas_per_sm == 0) {            // one warp per tile
-        G.probe_grid = (int)std::max<uint64_t>(1, need);
-        G.emit_grid = G.probe_grid;
-    } else {                           // persistent grids
-        G.probe_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)G.sms * ctas_per_sm));
-        // the emit is short and latency-bound: a full-occupancy grid
-        G.emit_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)G.sms * 8));
-    }
+    // per mode: one warp per tile, or persistent grids (the emit is short and
+    // latency-bound: a full-occupancy grid)
+    auto grids = [&](uint64_t tiles, int* probe, int* emit) {
+        const uint64_t need = std::max<uint64_t>(1, (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        *probe = (int)(ctas_per_sm == 0 ? need : std::min<uint64_t>(need, (uint64_t)G.sms * ctas_per_sm));
+        *emit = (int)(ctas_per_sm == 0 ? need : std::min<uint64_t>(need, (uint64_t)G.sms * 8));
+    };
+    G.persistent = ctas_per_sm != 0;
     G.pip_grid = G.sms * AGJ_PIP_MIN_BLOCKS;
     G.tile_job = src.tile_job;
     G.job_base = reinterpret_cast<uint32_t*>(base + S.off_job_base);
-    return enqueue_join<PPT, ManyJobs, kModeAny>(src, S.L, base + S.off_scratch, G, nullptr, 0, s, nullptr);
+    char* sc = base + S.off_scratch;
+    // One mode: that mode's kernels.  Both, over many tiles (16 waves and
+    // more, ~6e6 points): each mode's probe and emit as their own launches
+    // (the approximate ones at 6 CTAs per SM, no per-job mode branches); over
+    // fewer (a served step) the two extra launches cost more than they save,
+    // so one launch reads each job's mode.
+    const uint64_t split_min = (uint64_t)G.sms * AGJ_PROBE_MIN_BLOCKS * kWarpsPerBlock * 16;
+    if (S.Ta == S.T || S.Ta == 0 || S.T < split_min) {
+        grids(S.T, &G.probe_grid, &G.emit_grid);
+        if (S.Ta == S.T) return enqueue_join<PPT, ManyJobs, kModeApprox>(src, S.L, sc, G, nullptr, 0, s, nullptr);
+        if (S.Ta == 0) return enqueue_join<PPT, ManyJobs, kModeExact>(src, S.L, sc, G, nullptr, 0, s, nullptr);
+        return enqueue_join<PPT, ManyJobs, kModeAny>(src, S.L, sc, G, nullptr, 0, s, nullptr);
+    }
+    grids(S.Ta, &G.probe_grid_a, &G.emit_grid_a);
+    grids(S.T - S.Ta, &G.probe_grid, &G.emit_grid);
+    return enqueue_join<PPT, ManyJobs, kModeSplit>(src, S.L, sc, G, nullptr, 0, s, nullptr);
 }
 
 cudaError_t enqueue(const Shape& S, char* base, int ctas_per_sm, cudaStream_t s) {

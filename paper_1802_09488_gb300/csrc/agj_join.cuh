@@ -102,9 +102,12 @@ inline JoinScratch join_scratch(const JoinLayout& L, char* sc) {
 }
 
 struct JoinLaunch {
-    int probe_grid = 0;       // CTAs of the probe kernel
-    int emit_grid = 0;        // CTAs of the emit kernel
+    int probe_grid = 0;       // CTAs of the probe kernel (kModeSplit: of the exact tiles' probe)
+    int emit_grid = 0;        // CTAs of the emit kernel (kModeSplit: of the exact tiles' emit)
+    int probe_grid_a = 0;     // kModeSplit: CTAs of the approximate tiles' probe
+    int emit_grid_a = 0;      // kModeSplit: CTAs of the approximate tiles' emit
     int sms = 1;              // for the grid-stride kernels
+    bool persistent = false;  // batched form: probe grids smaller than the tile space stride over it
     int pip_grid = 0;
     const uint16_t* tile_job = nullptr;   // batched form: job of each tile
     uint32_t* job_base = nullptr;         // batched form: tile prefix at each job's first tile
@@ -128,17 +131,43 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
         k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint64_t*>(sc), zero_words, extra_zero, n_extra);
     }
     mark(0);
-    if (L.n_tiles) k_probe<PPT, Src, MODE><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+    if constexpr (MODE == kModeSplit) {
+        // the batched form's approximate tiles, then its exact ones
+        Src a = src, x = src;
+        a.t0 = 0;
+        x.t0 = src.ta;
+        if (G.persistent) {
+            if (src.ta) k_probe<PPT, Src, kModeApprox, true><<<G.probe_grid_a, kJoinBlock, 0, s>>>(a, src.ta, S);
+            if (L.n_tiles > src.ta)
+                k_probe<PPT, Src, kModeExact, true><<<G.probe_grid, kJoinBlock, 0, s>>>(x, L.n_tiles, S);
+        } else {
+            if (src.ta) k_probe<PPT, Src, kModeApprox><<<G.probe_grid_a, kJoinBlock, 0, s>>>(a, src.ta, S);
+            if (L.n_tiles > src.ta) k_probe<PPT, Src, kModeExact><<<G.probe_grid, kJoinBlock, 0, s>>>(x, L.n_tiles, S);
+        }
+    } else {
+        if (L.n_tiles) {
+            if constexpr (!Src::kSingle) {
+                if (G.persistent) {
+                    k_probe<PPT, Src, MODE, true><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+                } else {
+                    k_probe<PPT, Src, MODE><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+                }
+            } else {
+                k_probe<PPT, Src, MODE><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+            }
+        }
+    }
     mark(1);
     const bool refine = MODE != kModeApprox && L.exact && L.n_polys;
     if (refine && L.n_tiles) {
-        k_count<<<G.sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, S.poly_count,
+        const uint32_t ct = refine_chunk_tiles(L.n_tiles, G.sms);
+        k_count<<<G.sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, S.poly_count,
                                           (uint32_t)L.n_polys);
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
             S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.cursor), hdr + 2,
             reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
             reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
-        k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots,
+        k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct,
                                             reinterpret_cast<uint32_t*>(sc + L.cursor),
                                             reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
         k_pip<Src><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, reinterpret_cast<const uint2*>(sc + L.sorted),
@@ -160,7 +189,15 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
                                                                reinterpret_cast<uint64_t*>(sc) + kHdrScanErr,
                                                                G.tile_job, G.job_base);
     }
-    if (L.n_tiles) k_emit<PPT, Src, MODE><<<G.emit_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+    if constexpr (MODE == kModeSplit) {
+        Src a = src, x = src;
+        a.t0 = 0;
+        x.t0 = src.ta;
+        if (src.ta) k_emit<PPT, Src, kModeApprox><<<G.emit_grid_a, kJoinBlock, 0, s>>>(a, src.ta, S);
+        if (L.n_tiles > src.ta) k_emit<PPT, Src, kModeExact><<<G.emit_grid, kJoinBlock, 0, s>>>(x, L.n_tiles, S);
+    } else {
+        if (L.n_tiles) k_emit<PPT, Src, MODE><<<G.emit_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
+    }
     mark(3);
     return cudaGetLastError();
 }

@@ -142,19 +142,21 @@ __global__ void __launch_bounds__(256) k_poly_scan(const uint32_t* __restrict__ 
     }
 }
 
-// The candidates queued by a chunk of kChunkTiles tiles (tile t holds
+// The candidates queued by a chunk of ct <= kChunkTiles tiles (tile t holds
 // tile_cand[t] items from slot t x tile_slots) are numbered densely: the
 // chunk's counts are scanned into s_off, and item i lives in the last tile
 // whose offset is <= i.  Returns the chunk's item count (after a barrier).
 constexpr int kChunkTiles = 512;
 __device__ __forceinline__ uint32_t chunk_number(const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
-                                                 uint32_t tile_slots, uint64_t c0, uint32_t* s_off, uint32_t* s_warp) {
+                                                 uint32_t tile_slots, uint32_t ct, uint64_t c0, uint32_t* s_off,
+                                                 uint32_t* s_warp) {
     constexpr int kPer = kChunkTiles / 256;
     uint32_t v[kPer], sum = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-        const uint64_t t = c0 + (uint64_t)threadIdx.x * kPer + k;
-        v[k] = t < n_tiles ? min(tile_cand[t], tile_slots) : 0u;
+        const uint32_t r = threadIdx.x * kPer + k;
+        const uint64_t t = c0 + r;
+        v[k] = r < ct && t < n_tiles ? min(tile_cand[t], tile_slots) : 0u;
         sum += v[k];
     }
     uint32_t total;
@@ -168,8 +170,9 @@ __device__ __forceinline__ uint32_t chunk_number(const uint32_t* __restrict__ ti
     return total;
 }
 
-__device__ __forceinline__ uint64_t chunk_slot(const uint32_t* s_off, uint64_t c0, uint32_t tile_slots, uint32_t i) {
-    uint32_t lo = 0, hi = kChunkTiles;
+__device__ __forceinline__ uint64_t chunk_slot(const uint32_t* s_off, uint64_t c0, uint32_t tile_slots, uint32_t ct,
+                                               uint32_t i) {
+    uint32_t lo = 0, hi = ct;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (s_off[mid] <= i) lo = mid; else hi = mid;
@@ -182,18 +185,18 @@ __device__ __forceinline__ uint64_t chunk_slot(const uint32_t* s_off, uint64_t c
 // item beyond kCountMaxPolys polygons, where they rarely collide).
 constexpr int kCountMaxPolys = 8192;
 __global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand,
-                                               uint64_t n_tiles, uint32_t tile_slots, uint32_t* __restrict__ poly_count,
-                                               uint32_t n_polys) {
+                                               uint64_t n_tiles, uint32_t tile_slots, uint32_t ct,
+                                               uint32_t* __restrict__ poly_count, uint32_t n_polys) {
     __shared__ uint32_t s_cnt[kCountMaxPolys];
     __shared__ uint32_t s_off[kChunkTiles];
     __shared__ uint32_t s_warp[8];
     const bool shared_counts = n_polys <= (uint32_t)kCountMaxPolys;
     if (shared_counts)
         for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) s_cnt[p] = 0;
-    for (uint64_t c0 = (uint64_t)blockIdx.x * kChunkTiles; c0 < n_tiles; c0 += (uint64_t)gridDim.x * kChunkTiles) {
-        const uint32_t total = chunk_number(tile_cand, n_tiles, tile_slots, c0, s_off, s_warp);
+    for (uint64_t c0 = (uint64_t)blockIdx.x * ct; c0 < n_tiles; c0 += (uint64_t)gridDim.x * ct) {
+        const uint32_t total = chunk_number(tile_cand, n_tiles, tile_slots, ct, c0, s_off, s_warp);
         for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-            const uint32_t poly = queue[chunk_slot(s_off, c0, tile_slots, i)].y;
+            const uint32_t poly = queue[chunk_slot(s_off, c0, tile_slots, ct, i)].y;
             if (shared_counts) atomicAdd(&s_cnt[poly], 1u);
             else atomicAdd(&poly_count[poly], 1u);
         }
@@ -213,20 +216,21 @@ __global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ queue, 
 // reserves its slot globally.
 constexpr int kScatterMaxPolys = 4096;
 __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand,
-                                                 uint64_t n_tiles, uint32_t tile_slots, uint32_t* __restrict__ cursor,
-                                                 uint2* __restrict__ sorted, uint32_t n_polys) {
+                                                 uint64_t n_tiles, uint32_t tile_slots, uint32_t ct,
+                                                 uint32_t* __restrict__ cursor, uint2* __restrict__ sorted,
+                                                 uint32_t n_polys) {
     __shared__ uint32_t s_cnt[kScatterMaxPolys];
     __shared__ uint32_t s_base[kScatterMaxPolys];
     __shared__ uint32_t s_off[kChunkTiles];
     __shared__ uint32_t s_warp[8];
     const bool shared_counts = n_polys <= (uint32_t)kScatterMaxPolys;
-    for (uint64_t c0 = (uint64_t)blockIdx.x * kChunkTiles; c0 < n_tiles; c0 += (uint64_t)gridDim.x * kChunkTiles) {
+    for (uint64_t c0 = (uint64_t)blockIdx.x * ct; c0 < n_tiles; c0 += (uint64_t)gridDim.x * ct) {
         if (shared_counts)
             for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) s_cnt[p] = 0;
-        const uint32_t total = chunk_number(tile_cand, n_tiles, tile_slots, c0, s_off, s_warp);
+        const uint32_t total = chunk_number(tile_cand, n_tiles, tile_slots, ct, c0, s_off, s_warp);
         if (shared_counts) {
             for (uint32_t i = threadIdx.x; i < total; i += blockDim.x)
-                atomicAdd(&s_cnt[queue[chunk_slot(s_off, c0, tile_slots, i)].y], 1u);
+                atomicAdd(&s_cnt[queue[chunk_slot(s_off, c0, tile_slots, ct, i)].y], 1u);
             __syncthreads();
             for (uint32_t p = threadIdx.x; p < n_polys; p += blockDim.x) {
                 const uint32_t c = s_cnt[p];
@@ -235,13 +239,13 @@ __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue
             }
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-                const uint64_t q = chunk_slot(s_off, c0, tile_slots, i);
+                const uint64_t q = chunk_slot(s_off, c0, tile_slots, ct, i);
                 const uint2 it = queue[q];
                 sorted[s_base[it.y] + atomicAdd(&s_cnt[it.y], 1u)] = make_uint2(it.x, (uint32_t)q);
             }
         } else {
             for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-                const uint64_t q = chunk_slot(s_off, c0, tile_slots, i);
+                const uint64_t q = chunk_slot(s_off, c0, tile_slots, ct, i);
                 const uint2 it = queue[q];
                 sorted[atomicAdd(&cursor[it.y], 1u)] = make_uint2(it.x, (uint32_t)q);
             }

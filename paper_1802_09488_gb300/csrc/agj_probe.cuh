@@ -21,7 +21,7 @@
 namespace agj {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-static __device__ const HilbertLut g_hilbert_lut = make_hilbert_lut();
+static __device__ __align__(16) const HilbertLut g_hilbert_lut = make_hilbert_lut();
 constexpr uint32_t kSpinLimit = 1u << 22;
 // Resident CTAs per SM the probe kernels are compiled for (a register cap:
 // 65536 / (256 x blocks) per thread).  The probe is latency-bound (dependent
@@ -146,29 +146,40 @@ __device__ __forceinline__ uint32_t next_byte(const uint16_t* lut, Walk& w) {
     return e >> 2;
 }
 
-// Cell id + face/prefix stage (§IV-B stage 1) for one point.  With the
-// index's fast model (and exact == false) the id comes from the certified FP32
-// path; otherwise from the FP64 spec.  Leaves w.st = 0 when the point joins
-// nothing, 1 when the walk can start at w.node, 2 when an uncertified level
-// decides the prefix.
-__device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* faces, const uint16_t* lut, double lat,
-                                           double lng, bool exact, Walk& w) {
+// Leaf cell of a point: face, (i, j) and the leading levels certified.
+struct PointIJ {
     uint32_t i, j;
     int lc, face;
+};
+
+// Cell id stage (§IV-B stage 1) for one point.  With the index's fast model
+// (and exact == false) the id comes from the certified FP32 path; otherwise
+// from the FP64 spec.  Returns false when the point lies in no cell (invalid,
+// or outside the fast model's window).
+__device__ __forceinline__ bool point_ij(const DevIndex& X, double lat, double lng, bool exact, PointIJ& p) {
+    if (!exact && X.model.enabled) {
+        if (!model_ij(X.model, lat, lng, &p.i, &p.j, &p.lc)) return false;   // outside the window: in no cell
+        p.face = X.model.face;
+        if (p.lc >= kLevels) p.lc = kLevels + 2;                            // exact id: padding levels too
+        return true;
+    }
+    if (!point_valid(lat, lng)) return false;
+    double u, v;
+    p.face = face_uv(lat, lng, &u, &v);
+    p.i = st_to_ij(uv_to_st(u));
+    p.j = st_to_ij(uv_to_st(v));
+    p.lc = kLevels + 2;
+    return true;
+}
+
+// Face/prefix stage (§IV-B stage 1) for one point's leaf cell.  Leaves
+// w.st = 0 when the point joins nothing, 1 when the walk can start at
+// w.node, 2 when an uncertified level decides the prefix.
+__device__ __forceinline__ void start_walk(const DevFace* faces, const uint16_t* lut, const PointIJ& p, Walk& w) {
+    const uint32_t i = p.i, j = p.j;
+    const int lc = p.lc, face = p.face;
     w.st = 0;
     w.b = 0;
-    if (!exact && X.model.enabled) {
-        if (!model_ij(X.model, lat, lng, &i, &j, &lc)) return;       // outside the window: in no cell
-        face = X.model.face;
-        if (lc >= kLevels) lc = kLevels + 2;                        // exact id: padding levels too
-    } else {
-        if (!point_valid(lat, lng)) return;
-        double u, v;
-        face = face_uv(lat, lng, &u, &v);
-        i = st_to_ij(uv_to_st(u));
-        j = st_to_ij(uv_to_st(v));
-        lc = kLevels + 2;
-    }
     const DevFace fr = faces[face];
     if (fr.root == kNoRootDev) return;
     w.i32 = i << 2;
@@ -189,26 +200,27 @@ __device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* fac
     w.st = 1;
 }
 
-// Walks of PPT points advance level by level together, so their gathers
-// (Listing "Probe Adaptive Cell Trie") are in flight at the same time.
-// Points whose walk needs an uncertified key byte get their FP64 id and walk
-// again alone (counted in *fallbacks); they reload their coordinates from
-// pts[32 k] (the lane's points), so lat/lng need no registers during the
-// walk.  Returns the trie entries read.
+__device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* faces, const uint16_t* lut, double lat,
+                                           double lng, bool exact, Walk& w) {
+    PointIJ p;
+    w.st = 0;
+    w.b = 0;
+    if (point_ij(X, lat, lng, exact, p)) start_walk(faces, lut, p, w);
+}
+
+// Walks of PPT points (w, after their face/prefix stage) advance level by
+// level together, so their gathers (Listing "Probe Adaptive Cell Trie") are
+// in flight at the same time.  Points whose walk needs an uncertified key
+// byte get their FP64 id and walk again alone (counted in *fallbacks); they
+// reload their coordinates from pts[32 k] (the lane's points), so lat/lng
+// need no registers during the walk.  Returns the trie entries read.
 template <int PPT>
-__device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
-                                                 const uint64_t* s_root, const double* lat, const double* lng,
-                                                 const double2* pts, const bool* valid, uint64_t e[PPT],
-                                                 uint64_t* err, uint32_t* fallbacks) {
+__device__ __forceinline__ uint32_t walk_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
+                                                const uint64_t* s_root, Walk* w, const double2* pts, uint64_t e[PPT],
+                                                uint64_t* err, uint32_t* fallbacks) {
     uint32_t gathers = 0;
-    Walk w[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        e[k] = 0;
-        w[k].st = 0;
-        w[k].b = 0;
-        if (valid[k]) begin_walk(X, faces, lut, lat[k], lng[k], false, w[k]);
-    }
+    for (int k = 0; k < PPT; ++k) e[k] = 0;
     uint32_t prefix_bytes[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) prefix_bytes[k] = w[k].b;
@@ -298,12 +310,45 @@ __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFac
     return gathers;
 }
 
-// Adds two per-thread counts (a < 2^15, b < 2^11 per thread) to two device
-// counters with one warp reduction and at most two atomics per warp.
-__device__ __forceinline__ void warp_count2(uint32_t a, uint32_t b, uint64_t* ca, uint64_t* cb) {
-    uint32_t v = a | (b << 20);
+// The probe of PPT points from their leaf cells (ok[k] false: point k is in
+// no cell).
+template <int PPT>
+__device__ __forceinline__ uint32_t probe_cells(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
+                                                const uint64_t* s_root, const PointIJ* p, const bool* ok,
+                                                const double2* pts, uint64_t e[PPT], uint64_t* err,
+                                                uint32_t* fallbacks) {
+    Walk w[PPT];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    for (int k = 0; k < PPT; ++k) {
+        w[k].st = 0;
+        w[k].b = 0;
+        if (ok[k]) start_walk(faces, lut, p[k], w[k]);
+    }
+    return walk_points<PPT>(X, faces, lut, s_root, w, pts, e, err, fallbacks);
+}
+
+// The probe of PPT points from their coordinates (valid[k] false: padding
+// lane), cell id and face/prefix stage point by point.
+template <int PPT>
+__device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
+                                                 const uint64_t* s_root, const double* lat, const double* lng,
+                                                 const double2* pts, const bool* valid, uint64_t e[PPT],
+                                                 uint64_t* err, uint32_t* fallbacks) {
+    Walk w[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        w[k].st = 0;
+        w[k].b = 0;
+        if (valid[k]) begin_walk(X, faces, lut, lat[k], lng[k], false, w[k]);
+    }
+    return walk_points<PPT>(X, faces, lut, s_root, w, pts, e, err, fallbacks);
+}
+
+// Adds two per-thread counts (a < 2^15, b < 2^7 per thread) to two device
+// counters with one warp reduction (a single redux instruction) and at most
+// two atomics per warp.
+__device__ __forceinline__ void warp_count2(uint32_t a, uint32_t b, uint64_t* ca, uint64_t* cb) {
+    const uint32_t v = __reduce_add_sync(kFull, a | (b << 20));
     if ((threadIdx.x & 31) == 0) {
         if (v & 0xFFFFFu) atomicAdd((unsigned long long*)ca, (unsigned long long)(v & 0xFFFFFu));
         if (v >> 20) atomicAdd((unsigned long long*)cb, (unsigned long long)(v >> 20));
@@ -312,8 +357,7 @@ __device__ __forceinline__ void warp_count2(uint32_t a, uint32_t b, uint64_t* ca
 
 // Adds a per-thread count to a device counter with one atomic per warp.
 __device__ __forceinline__ void warp_count(uint32_t v, uint64_t* counter) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    v = __reduce_add_sync(kFull, v);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long*)counter, (unsigned long long)v);
 }
 
@@ -343,6 +387,33 @@ __device__ __forceinline__ const uint64_t* cta_setup(const DevIndex* X, uint16_t
     const ulonglong2* src = reinterpret_cast<const ulonglong2*>(X->nodes + (uint64_t)root * 256);
     for (int t = threadIdx.x; t < 128; t += blockDim.x) reinterpret_cast<ulonglong2*>(s_root)[t] = __ldg(src + t);
     return s_root;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// cta_setup for one index without the wait: the Hilbert table and the model
+// face's root node go to shared memory as asynchronous 16-byte copies (one
+// per thread of the 256), so the CTA computes its points' cell ids while
+// they land; the face table is stored directly.  Every thread must call
+// cp_async_wait_all and then __syncthreads before reading any of the three.
+// Returns the shared root (or null).
+__device__ __forceinline__ const uint64_t* cta_setup_async(const DevIndex& X, uint16_t* s_hlut, DevFace* s_faces,
+                                                           uint64_t* s_root) {
+    static_assert(kJoinBlock == 256, "one 16-byte copy per thread: 128 for the table, 128 for the root");
+    const uint32_t t = threadIdx.x;
+    if (t < 128) cp_async16(s_hlut + 8 * t, g_hilbert_lut.v + 8 * t);
+    const uint32_t root = X.model.enabled ? X.faces[X.model.face].root : kNoRootDev;
+    if (root != kNoRootDev && t >= 128) cp_async16(s_root + 2 * (t - 128), X.nodes + (uint64_t)root * 256 + 2 * (t - 128));
+    cp_async_commit();
+    if (t < 6) s_faces[t] = X.faces[t];
+    return root != kNoRootDev ? s_root : nullptr;
 }
 
 __device__ __forceinline__ uint32_t payload_of(uint64_t e, int which) {
@@ -437,11 +508,16 @@ struct OneJob {
     __device__ __forceinline__ uint32_t job_base(uint32_t) const { return 0; }
 };
 
-// The batched form: m jobs in device memory, laid end to end.
+// The batched form: m jobs in device memory, laid end to end, the
+// approximate jobs' tiles first.  A probe or emit launch covers the tiles
+// t0 .. T - 1 of one mode (t0 a multiple of the CTA's 8 tiles); ta is where
+// the exact jobs' tiles begin.
 struct ManyJobs {
     const JobDesc* d;
     const uint16_t* tile_job; // job of each global tile
     const uint32_t* base;     // per job: tile prefix (mod 2^32) at its first tile, written by the scan
+    uint64_t t0;
+    uint64_t ta;
     uint32_t m;
     static constexpr bool kSingle = false;
     __device__ __forceinline__ uint32_t find_tile(uint64_t wt) const { return __ldg(tile_job + wt); }
@@ -449,8 +525,10 @@ struct ManyJobs {
     __device__ __forceinline__ uint32_t job_base(uint32_t j) const { return base[j]; }
 };
 
-// Join mode of a kernel instance: fixed, or read from each job (batched form).
-enum : int { kModeApprox = 0, kModeExact = 1, kModeAny = 2 };
+// Join mode of a kernel instance: fixed, or read from each job (batched
+// form); kModeSplit (batched form, launch sequence only): approximate kernels
+// over the tiles before ManyJobs::ta, exact ones after.
+enum : int { kModeApprox = 0, kModeExact = 1, kModeAny = 2, kModeSplit = 3 };
 
 template <int MODE>
 __device__ __forceinline__ bool job_exact(const JobDesc& J) {
@@ -528,27 +606,51 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
 // the tile; exact jobs count the true hits and queue the candidate
 // references (warp ballot: one atomic reserves a warp's queue slots).  No
 // tile waits on another.
-template <int PPT, int MODE>
+// With kAsync the CTA's shared tables are still in flight (cta_setup_async):
+// every thread of the CTA calls this (active false: a warp past the last
+// tile), and the wait and barrier come after the cell ids, before the first
+// table read.
+template <int PPT, int MODE, bool kAsync = false>
 __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
                                            const uint64_t* s_root, uint64_t wt, uint64_t lt, uint32_t gpoly0,
-                                           const JoinScratch& S) {
+                                           const JoinScratch& S, bool active = true) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t base = lt * (32 * PPT);
     const uint64_t gbase = wt * (32 * PPT);
-    double lat[PPT], lng[PPT];
-    bool valid[PPT];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const uint64_t p = base + lane + 32 * k;
-        valid[k] = p < J.n;
-        const double2 q = valid[k] ? __ldcs(J.pts + p) : make_double2(0.0, 0.0);   // streamed once
-        lat[k] = q.x;
-        lng[k] = q.y;
-    }
     uint64_t e[PPT];
     uint32_t fallbacks = 0;
-    const uint32_t gathers =
-        probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, J.pts + base + lane, valid, e, &J.status[1], &fallbacks);
+    uint32_t gathers;
+    if constexpr (kAsync) {
+        PointIJ pij[PPT];
+        bool ok[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const uint64_t p = base + lane + 32 * k;
+            ok[k] = false;
+            if (active && p < J.n) {
+                const double2 q = __ldcs(J.pts + p);     // streamed once
+                ok[k] = point_ij(J.X, q.x, q.y, false, pij[k]);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (!active) return;
+        gathers = probe_cells<PPT>(J.X, faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1],
+                                   &fallbacks);
+    } else {
+        double lat[PPT], lng[PPT];
+        bool valid[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const uint64_t p = base + lane + 32 * k;
+            valid[k] = p < J.n;
+            const double2 q = valid[k] ? __ldcs(J.pts + p) : make_double2(0.0, 0.0);   // streamed once
+            lat[k] = q.x;
+            lng[k] = q.y;
+        }
+        gathers = probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, J.pts + base + lane, valid, e,
+                                    &J.status[1], &fallbacks);
+    }
     warp_count2(gathers, fallbacks, &J.status[3], &J.counters[0]);
     const bool exact = job_exact<MODE>(J);
     uint32_t nc[PPT], csum = 0, tsum = 0;
@@ -560,11 +662,13 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
         csum += exact ? nc[k] : 0u;
         S.entries[gbase + lane + 32 * k] = e[k];        // 0 for padding lanes
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(kFull, tsum, o);
+    tsum = __reduce_add_sync(kFull, tsum);
     if (lane == 0) S.tile_count[wt] = tsum;
-    if constexpr (MODE != kModeApprox)
+    if constexpr (MODE != kModeApprox) {
         if (S.tile_cand) queue_tile<PPT>(J, e, nc, csum, wt, gbase, gpoly0, S);
+    } else {
+        if (S.tile_cand && lane == 0) S.tile_cand[wt] = 0;      // a batched plan's approximate tile
+    }
 }
 
 // Stages job J's face table and (with the fast model) the model face's root
@@ -589,35 +693,36 @@ __device__ __forceinline__ const uint64_t* cta_stage_job(const JobDesc& J, DevFa
 // compile-time zero).  The batched form aligns every job's tile range to
 // whole CTAs, so the 8 tiles a CTA takes at a time belong to one job, whose
 // face table and root node the CTA stages in shared memory when the job
-// changes; the grid either covers the tile space (one warp per tile) or is
-// persistent and strides over it.
-template <int PPT, class Src, int MODE>
-__global__ void __launch_bounds__(kJoinBlock, !Src::kSingle ? AGJ_BATCH_PROBE_MIN_BLOCKS
-                                                 : MODE == kModeApprox ? AGJ_APPROX_PROBE_MIN_BLOCKS
-                                                                       : AGJ_PROBE_MIN_BLOCKS)
+// changes; the grid either covers the tile space (one warp per tile) or, with
+// kPersist, is persistent and strides over it (separate instances, so the
+// one-warp-per-tile form carries no loop state).
+template <int PPT, class Src, int MODE, bool kPersist = false>
+__global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_PROBE_MIN_BLOCKS
+                                             : !Src::kSingle          ? AGJ_BATCH_PROBE_MIN_BLOCKS
+                                                                      : AGJ_PROBE_MIN_BLOCKS)
     k_probe(const Src src, uint64_t T, const JoinScratch S) {
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
     const uint32_t warp = threadIdx.x >> 5;
     if constexpr (Src::kSingle) {
-        const uint64_t* s_root = cta_setup(&src.job(0).X, s_hlut, s_faces, s_rootbuf);
-        __syncthreads();
+        const uint64_t* s_root = cta_setup_async(src.job(0).X, s_hlut, s_faces, s_rootbuf);
         const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
-        if (wt < T) probe_tile<PPT, MODE>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S);
+        probe_tile<PPT, MODE, true>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S, wt < T);
     } else {
-        cta_setup(nullptr, s_hlut, s_faces, s_rootbuf);
-        if ((uint64_t)gridDim.x * kWarpsPerBlock >= T) {            // one CTA per 8 tiles
-            const uint64_t g = blockIdx.x;
+        const uint64_t g0 = src.t0 / kWarpsPerBlock;
+        if constexpr (!kPersist) {                                  // one CTA per 8 tiles of one job
+            const uint64_t g = g0 + blockIdx.x;
             if (g * kWarpsPerBlock >= T) return;
             const JobDesc& J = src.job(src.find_tile(g * kWarpsPerBlock));
-            const uint64_t* s_root = cta_stage_job(J, s_faces, s_rootbuf);
+            const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
             const uint64_t wt = g * kWarpsPerBlock + warp;
-            probe_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S);
+            probe_tile<PPT, MODE, true>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S);
         } else {                                                    // persistent grid
+            cta_setup(nullptr, s_hlut, s_faces, s_rootbuf);
             uint32_t cur = 0xFFFFFFFFu;
             const uint64_t* s_root = nullptr;
-            for (uint64_t g = blockIdx.x; g * kWarpsPerBlock < T; g += gridDim.x) {
+            for (uint64_t g = g0 + blockIdx.x; g * kWarpsPerBlock < T; g += gridDim.x) {
                 const uint32_t j = src.find_tile(g * kWarpsPerBlock);
                 const JobDesc& J = src.job(j);
                 if (j != cur) {
@@ -654,15 +759,25 @@ __global__ void k_poly_scan(const uint32_t* __restrict__ poly_count, uint32_t n_
                             uint32_t* __restrict__ chunk_counter, uint64_t* __restrict__ err);
 
 // Candidates per polygon of the queue (tile_cand[t] items from slot
-// t x tile_slots of each tile t).
+// t x tile_slots of each tile t), taken in chunks of chunk_tiles tiles
+// (a power of two, 32 .. 512).
 __global__ void k_count(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
-                        uint32_t tile_slots, uint32_t* __restrict__ poly_count, uint32_t n_polys);
+                        uint32_t tile_slots, uint32_t chunk_tiles, uint32_t* __restrict__ poly_count,
+                        uint32_t n_polys);
 
 // Groups the queued candidates by polygon: a counting-sort scatter of
-// (global point, queue slot) pairs.
+// (global point, queue slot) pairs, same chunks as k_count.
 __global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __restrict__ tile_cand, uint64_t n_tiles,
-                          uint32_t tile_slots, uint32_t* __restrict__ cursor, uint2* __restrict__ sorted,
-                          uint32_t n_polys);
+                          uint32_t tile_slots, uint32_t chunk_tiles, uint32_t* __restrict__ cursor,
+                          uint2* __restrict__ sorted, uint32_t n_polys);
+
+// Tiles per chunk of k_count / k_scatter: 512 for large queues, smaller ones
+// split so that about four chunks per SM share the work.
+inline uint32_t refine_chunk_tiles(uint64_t n_tiles, int sms) {
+    uint32_t ct = 32;
+    while (ct < 512 && (uint64_t)ct * 4 * (uint64_t)sms < n_tiles) ct <<= 1;
+    return ct;
+}
 
 // Refine (Listing "Join" step 3 on candidate references): ST_Covers of
 // (point, polygon) candidates, grouped by polygon.  Per chunk of one
@@ -873,10 +988,14 @@ __global__ void __launch_bounds__(kJoinBlock) k_emit(const Src src, uint64_t T, 
     uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if constexpr (Src::kSingle) {
         if (wt < T) emit_tile<PPT, MODE>(src, 0, wt, S, s_pass);
-    } else if ((uint64_t)gridDim.x * kWarpsPerBlock >= T) {     // one warp per tile
-        if (wt < T) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S, s_pass);
-    } else {                                                     // persistent grid
-        for (; wt < T; wt += (uint64_t)gridDim.x * kWarpsPerBlock) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S, s_pass);
+    } else {
+        wt += src.t0;
+        if ((uint64_t)gridDim.x * kWarpsPerBlock >= T - src.t0) {   // one warp per tile
+            if (wt < T) emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S, s_pass);
+        } else {                                                     // persistent grid
+            for (; wt < T; wt += (uint64_t)gridDim.x * kWarpsPerBlock)
+                emit_tile<PPT, MODE>(src, src.find_tile(wt), wt, S, s_pass);
+        }
     }
 }
 

@@ -139,3 +139,48 @@ def test_batch_single_mode_plans(torch, agj, jobs, indexes, expected, which):
         torch.cuda.synchronize()
         _check(pr, [expected[j] for j in sel])
         b.close()
+
+
+@pytest.fixture(scope="module")
+def big_jobs(agj):
+    """Two city-scale jobs (one approximate, one exact, 3.2e6 points each):
+    enough tiles that a mixed plan launches each mode's probe and emit on
+    its own."""
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c2_city_polygons()
+    pts = synth.points_mixture(6_400_000, synth.BOX_CITY, seed=21, dist_seed=3)
+    train = synth.points_mixture(100_000, synth.BOX_CITY, seed=22, dist_seed=3)
+    ia = agj.Index(polys, agj.APPROX, 4.0)
+    ie = agj.Index(polys, agj.EXACT, 0, train=train)
+    return polys, [(ia, pts[:3_200_000]), (ie, pts[3_200_000:])]
+
+
+@pytest.mark.parametrize("ppt,ctas", [(2, 0), (1, 3)])
+def test_batch_mode_split_launches(torch, agj, oracle, jobs, indexes, expected, big_jobs, ppt, ctas):
+    """A mixed plan over 1e5+ tiles (approximate and exact probes and emits
+    as separate launches, one warp per tile and persistent): every job equals
+    its plain join, and sampled rows of the big jobs equal the oracle."""
+    polys, big = big_jobs
+    ix = [b[0] for b in big] + indexes
+    pts = [b[1] for b in big] + [jb.points for jb in jobs]
+    b = agj.Batch(ix, [len(p) for p in pts], points_per_lane=ppt, ctas_per_sm=ctas)
+    pr = b.run([_dev(torch, p) for p in pts], b.pairs())
+    torch.cuda.synchronize()
+    _check(pr[2:], expected)
+    rng = np.random.default_rng(5)
+    ps = oracle.PolySet(polys)
+    for k, (index, p) in enumerate(big):
+        plain = agj.join(index, _dev(torch, p))
+        off, ids = plain.to_host()
+        got_off, got_ids = pr[k].to_host()
+        assert np.array_equal(got_off, off) and np.array_equal(got_ids, ids), k
+        assert np.array_equal(pr[k].status.cpu().numpy(), plain.status.cpu().numpy()), k
+        rows = np.sort(rng.choice(len(p), 2000, replace=False))
+        if k == 1:
+            eo, ei = ps.join_exact(p[rows])
+        else:
+            cells, ro, refs = index.logical()
+            eo, ei = oracle.join_approx_logical(cells, ro, refs, p[rows])
+        for r, row in enumerate(rows):
+            assert list(ids[off[row]:off[row + 1]]) == list(ei[eo[r]:eo[r + 1]]), (k, row)
+    b.close()
