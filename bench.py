@@ -40,7 +40,7 @@ LAUNCHES_PER_STEP = {"approx": 4, "exact": 8}
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the points); a full
 # launch's traffic scales with its points (the trie gathers per point do not
 # depend on n).  Must be re-captured whenever a probe kernel changes.
-PROBE_DRAM_BYTES_PER_POINT = {"k_probe_approx": 25.01, "k_probe_exact": 25.15}
+PROBE_DRAM_BYTES_PER_POINT = {"k_probe_approx": 24.93, "k_probe_exact": 25.22}
 
 
 def parse():
