@@ -159,8 +159,15 @@ int fill_jobs(const Shape& S, const Index* const* X, const uint64_t* n, const do
     return AGJ_OK;
 }
 
+// An auxiliary stream and fork/join events: where the two modes' chains of a
+// large mixed launch may run side by side (a captured graph's branches).
+struct Aux {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 template <int PPT>
-cudaError_t enqueue_kernels(const Shape& S, char* base, int ctas_per_sm, cudaStream_t s) {
+cudaError_t enqueue_kernels(const Shape& S, char* base, int ctas_per_sm, cudaStream_t s, const Aux* aux) {
     ManyJobs src;
     src.d = reinterpret_cast<const JobDesc*>(base + S.off_jobs);
     src.tile_job = reinterpret_cast<const uint16_t*>(base + S.off_tile_job);
@@ -184,10 +191,11 @@ cudaError_t enqueue_kernels(const Shape& S, char* base, int ctas_per_sm, cudaStr
     G.job_base = reinterpret_cast<uint32_t*>(base + S.off_job_base);
     char* sc = base + S.off_scratch;
     // One mode: that mode's kernels.  Both, over many tiles (16 waves and
-    // more, ~6e6 points): each mode's probe and emit as their own launches
-    // (the approximate ones at 6 CTAs per SM, no per-job mode branches); over
-    // fewer (a served step) the two extra launches cost more than they save,
-    // so one launch reads each job's mode.
+    // more, ~6e6 points): each mode's chain of kernels on its own tiles (the
+    // approximate probe at 6 CTAs per SM, no per-job mode branches, the
+    // chains side by side where an auxiliary stream is given); over fewer (a
+    // served step) the extra launches cost more than they save, so one
+    // launch reads each job's mode.
     const uint64_t split_min = (uint64_t)G.sms * AGJ_PROBE_MIN_BLOCKS * kWarpsPerBlock * 16;
     if (S.Ta == S.T || S.Ta == 0 || S.T < split_min) {
         grids(S.T, &G.probe_grid, &G.emit_grid);
@@ -197,14 +205,15 @@ cudaError_t enqueue_kernels(const Shape& S, char* base, int ctas_per_sm, cudaStr
     }
     grids(S.Ta, &G.probe_grid_a, &G.emit_grid_a);
     grids(S.T - S.Ta, &G.probe_grid, &G.emit_grid);
-    return enqueue_join<PPT, ManyJobs, kModeSplit>(src, S.L, sc, G, nullptr, 0, s, nullptr);
+    return enqueue_join_split<PPT>(src, S.L, sc, G, s, aux ? aux->stream : nullptr, aux ? aux->fork : nullptr,
+                                   aux ? aux->join : nullptr);
 }
 
-cudaError_t enqueue(const Shape& S, char* base, int ctas_per_sm, cudaStream_t s) {
+cudaError_t enqueue(const Shape& S, char* base, int ctas_per_sm, cudaStream_t s, const Aux* aux = nullptr) {
     switch (S.ppt) {
-        case 1: return enqueue_kernels<1>(S, base, ctas_per_sm, s);
-        case 4: return enqueue_kernels<4>(S, base, ctas_per_sm, s);
-        default: return enqueue_kernels<2>(S, base, ctas_per_sm, s);
+        case 1: return enqueue_kernels<1>(S, base, ctas_per_sm, s, aux);
+        case 4: return enqueue_kernels<4>(S, base, ctas_per_sm, s, aux);
+        default: return enqueue_kernels<2>(S, base, ctas_per_sm, s, aux);
     }
 }
 
@@ -233,6 +242,7 @@ struct Batch {
     bool uploaded = false;
     cudaEvent_t upload_done = nullptr;
     cudaStream_t cap_stream = nullptr;
+    Aux cap_aux;                        // second branch of the captured graph
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -240,6 +250,9 @@ void batch_free(Batch* B) {
     if (!B) return;
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+    if (B->cap_aux.stream) cudaStreamDestroy(B->cap_aux.stream);
+    if (B->cap_aux.fork) cudaEventDestroy(B->cap_aux.fork);
+    if (B->cap_aux.join) cudaEventDestroy(B->cap_aux.join);
     if (B->upload_done) cudaEventDestroy(B->upload_done);
     if (B->h_jobs) cudaFreeHost(B->h_jobs);
     if (B->d_mem) cudaFree(B->d_mem);
@@ -285,10 +298,17 @@ int batch_create(const Index* const* X, const uint64_t* n, uint32_t m, int ppt, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(B->cap_stream);
     if (e != cudaSuccess) { cudaGetLastError(); batch_free(B); return AGJ_ECUDA; }
     if (use_graph && m) {
+        if (cudaStreamCreateWithFlags(&B->cap_aux.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->cap_aux.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->cap_aux.join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            batch_free(B);
+            return AGJ_ECUDA;
+        }
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t e1 = enqueue(S, B->d_mem, ctas_per_sm, B->cap_stream);
+            const cudaError_t e1 = enqueue(S, B->d_mem, ctas_per_sm, B->cap_stream, &B->cap_aux);
             e = cudaStreamEndCapture(B->cap_stream, &g);
             if (e1 != cudaSuccess) e = e1;
         }

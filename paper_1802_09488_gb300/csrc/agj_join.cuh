@@ -59,7 +59,7 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
     L.n_chunks = (n_tiles + 256 * kScanItems - 1) / (256 * kScanItems);
     uint64_t o = 256;
     L.chunks = o;
-    o += align256(std::max<uint64_t>(L.n_chunks, 1) * 8);
+    o += align256((L.n_chunks + 1) * 8);        // + 1: the batched form scans its two modes' tiles apart
     if (exact) {
         L.n_polys = n_polys;
         L.tile_slots = tile_slots;
@@ -102,10 +102,10 @@ inline JoinScratch join_scratch(const JoinLayout& L, char* sc) {
 }
 
 struct JoinLaunch {
-    int probe_grid = 0;       // CTAs of the probe kernel (kModeSplit: of the exact tiles' probe)
-    int emit_grid = 0;        // CTAs of the emit kernel (kModeSplit: of the exact tiles' emit)
-    int probe_grid_a = 0;     // kModeSplit: CTAs of the approximate tiles' probe
-    int emit_grid_a = 0;      // kModeSplit: CTAs of the approximate tiles' emit
+    int probe_grid = 0;       // CTAs of the probe kernel (split form: of the exact tiles' probe)
+    int emit_grid = 0;        // CTAs of the emit kernel (split form: of the exact tiles' emit)
+    int probe_grid_a = 0;     // split form: CTAs of the approximate tiles' probe
+    int emit_grid_a = 0;      // split form: CTAs of the approximate tiles' emit
     int sms = 1;              // for the grid-stride kernels
     bool persistent = false;  // batched form: probe grids smaller than the tile space stride over it
     int pip_grid = 0;
@@ -131,30 +131,15 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
         k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint64_t*>(sc), zero_words, extra_zero, n_extra);
     }
     mark(0);
-    if constexpr (MODE == kModeSplit) {
-        // the batched form's approximate tiles, then its exact ones
-        Src a = src, x = src;
-        a.t0 = 0;
-        x.t0 = src.ta;
-        if (G.persistent) {
-            if (src.ta) k_probe<PPT, Src, kModeApprox, true><<<G.probe_grid_a, kJoinBlock, 0, s>>>(a, src.ta, S);
-            if (L.n_tiles > src.ta)
-                k_probe<PPT, Src, kModeExact, true><<<G.probe_grid, kJoinBlock, 0, s>>>(x, L.n_tiles, S);
-        } else {
-            if (src.ta) k_probe<PPT, Src, kModeApprox><<<G.probe_grid_a, kJoinBlock, 0, s>>>(a, src.ta, S);
-            if (L.n_tiles > src.ta) k_probe<PPT, Src, kModeExact><<<G.probe_grid, kJoinBlock, 0, s>>>(x, L.n_tiles, S);
-        }
-    } else {
-        if (L.n_tiles) {
-            if constexpr (!Src::kSingle) {
-                if (G.persistent) {
-                    k_probe<PPT, Src, MODE, true><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
-                } else {
-                    k_probe<PPT, Src, MODE><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
-                }
+    if (L.n_tiles) {
+        if constexpr (!Src::kSingle) {
+            if (G.persistent) {
+                k_probe<PPT, Src, MODE, true><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
             } else {
                 k_probe<PPT, Src, MODE><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
             }
+        } else {
+            k_probe<PPT, Src, MODE><<<G.probe_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
         }
     }
     mark(1);
@@ -189,16 +174,80 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
                                                                reinterpret_cast<uint64_t*>(sc) + kHdrScanErr,
                                                                G.tile_job, G.job_base);
     }
-    if constexpr (MODE == kModeSplit) {
-        Src a = src, x = src;
-        a.t0 = 0;
-        x.t0 = src.ta;
-        if (src.ta) k_emit<PPT, Src, kModeApprox><<<G.emit_grid_a, kJoinBlock, 0, s>>>(a, src.ta, S);
-        if (L.n_tiles > src.ta) k_emit<PPT, Src, kModeExact><<<G.emit_grid, kJoinBlock, 0, s>>>(x, L.n_tiles, S);
-    } else {
-        if (L.n_tiles) k_emit<PPT, Src, MODE><<<G.emit_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
-    }
+    if (L.n_tiles) k_emit<PPT, Src, MODE><<<G.emit_grid, kJoinBlock, 0, s>>>(src, L.n_tiles, S);
     mark(3);
+    return cudaGetLastError();
+}
+
+// The batched form with both modes over many tiles: the approximate tiles
+// (0 .. src.ta - 1) and the exact ones (src.ta .. n_tiles - 1) run as two
+// independent chains, each with its own probe, scan and emit compiled for
+// its mode, the exact one with the refine over its tiles only.  The chains
+// share no work space (disjoint tiles, points, queue regions, scan states and
+// tickets), so with an auxiliary stream (s_aux, fork and join events) the
+// approximate chain runs beside the exact one, e.g. as a parallel branch of
+// a captured graph; without one, both run on s in turn.
+template <int PPT>
+cudaError_t enqueue_join_split(const ManyJobs& src, const JoinLayout& L, char* sc, const JoinLaunch& G,
+                               cudaStream_t s, cudaStream_t s_aux, cudaEvent_t fork, cudaEvent_t join) {
+    const JoinScratch S = join_scratch(L, sc);
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(sc);
+    uint64_t* err = reinterpret_cast<uint64_t*>(sc) + kHdrScanErr;
+    uint64_t* chunks = reinterpret_cast<uint64_t*>(sc + L.chunks);
+    const uint64_t ta = src.ta, T = L.n_tiles;
+    {
+        const uint64_t zero_words = L.zero_end / 8;
+        const int grid = (int)std::min<uint64_t>((zero_words + 255) / 256 + 1, (uint64_t)G.sms * 4);
+        k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint64_t*>(sc), zero_words, nullptr, 0);
+    }
+    cudaStream_t sa = s;
+    if (s_aux) {
+        if (cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(s_aux, fork, 0) != cudaSuccess)
+            return cudaGetLastError();
+        sa = s_aux;
+    }
+    const uint64_t per_chunk = 256 * kScanItems;
+    const uint64_t na = (ta + per_chunk - 1) / per_chunk, ne = (T - ta + per_chunk - 1) / per_chunk;
+    // approximate chain: tiles 0 .. ta - 1, scan ticket hdr[0], chunk states 0 .. na - 1
+    {
+        ManyJobs a = src;
+        a.t0 = 0;
+        if (G.persistent) k_probe<PPT, ManyJobs, kModeApprox, true><<<G.probe_grid_a, kJoinBlock, 0, sa>>>(a, ta, S);
+        else k_probe<PPT, ManyJobs, kModeApprox><<<G.probe_grid_a, kJoinBlock, 0, sa>>>(a, ta, S);
+        k_scan_counts<<<(unsigned)na, 256, 0, sa>>>(S.tile_count, ta, S.tile_prefix, chunks, hdr, err, G.tile_job,
+                                                    G.job_base);
+        k_emit<PPT, ManyJobs, kModeApprox><<<G.emit_grid_a, kJoinBlock, 0, sa>>>(a, ta, S);
+    }
+    // exact chain: tiles ta .. T - 1, scan ticket hdr[1], chunk states na .. na + ne - 1
+    {
+        ManyJobs x = src;
+        x.t0 = ta;
+        if (G.persistent) k_probe<PPT, ManyJobs, kModeExact, true><<<G.probe_grid, kJoinBlock, 0, s>>>(x, T, S);
+        else k_probe<PPT, ManyJobs, kModeExact><<<G.probe_grid, kJoinBlock, 0, s>>>(x, T, S);
+        if (L.n_polys) {
+            // the refine over the exact tiles' queue regions (slots relative to tile ta)
+            const uint64_t q0 = ta * L.tile_slots;
+            const uint32_t ct = refine_chunk_tiles(T - ta, G.sms);
+            k_count<<<G.sms * 2, 256, 0, s>>>(S.queue + q0, S.tile_cand + ta, T - ta, L.tile_slots, ct, S.poly_count,
+                                              (uint32_t)L.n_polys);
+            k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
+                S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.cursor), hdr + 2,
+                reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3, err);
+            k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue + q0, S.tile_cand + ta, T - ta, L.tile_slots, ct,
+                                                reinterpret_cast<uint32_t*>(sc + L.cursor),
+                                                reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
+            k_pip<ManyJobs><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, reinterpret_cast<const uint2*>(sc + L.sorted),
+                                                            reinterpret_cast<const uint4*>(sc + L.cpoly), hdr + 2,
+                                                            S.pass + q0, S.tile_count);
+        }
+        k_scan_counts<<<(unsigned)ne, 256, 0, s>>>(S.tile_count + ta, T - ta, S.tile_prefix + ta, chunks + na, hdr + 1,
+                                                   err, G.tile_job + ta, G.job_base);
+        k_emit<PPT, ManyJobs, kModeExact><<<G.emit_grid, kJoinBlock, 0, s>>>(x, T, S);
+    }
+    if (s_aux) {
+        if (cudaEventRecord(join, s_aux) != cudaSuccess || cudaStreamWaitEvent(s, join, 0) != cudaSuccess)
+            return cudaGetLastError();
+    }
     return cudaGetLastError();
 }
 

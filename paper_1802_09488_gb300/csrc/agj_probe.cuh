@@ -156,10 +156,10 @@ struct PointIJ {
 // (and exact == false) the id comes from the certified FP32 path; otherwise
 // from the FP64 spec.  Returns false when the point lies in no cell (invalid,
 // or outside the fast model's window).
-__device__ __forceinline__ bool point_ij(const DevIndex& X, double lat, double lng, bool exact, PointIJ& p) {
-    if (!exact && X.model.enabled) {
-        if (!model_ij(X.model, lat, lng, &p.i, &p.j, &p.lc)) return false;   // outside the window: in no cell
-        p.face = X.model.face;
+__device__ __forceinline__ bool point_ij(const FastModel& M, double lat, double lng, bool exact, PointIJ& p) {
+    if (!exact && M.enabled) {
+        if (!model_ij(M, lat, lng, &p.i, &p.j, &p.lc)) return false;   // outside the window: in no cell
+        p.face = M.face;
         if (p.lc >= kLevels) p.lc = kLevels + 2;                            // exact id: padding levels too
         return true;
     }
@@ -205,7 +205,7 @@ __device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* fac
     PointIJ p;
     w.st = 0;
     w.b = 0;
-    if (point_ij(X, lat, lng, exact, p)) start_walk(faces, lut, p, w);
+    if (point_ij(X.model, lat, lng, exact, p)) start_walk(faces, lut, p, w);
 }
 
 // Walks of PPT points (w, after their face/prefix stage) advance level by
@@ -525,10 +525,8 @@ struct ManyJobs {
     __device__ __forceinline__ uint32_t job_base(uint32_t j) const { return base[j]; }
 };
 
-// Join mode of a kernel instance: fixed, or read from each job (batched
-// form); kModeSplit (batched form, launch sequence only): approximate kernels
-// over the tiles before ManyJobs::ta, exact ones after.
-enum : int { kModeApprox = 0, kModeExact = 1, kModeAny = 2, kModeSplit = 3 };
+// Join mode of a kernel instance: fixed, or read from each job (batched form).
+enum : int { kModeApprox = 0, kModeExact = 1, kModeAny = 2 };
 
 template <int MODE>
 __device__ __forceinline__ bool job_exact(const JobDesc& J) {
@@ -629,7 +627,7 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
             ok[k] = false;
             if (active && p < J.n) {
                 const double2 q = __ldcs(J.pts + p);     // streamed once
-                ok[k] = point_ij(J.X, q.x, q.y, false, pij[k]);
+                ok[k] = point_ij(J.X.model, q.x, q.y, false, pij[k]);
             }
         }
         cp_async_wait_all();

@@ -155,16 +155,20 @@ def big_jobs(agj):
     return polys, [(ia, pts[:3_200_000]), (ie, pts[3_200_000:])]
 
 
-@pytest.mark.parametrize("ppt,ctas", [(2, 0), (1, 3)])
-def test_batch_mode_split_launches(torch, agj, oracle, jobs, indexes, expected, big_jobs, ppt, ctas):
-    """A mixed plan over 1e5+ tiles (approximate and exact probes and emits
-    as separate launches, one warp per tile and persistent): every job equals
-    its plain join, and sampled rows of the big jobs equal the oracle."""
+@pytest.mark.parametrize("ppt,ctas,graph", [(2, 0, True), (1, 3, True), (2, 0, False)])
+def test_batch_mode_split_launches(torch, agj, oracle, jobs, indexes, expected, big_jobs, ppt, ctas, graph):
+    """A mixed plan over 1e5+ tiles (each mode's probe, scan and emit on its
+    own tiles; with the graph the two chains are parallel branches; one warp
+    per tile and persistent): every job equals its plain join, and sampled
+    rows of the big jobs equal the oracle."""
     polys, big = big_jobs
     ix = [b[0] for b in big] + indexes
     pts = [b[1] for b in big] + [jb.points for jb in jobs]
-    b = agj.Batch(ix, [len(p) for p in pts], points_per_lane=ppt, ctas_per_sm=ctas)
-    pr = b.run([_dev(torch, p) for p in pts], b.pairs())
+    b = agj.Batch(ix, [len(p) for p in pts], points_per_lane=ppt, ctas_per_sm=ctas, graph=graph)
+    dev = [_dev(torch, p) for p in pts]
+    pr = b.pairs()
+    for _ in range(2):                       # replay: both chains' scan states and tickets are reset
+        b.run(dev, pr)
     torch.cuda.synchronize()
     _check(pr[2:], expected)
     rng = np.random.default_rng(5)
