@@ -145,7 +145,7 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
     mark(1);
     const bool refine = MODE != kModeApprox && L.exact && L.n_polys;
     if (refine && L.n_tiles) {
-        const uint32_t ct = refine_chunk_tiles(L.n_tiles, G.sms);
+        const uint32_t ct = refine_chunk_tiles(L.n_tiles, G.sms, L.n_polys);
         k_count<<<G.sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, S.poly_count,
                                           (uint32_t)L.n_polys);
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
@@ -227,7 +227,7 @@ cudaError_t enqueue_join_split(const ManyJobs& src, const JoinLayout& L, char* s
         if (L.n_polys) {
             // the refine over the exact tiles' queue regions (slots relative to tile ta)
             const uint64_t q0 = ta * L.tile_slots;
-            const uint32_t ct = refine_chunk_tiles(T - ta, G.sms);
+            const uint32_t ct = refine_chunk_tiles(T - ta, G.sms, L.n_polys);
             k_count<<<G.sms * 2, 256, 0, s>>>(S.queue + q0, S.tile_cand + ta, T - ta, L.tile_slots, ct, S.poly_count,
                                               (uint32_t)L.n_polys);
             k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(

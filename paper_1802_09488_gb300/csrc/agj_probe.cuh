@@ -770,10 +770,12 @@ __global__ void k_scatter(const uint2* __restrict__ queue, const uint32_t* __res
                           uint2* __restrict__ sorted, uint32_t n_polys);
 
 // Tiles per chunk of k_count / k_scatter: 512 for large queues, smaller ones
-// split so that about four chunks per SM share the work.
-inline uint32_t refine_chunk_tiles(uint64_t n_tiles, int sms) {
+// split so that about four chunks per SM share the work, but at least
+// n_polys / 8 tiles, since k_scatter clears and reserves its shared
+// counters (one per polygon) once per chunk.
+inline uint32_t refine_chunk_tiles(uint64_t n_tiles, int sms, uint64_t n_polys) {
     uint32_t ct = 32;
-    while (ct < 512 && (uint64_t)ct * 4 * (uint64_t)sms < n_tiles) ct <<= 1;
+    while (ct < 512 && ((uint64_t)ct * 4 * (uint64_t)sms < n_tiles || (uint64_t)ct * 8 < n_polys)) ct <<= 1;
     return ct;
 }
 
