@@ -263,6 +263,17 @@ def workload(name: str, n: int, rank: int):
     return polys, pts, train
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x (x itself with one process): the job's
+    time is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def step_config(args, n: int, n_polys: int, eps: float, n_train: int, world: int) -> dict:
     """The workload both arms report: per-GPU point count, polygons, precision
     and training sample of the exact index."""
@@ -442,10 +453,7 @@ def main():
                   "csr (k_scan_counts + k_emit_exact)": [ev[1][2].elapsed_time(ev[1][3]) for ev in stage_ev]},
     }
     total_ms = step_ev[0][0].elapsed_time(step_ev[-1][1])
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     # correctness of the timed runs
     assert pa.check() == nnz_a and pe.check() == nnz_e
 
@@ -518,12 +526,8 @@ def main():
             agj.join_host(ia, h_pts, pa, staging, h_off, h_ids_a)
             agj.join_host(ie, h_pts, pe, staging, h_off, h_ids_e)
         barrier()
-        dt = time.perf_counter() - t0
+        dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         e2e_val = world * 2.0 * n * ksteps / dt
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = world * 2.0 * n * ksteps / float(t.item())
         result["e2e"] = {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": 2 * 16 * n,
                          "d2h_bytes_per_step": 2 * 4 * (n + 1) + 4 * (nnz_a + nnz_e) + 2 * 32, "steps": ksteps}
         del staging, h_pts
