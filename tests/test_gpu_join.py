@@ -258,6 +258,22 @@ def test_join_host_pinned_pageable_and_unaligned(torch, agj, c1):
         nnz = agj.join_host(ix, src, pairs, staging, off, ids)
         assert nnz == len(ref_ids)
         assert np.array_equal(off, ref_off) and np.array_equal(ids[:nnz], ref_ids)
+    # page-locked output arrays
+    for src in (torch.from_numpy(pts).pin_memory(), pts):
+        off = torch.empty(len(pts) + 1, dtype=torch.int32).pin_memory()
+        ids = torch.empty(len(ref_ids), dtype=torch.int32).pin_memory()
+        nnz = agj.join_host(ix, src, pairs, staging, off, ids)
+        assert nnz == len(ref_ids)
+        assert np.array_equal(off.numpy().view(np.uint32), ref_off)
+        assert np.array_equal(ids.numpy().view(np.uint32), ref_ids)
+    # an ids buffer one short: nothing is written past it, and the call
+    # reports the missing capacity
+    guard = torch.full((len(ref_ids) + 64,), -7, dtype=torch.int32).pin_memory()
+    short = guard[:len(ref_ids) - 1]
+    off = torch.empty(len(pts) + 1, dtype=torch.int32).pin_memory()
+    with pytest.raises(agj.AgjError):
+        agj.join_host(ix, pts, pairs, staging, off, short)
+    assert (guard[len(ref_ids) - 1:].numpy() == -7).all()
 
 
 def test_scan_wait_is_bounded_and_reported(torch, agj, c1):
