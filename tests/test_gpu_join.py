@@ -285,3 +285,36 @@ def test_scan_wait_is_bounded_and_reported(torch, agj, c1):
     ix = agj.Index(c1.polygons, agj.APPROX, c1.eps_m)
     off, ids = agj.join(ix, _dev(torch, c1.points[:10_000])).to_host()
     assert off[-1] == len(ids) > 0
+
+
+def test_join_host_large(torch, agj):
+    """A 2e7-point host join equals the device join bit for bit, approximate
+    and exact, with page-locked or pageable buffers; an ids buffer one short
+    reports the missing capacity and is not overrun."""
+    from paper_1802_09488_gb300 import synth
+    polys = synth.c2_city_polygons()
+    n = 20_000_000
+    pts = synth.points_mixture(n, synth.BOX_CITY, seed=31, dist_seed=3)
+    train = synth.points_mixture(100_000, synth.BOX_CITY, seed=32, dist_seed=3)
+    h_pts = torch.from_numpy(pts).pin_memory()
+    staging = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+    for ix in (agj.Index(polys, agj.APPROX, 4.0), agj.Index(polys, agj.EXACT, 0, train=train)):
+        ref_off, ref_ids = agj.join(ix, h_pts.cuda()).to_host()
+        pairs = agj.Pairs(ix, n)
+        for src, pinned_out in ((h_pts, True), (pts, False)):
+            if pinned_out:
+                off = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+                ids = torch.empty(len(ref_ids), dtype=torch.int32).pin_memory()
+            else:
+                off = np.empty(n + 1, dtype=np.uint32)
+                ids = np.empty(len(ref_ids), dtype=np.uint32)
+            nnz = agj.join_host(ix, src, pairs, staging, off, ids)
+            got_off = off.numpy().view(np.uint32) if pinned_out else off
+            got_ids = ids.numpy().view(np.uint32) if pinned_out else ids
+            assert nnz == len(ref_ids)
+            assert np.array_equal(got_off, ref_off) and np.array_equal(got_ids, ref_ids)
+        guard = torch.full((len(ref_ids) + 64,), -7, dtype=torch.int32).pin_memory()
+        off = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+        with pytest.raises(agj.AgjError):
+            agj.join_host(ix, h_pts, pairs, staging, off, guard[:len(ref_ids) - 1])
+        assert (guard[len(ref_ids) - 1:].numpy() == -7).all()
