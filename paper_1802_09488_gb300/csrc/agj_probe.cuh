@@ -26,9 +26,10 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 // Resident CTAs per SM the probe kernels are compiled for (a register cap:
 // 65536 / (256 x blocks) per thread).  The probe is latency-bound (dependent
 // trie gathers), so more resident warps pay while the registers last: at 5
-// CTAs (40 warps, 48 registers) both the single-job and the batched probe
-// beat 3 and 4 CTAs on the city workload although the batched one spills a
-// little; at 6 the single-job probe spills more and the exact probe slows.
+// CTAs (40 warps, 48 registers) the exact probes, single-job and batched,
+// beat 3 and 4 CTAs on the city workload (at 6 the exact probe spills and
+// slows); the approximate probes, which queue no candidates, run at 6 CTAs
+// (48 warps, 40 registers).
 #ifndef AGJ_PROBE_MIN_BLOCKS
 #define AGJ_PROBE_MIN_BLOCKS 5
 #endif
@@ -36,7 +37,7 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 #define AGJ_BATCH_PROBE_MIN_BLOCKS 5
 #endif
 #ifndef AGJ_APPROX_PROBE_MIN_BLOCKS
-#define AGJ_APPROX_PROBE_MIN_BLOCKS 6     // the single-job approximate probe: 40 registers pay there
+#define AGJ_APPROX_PROBE_MIN_BLOCKS 6     // approximate probes (single-job and batched): 40 registers pay there
 #endif
 constexpr int kJoinBlock = 256;
 constexpr int kJoinPPT = 2;                    // points per lane of the plain join
@@ -601,9 +602,9 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
 // warp tile wt = tile lt of job J: cell id + walk for every point of the tile (32 lanes x PPT
 // points, point base + lane + 32 k, so the 16-byte loads coalesce), the
 // tagged entry stored per point.  Approximate jobs count every reference of
-// the tile; exact jobs count the true hits and queue the candidate
-// references (warp ballot: one atomic reserves a warp's queue slots).  No
-// tile waits on another.
+// the tile; exact jobs count the true hits and write the candidate
+// references to the tile's own queue region (queue_tile).  No tile waits on
+// another.
 // With kAsync the CTA's shared tables are still in flight (cta_setup_async):
 // every thread of the CTA calls this (active false: a warp past the last
 // tile), and the wait and barrier come after the cell ids, before the first
