@@ -286,10 +286,13 @@ int agj_join_timed(const agj_index* index, const double* d_points, uint64_t n, v
 
 /*
  * A plan that joins m (index, point batch) jobs of uneven sizes in one
- * launch sequence: the probe and emit kernels are persistent grids striding
- * over every job's warp tiles, the refine step covers the candidates of all
- * exact jobs at once, and the sequence is captured once into a CUDA graph
- * that each run replays.  The paper joins one point stream against one
+ * launch sequence: the probe and emit kernels cover every job's warp tiles
+ * (one warp per tile, or persistent grids striding over them), the refine
+ * step covers the candidates of all exact jobs at once, and the sequence is
+ * captured once into a CUDA graph that each run replays.  In a large plan
+ * with both modes the approximate and the exact jobs run as two independent
+ * chains of kernels compiled for their mode, parallel branches of the graph.
+ * The paper joins one point stream against one
  * index; the batched form serves callers with many small or uneven batches,
  * where one plain join per batch pays a launch sequence and a grid tail per
  * batch.
