@@ -262,6 +262,7 @@ def voronoi_tiling(n_polys: int, box: Box, seed: int, vmin: int, vmax: int,
 
     out = [None] * n
     todo = list(range(n))
+    converged = False
     for _ in range(12):
         nxt = set()
         for k in todo:
@@ -274,13 +275,18 @@ def voronoi_tiling(n_polys: int, box: Box, seed: int, vmin: int, vmax: int,
             else:
                 out[k] = r
         if not nxt:
+            converged = True
             break
         todo = sorted(nxt)
-    for k in range(n):
-        r = ring_xy(k)
-        if _segments_cross(r):
-            raise RuntimeError(f"polygon {k} is not simple after jitter reduction")
-        out[k] = r
+    # Every polygon touched by an amplitude change is re-checked above, so on
+    # convergence out[k] is ring_xy(k) at the final amplitudes and simple;
+    # otherwise re-check them all.
+    if not converged:
+        for k in range(n):
+            r = ring_xy(k)
+            if _segments_cross(r):
+                raise RuntimeError(f"polygon {k} is not simple after jitter reduction")
+            out[k] = r
     return [np.ascontiguousarray(box.to_latlng(r)) for r in out]
 
 
