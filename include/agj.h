@@ -245,10 +245,11 @@ int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* s
  * owns every device allocation, and latency-bound loops where an allocation
  * could synchronise the device and stall other streams.
  *
- * It computes exactly what agj_join computes for an AGJ_APPROX index, with
- * the same kernel; its scan work space is a static device array of the
- * library, sized for at most AGJ_NOALLOC_MAX_POINTS points per call, held
- * by every device that loads the library until the process exits.
+ * It computes the same CSR as agj_join for an AGJ_APPROX index, with a
+ * one-pass kernel built on the same probe and emit helpers (probe, tile
+ * scan by look-back, emit); that scan's work space is a static device array
+ * of the library, sized for at most AGJ_NOALLOC_MAX_POINTS points per call,
+ * held by every device that loads the library until the process exits.
  * The caller passes the inputs and outputs: d_points (device, n x {lat, lng},
  * 16-byte aligned), d_offsets (device, n + 1 uint32), d_ids (device,
  * ids_capacity uint32, at least n * max_refs of agj_index_stats) and
@@ -259,8 +260,10 @@ int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* s
  * the GPU (different streams, no ordering between them) race and give wrong
  * results; order them on one stream or with events.
  * Errors: AGJ_EINVAL (null or misaligned pointer, exact-mode index, index
- * built with host_only), AGJ_ECAPACITY (n > AGJ_NOALLOC_MAX_POINTS, or
- * ids_capacity too small), AGJ_ECUDA.  Device-side conditions land in
+ * built with host_only), AGJ_ECAPACITY (n > AGJ_NOALLOC_MAX_POINTS;
+ * ids_capacity below n * max_refs; or n * max_refs >= 2^32 - 1, beyond the
+ * 32-bit offsets, as for agj_join), AGJ_ECUDA.  Only the first
+ * n * max_refs ids are ever written.  Device-side conditions land in
  * d_status[1] as for agj_join.  Asynchronous on `stream`.
  */
 #define AGJ_NOALLOC_MAX_POINTS (1ull << 24)

@@ -565,6 +565,7 @@ int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t 
     if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return AGJ_EINVAL;
     if (n > kNoAllocMaxPoints) return AGJ_ECAPACITY;
     const uint64_t need = n * std::max<uint64_t>(X.stats.max_refs, 1);
+    if (need >= 0xFFFFFFFFull) return AGJ_ECAPACITY;       // offsets are 32-bit, as in agj_join
     if (ids_capacity < need) return AGJ_ECAPACITY;
     if (need && !d_ids) return AGJ_EINVAL;
     uint64_t* sc = nullptr;
@@ -582,7 +583,7 @@ int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t 
     }
     const DevIndex D = make_dev_index(X);
     k_join_approx<kNoAllocPPT><<<(unsigned)((n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock), kJoinBlock, 0, s>>>(
-        D, reinterpret_cast<const double2*>(d_points), (uint32_t)n, d_offsets, d_ids, ids_capacity,
+        D, reinterpret_cast<const double2*>(d_points), (uint32_t)n, d_offsets, d_ids, need,
         sc + kNoAllocHeaderWords, reinterpret_cast<uint32_t*>(sc), d_status, sc + 2);
     return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
