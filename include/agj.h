@@ -283,6 +283,45 @@ int agj_join_approx_noalloc(const agj_index* index, const double* d_points, uint
 int agj_join_timed(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out,
                    void* const events[4]);
 
+/*
+ * Aggregation mode: the query the paper benchmarks (§V: the points of a
+ * stream joined with a polygon set, "count(*) ... group by polygon_id").
+ * The probe is the join's (cell id, face/prefix stage, trie walk, §III-E);
+ * instead of pairs it adds every counted reference to its polygon, as the
+ * SIMD aggregation of §IV does with gather/scatter: the lanes of a warp
+ * that name the same polygon are combined into one add, and the rare
+ * lanes (cells with more than two references; in exact mode candidate
+ * references) are handled apart.  In exact mode the candidates are refined
+ * by the same ST_Covers step as agj_join, grouped by polygon, and each
+ * group's passes are added at once.
+ *
+ * Result: d_counts[P] (device, n_polys uint64) = the number of points p of
+ * this call for which agj_join on the same index and points would output
+ * the pair (p, P), i.e. the number of times P occurs in its ids; with
+ * accumulate != 0 these are added to d_counts, else d_counts is
+ * overwritten.  d_status (device, 4 uint64 words): [0] pairs counted (the
+ * sum of this call's counts), [1] error flags as for agj_join (bit 1 scan
+ * wait timed out, bit 2 trie bounds check, bit 3 candidate queue
+ * overflow), [2] candidate pairs refined (exact mode), [3] trie node
+ * entries read.  d_points: device, n x {lat, lng}, 16-byte aligned,
+ * borrowed; n < 2^32.  d_scratch: device work space of at least
+ * agj_count_scratch_bytes(index, n) bytes, 256-byte aligned (bytes 16..23
+ * receive the count of points whose walk recomputed the FP64 cell id,
+ * 24..31 the count of candidates refined in FP64).  Asynchronous on
+ * `stream`.  Errors (returned immediately): AGJ_EINVAL (null or misaligned
+ * pointer, n >= 2^32, index built with host_only), AGJ_ECAPACITY (scratch
+ * too small, or the exact candidate queue beyond 32-bit slots), AGJ_ECUDA.
+ */
+uint64_t agj_count_scratch_bytes(const agj_index* index, uint64_t n);
+int agj_join_count(const agj_index* index, const double* d_points, uint64_t n, void* stream, uint64_t* d_counts,
+                   int accumulate, uint64_t* d_status, void* d_scratch, uint64_t scratch_bytes);
+/* agj_join_count recording four caller-created events on `stream`: [0]
+ * before the probe kernel, [1] after it, [2] after the refine (exact mode;
+ * right after [1] in approx mode), [3] at the end. */
+int agj_join_count_timed(const agj_index* index, const double* d_points, uint64_t n, void* stream, uint64_t* d_counts,
+                         int accumulate, uint64_t* d_status, void* d_scratch, uint64_t scratch_bytes,
+                         void* const events[4]);
+
 /* ---------------------------------------------------------------------- */
 /* batched form (no counterpart in the paper)                               */
 /* ---------------------------------------------------------------------- */
@@ -495,6 +534,15 @@ int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, do
  * Synchronises `stream`.
  */
 int agj_selftest_scan_timeout(void* stream);
+
+/*
+ * Measurement utility (no counterpart in the paper): the FP64 fused
+ * multiply-add rate of the current device in flop/s (2 per FMA), from the
+ * library's own kernel of independent FMA chains on every SM, best of five
+ * timed launches.  The cell-id kernel's FP64 roofline is stated against
+ * it.  Allocates 64 bytes of device memory and synchronises `stream`.
+ */
+int agj_measure_fp64_rate(void* stream, double* flops_per_s);
 
 /* Cell ids of points with the device kernel (FP64 spec, bit-exact); for
  * checking the id step alone.  d_ids: device, n uint64. */

@@ -216,6 +216,12 @@ class PolySet:
         self._lib.or_join_exact_fill(self._h, _ptr(pts), n, _ptr(offs), _ptr(ids), threads)
         return offs, ids[:nnz]
 
+    def count_exact(self, points: np.ndarray, threads: int = 0) -> np.ndarray:
+        """Aggregation query of §V (count(*) group by polygon) for the exact
+        join: how often each polygon occurs in the brute-force CSR."""
+        _, ids = self.join_exact(points, threads)
+        return np.bincount(ids, minlength=self.n).astype(np.uint64)
+
     def check_covering(self, cells, ref_off, refs, eps_m: float = 0.0, cand_margin: float = 1e-11) -> dict:
         cells = np.ascontiguousarray(cells, dtype=np.uint64)
         ref_off = np.ascontiguousarray(ref_off, dtype=np.uint64)
@@ -248,3 +254,10 @@ def join_approx_logical(cells, ref_off, refs, points: np.ndarray, threads: int =
 def logical_find(cells, cid: int) -> int:
     cells = np.ascontiguousarray(cells, dtype=np.uint64)
     return int(_load().or_logical_find(_ptr(cells), len(cells), cid))
+
+
+def count_approx_logical(cells, ref_off, refs, points: np.ndarray, n_polys: int, threads: int = 0) -> np.ndarray:
+    """Aggregation query (§V) for the approximate join read off a logical
+    covering: how often each polygon occurs in that CSR."""
+    _, ids = join_approx_logical(cells, ref_off, refs, points, threads)
+    return np.bincount(ids, minlength=n_polys).astype(np.uint64)

@@ -244,6 +244,34 @@ int agj_join_approx_noalloc(const agj_index* index, const double* d_points, uint
                                            as_stream(stream));
 }
 
+uint64_t agj_count_scratch_bytes(const agj_index* index, uint64_t n) {
+    return index ? agj::count_scratch_bytes(index->X, n) : 0;
+}
+
+int agj_join_count(const agj_index* index, const double* d_points, uint64_t n, void* stream, uint64_t* d_counts,
+                   int accumulate, uint64_t* d_status, void* d_scratch, uint64_t scratch_bytes) {
+    if (!index || !index->X.d_blob) return AGJ_EINVAL;
+    return agj::launch_join_count(index->X, d_points, n, as_stream(stream), d_counts, d_status, d_scratch,
+                                  scratch_bytes, accumulate != 0);
+}
+
+int agj_join_count_timed(const agj_index* index, const double* d_points, uint64_t n, void* stream, uint64_t* d_counts,
+                         int accumulate, uint64_t* d_status, void* d_scratch, uint64_t scratch_bytes,
+                         void* const events[4]) {
+    if (!index || !index->X.d_blob || !events) return AGJ_EINVAL;
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) {
+        if (!events[k]) return AGJ_EINVAL;
+        ev[k] = static_cast<cudaEvent_t>(events[k]);
+    }
+    return agj::launch_join_count(index->X, d_points, n, as_stream(stream), d_counts, d_status, d_scratch,
+                                  scratch_bytes, accumulate != 0, ev);
+}
+
+int agj_measure_fp64_rate(void* stream, double* flops_per_s) {
+    return agj::measure_fp64_rate(as_stream(stream), flops_per_s);
+}
+
 int agj_join_check(const agj_pairs* pairs, void* stream, uint64_t* nnz) {
     if (!pairs || !pairs->status) return AGJ_EINVAL;
     uint64_t st[4] = {0, 0, 0, 0};

@@ -50,8 +50,11 @@ constexpr uint64_t kPolyScanPerCta = 256 * 4;
 
 // n_points / n_tiles: sizes of the (tile-padded) global point space and of
 // the tile space; exact: some job refines; tile_slots: queue slots per tile;
-// n_polys: polygons of the exact jobs.
-inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, uint32_t tile_slots, uint64_t n_polys) {
+// n_polys: polygons of the exact jobs.  count: the aggregation mode's work
+// space, which holds no per-point entries, tile counts, prefixes or pass
+// bytes (those offsets stay 0 and are not used).
+inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, uint32_t tile_slots, uint64_t n_polys,
+                              bool count = false) {
     JoinLayout L;
     L.n_points = n_points;
     L.n_tiles = n_tiles;
@@ -71,13 +74,15 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
         o += align256(n_polys * 4 + 4);
     }
     L.zero_end = o;
-    L.entries = o; o += align256(n_points * 8 + 8);
-    L.tcount = o; o += align256(n_tiles * 4 + 4);
-    L.tprefix = o; o += align256(n_tiles * 4 + 4);
+    if (!count) {
+        L.entries = o; o += align256(n_points * 8 + 8);
+        L.tcount = o; o += align256(n_tiles * 4 + 4);
+        L.tprefix = o; o += align256(n_tiles * 4 + 4);
+    }
     if (exact) {
         L.tcand = o; o += align256(n_tiles * 4 + 4);
         L.queue = o; o += align256(L.queue_cap * 8 + 8);
-        L.pass = o; o += align256(L.queue_cap + 32);
+        if (!count) { L.pass = o; o += align256(L.queue_cap + 32); }
         L.sorted = o; o += align256(L.queue_cap * 8 + 8);
         L.cursor = o; o += align256((n_polys + 1) * 4);
         // refine chunk descriptors: one per kPipBlock candidates of a polygon, plus one partial per polygon

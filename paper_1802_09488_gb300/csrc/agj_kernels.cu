@@ -48,6 +48,12 @@ __global__ void __launch_bounds__(256) k_zero(uint64_t* __restrict__ a, uint64_t
     }
 }
 
+// ORs the scan error bits into a status word (aggregation mode has no emit
+// kernel to carry them).
+__global__ void k_merge_err(const uint64_t* __restrict__ err, uint64_t* __restrict__ status_err) {
+    if (threadIdx.x == 0 && *err) atomicOr((unsigned long long*)status_err, (unsigned long long)*err);
+}
+
 __global__ void k_cell_ids(const double2* __restrict__ pts, uint64_t n, uint64_t* __restrict__ out) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -251,6 +257,132 @@ __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue
             }
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// aggregation mode: count(*) group by polygon
+// ---------------------------------------------------------------------------
+// The paper's benchmark query (§V) counts the points of each polygon; its
+// SIMD aggregation (§IV) adds the references of a vector of points with
+// gather/scatter and defers the rare lanes (several references, candidates)
+// to a buffer.  Here a warp adds the references of its 32 lanes with one
+// atomic per distinct polygon (lanes naming the same polygon are combined by
+// __match_any_sync), into a shared-memory histogram per CTA that is added to
+// the global counts once, when the persistent CTA is done; lookup-table
+// cells (more than two references) are added lane by lane.  In exact mode
+// only true hits are counted here; candidates go to the tile's queue region
+// and are refined and counted by k_pip<..., true>.
+constexpr uint32_t kAggSmemPolys = 4096;       // polygons counted in shared memory (16 KB)
+constexpr uint32_t kNoPoly = 0xFFFFFFFFu;
+
+// One atomic per distinct polygon among the warp's lanes (kNoPoly: none).
+__device__ __forceinline__ void agg_add_warp(uint32_t poly, uint32_t* s_hist, uint64_t* counts) {
+    const uint32_t active = __ballot_sync(kFull, poly != kNoPoly);
+    if (poly == kNoPoly) return;
+    const uint32_t peers = __match_any_sync(active, poly);
+    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) {
+        if (s_hist) atomicAdd(&s_hist[poly], (uint32_t)__popc(peers));
+        else atomicAdd((unsigned long long*)&counts[poly], (unsigned long long)__popc(peers));
+    }
+}
+
+__device__ __forceinline__ void agg_add_lane(uint32_t poly, uint32_t* s_hist, uint64_t* counts) {
+    if (s_hist) atomicAdd(&s_hist[poly], 1u);
+    else atomicAdd((unsigned long long*)&counts[poly], 1ull);
+}
+
+// One warp tile (32 lanes x PPT points) of the aggregation: cell id, walk,
+// then every counted reference added; *pairs, *gathers and *fallbacks
+// accumulate the lane's totals across tiles.
+template <int PPT, int MODE>
+__device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
+                                         const uint64_t* s_root, uint64_t wt, const JoinScratch& S, uint32_t* s_hist,
+                                         uint64_t* counts, uint32_t* pairs, uint32_t* gathers, uint32_t* fallbacks) {
+    constexpr bool exact = MODE == kModeExact;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t base = wt * (32 * PPT);
+    PointIJ pij[PPT];
+    bool ok[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        ok[k] = false;
+        if (p < J.n) {
+            const double2 q = __ldcs(J.pts + p);      // streamed once
+            ok[k] = point_ij(J.X.model, q.x, q.y, false, pij[k]);
+        }
+    }
+    uint64_t e[PPT];
+    *gathers += probe_cells<PPT>(J.X, faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], fallbacks);
+    uint32_t nc[PPT], csum = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        uint32_t nt;
+        entry_counts(J.X, e[k], &nt, &nc[k]);
+        *pairs += exact ? nt : nt + nc[k];
+        csum += exact ? nc[k] : 0u;
+        const uint32_t tag = (uint32_t)(e[k] & 3ull);
+        // one or two inline references: warp-combined adds
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            uint32_t poly = kNoPoly;
+            if ((tag == 1 && r == 0) || tag == 2) {
+                const uint32_t pl = payload_of(e[k], r);
+                if (pl != kInvalidPayloadDev && (!exact || (pl & 1u))) poly = pl >> 1;
+            }
+            agg_add_warp(poly, s_hist, counts);
+        }
+        // a lookup-table cell: its lists, lane by lane (rare)
+        if (tag == 3) {
+            const uint32_t off = payload_of(e[k], 0);
+            const uint32_t nt3 = __ldg(J.X.lut + off);
+            for (uint32_t t = 0; t < nt3; ++t) agg_add_lane(__ldg(J.X.lut + off + 1 + t), s_hist, counts);
+            if (!exact) {
+                const uint32_t nc3 = __ldg(J.X.lut + off + 1 + nt3);
+                for (uint32_t t = 0; t < nc3; ++t) agg_add_lane(__ldg(J.X.lut + off + 2 + nt3 + t), s_hist, counts);
+            }
+        }
+    }
+    if constexpr (exact) queue_tile<PPT>(J, e, nc, csum, wt, base, 0, S);
+}
+
+// Persistent CTAs stride over the warp tiles (a warp takes every
+// (gridDim.x x 8)-th tile, no CTA barrier between tiles); each CTA keeps
+// its histogram (n_polys <= kAggSmemPolys, else the global counts directly)
+// and its warps' totals until the end.
+#ifndef AGJ_AGG_PROBE_MIN_BLOCKS
+#define AGJ_AGG_PROBE_MIN_BLOCKS 4      // 64 registers: the aggregation's extra state spills at 40-48
+#endif
+template <int PPT, int MODE>
+__global__ void __launch_bounds__(kJoinBlock, AGJ_AGG_PROBE_MIN_BLOCKS)
+    k_agg_probe(const JobDesc J, uint64_t T, const JoinScratch S, uint64_t* __restrict__ counts) {
+    __shared__ __align__(16) uint16_t s_hlut[1024];
+    __shared__ __align__(16) uint64_t s_rootbuf[256];
+    __shared__ DevFace s_faces[6];
+    __shared__ uint32_t s_hist[kAggSmemPolys];
+    const bool smem = J.X.n_polys <= kAggSmemPolys;
+    if (smem)
+        for (uint32_t p = threadIdx.x; p < J.X.n_polys; p += blockDim.x) s_hist[p] = 0;
+    const uint64_t* s_root = cta_setup(&J.X, s_hlut, s_faces, s_rootbuf);
+    __syncthreads();
+    uint32_t pairs = 0, gathers = 0, fallbacks = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * kWarpsPerBlock;
+    for (uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); wt < T; wt += stride)
+        agg_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, S, smem ? s_hist : nullptr, counts, &pairs, &gathers,
+                            &fallbacks);
+    // every warp of the CTA runs the same number of reductions here
+    const uint32_t wp = __reduce_add_sync(kFull, pairs), wg = __reduce_add_sync(kFull, gathers),
+                   wf = __reduce_add_sync(kFull, fallbacks);
+    if ((threadIdx.x & 31) == 0) {
+        if (wp) atomicAdd((unsigned long long*)&J.status[0], (unsigned long long)wp);
+        if (wg) atomicAdd((unsigned long long*)&J.status[3], (unsigned long long)wg);
+        if (wf) atomicAdd((unsigned long long*)&J.counters[0], (unsigned long long)wf);
+    }
+    if (smem) {
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < J.X.n_polys; p += blockDim.x)
+            if (s_hist[p]) atomicAdd((unsigned long long*)&counts[p], (unsigned long long)s_hist[p]);
     }
 }
 
@@ -476,6 +608,132 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
             ? enqueue_join<kJoinPPT, OneJob, kModeApprox>(src, L, sc, G, out->status, 4, s, events)
             : enqueue_join<kJoinPPT, OneJob, kModeExact>(src, L, sc, G, out->status, 4, s, events);
     return e == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+}
+
+namespace {
+
+JoinLayout count_layout(const Index& X, uint64_t n) {
+    const uint64_t tiles = (n + 32 * kJoinPPT - 1) / (32 * kJoinPPT);
+    const bool exact = X.mode == AGJ_EXACT;
+    return join_layout(tiles * 32 * kJoinPPT, tiles, exact,
+                       exact ? 32u * kJoinPPT * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
+                       exact ? X.n_polys : 0, true);
+}
+
+}  // namespace
+
+uint64_t count_scratch_bytes(const Index& X, uint64_t n) { return count_layout(X, n).total; }
+
+int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, uint64_t* d_counts,
+                      uint64_t* d_status, void* scratch, uint64_t scratch_bytes, bool accumulate,
+                      cudaEvent_t const* events) {
+    if (!d_status || (X.n_polys && !d_counts) || (n && !d_points) || !scratch) return AGJ_EINVAL;
+    if (n >= 0xFFFFFFFFull) return AGJ_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0 || (reinterpret_cast<uintptr_t>(scratch) & 255u) != 0)
+        return AGJ_EINVAL;
+    const JoinLayout L = count_layout(X, n);
+    if (L.queue_cap >= 0xFFFFFFFFull) return AGJ_ECAPACITY;
+    if (scratch_bytes < L.total) return AGJ_ECAPACITY;
+    char* sc = static_cast<char*>(scratch);
+    const JoinScratch S = join_scratch(L, sc);
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(sc);
+    const int sms = sm_count();
+    auto mark = [&](int k) {
+        if (events) cudaEventRecord(events[k], s);
+    };
+    // zero the header, scan states and per-polygon candidate counts, the
+    // status words and (unless accumulating) the counts
+    {
+        const uint64_t zw = L.zero_end / 8, cw = accumulate ? 0 : X.n_polys;
+        const int grid = (int)std::min<uint64_t>((zw + cw + 4 + 255) / 256 + 1, (uint64_t)sms * 4);
+        k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint64_t*>(sc), zw, d_status, 4);
+        if (cw) k_zero<<<grid, 256, 0, s>>>(d_counts, cw, nullptr, 0);
+    }
+    mark(0);
+    agj_pairs none;
+    memset(&none, 0, sizeof none);
+    none.status = d_status;
+    const JobDesc J = make_job(X, d_points, n, &none, reinterpret_cast<uint64_t*>(sc) + kHdrIdFallbacks);
+    const bool exact = X.mode == AGJ_EXACT;
+    if (L.n_tiles) {
+        const uint64_t ctas = (L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const int per_sm = AGJ_AGG_PROBE_MIN_BLOCKS;
+        const int grid = (int)std::min<uint64_t>(ctas, (uint64_t)sms * per_sm);
+        if (exact) k_agg_probe<kJoinPPT, kModeExact><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts);
+        else k_agg_probe<kJoinPPT, kModeApprox><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts);
+    }
+    mark(1);
+    if (exact && L.n_tiles && L.n_polys) {
+        OneJob src;
+        src.d = J;
+        const uint32_t ct = refine_chunk_tiles(L.n_tiles, sms, L.n_polys);
+        k_count<<<sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, S.poly_count,
+                                        (uint32_t)L.n_polys);
+        k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
+            S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.cursor), hdr + 2,
+            reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
+            reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
+        k_scatter<<<sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct,
+                                          reinterpret_cast<uint32_t*>(sc + L.cursor),
+                                          reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
+        k_pip<OneJob, true><<<sms * AGJ_PIP_MIN_BLOCKS, kPipBlock, 0, s>>>(
+            src, 32 * kJoinPPT, reinterpret_cast<const uint2*>(sc + L.sorted), reinterpret_cast<const uint4*>(sc + L.cpoly),
+            hdr + 2, nullptr, nullptr, d_counts);
+        // the polygon scan's wait status goes to the join's error word
+        k_merge_err<<<1, 32, 0, s>>>(reinterpret_cast<const uint64_t*>(sc) + kHdrScanErr, d_status + 1);
+    }
+    mark(2);
+    mark(3);
+    return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 throughput (a measurement utility for the cell-id kernel's roofline)
+// ---------------------------------------------------------------------------
+// Each thread runs kFmaChains independent chains of x = x * a + b (one
+// rounding each, __fma_rn), so the FP64 pipe has independent work every
+// cycle; 2 flops per FMA.  The result is stored so nothing is removed.
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(256) k_fp64_fma(double a, double b, uint32_t iters, double* __restrict__ out) {
+    double x[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = (double)(threadIdx.x + c) * 1e-3;
+    for (uint32_t t = 0; t < iters; ++t) {
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) x[c] = __fma_rn(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += x[c];
+    if (s == 12345.678) out[0] = s;       // practically never true; keeps the chains live
+}
+
+int measure_fp64_rate(cudaStream_t s, double* flops_per_s) {
+    if (!flops_per_s) return AGJ_EINVAL;
+    double* d = nullptr;
+    if (cudaMalloc(&d, 64) != cudaSuccess) { cudaGetLastError(); return AGJ_ENOMEM; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int grid = sm_count() * 8;
+    const uint32_t iters = 1u << 14;
+    k_fp64_fma<<<grid, 256, 0, s>>>(0.999999, 1e-7, 256, d);        // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < 5; ++r) {
+        cudaEventRecord(e0, s);
+        k_fp64_fma<<<grid, 256, 0, s>>>(0.999999, 1e-7, iters, d);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = ms < best ? ms : best;
+    }
+    const int rc = cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    *flops_per_s = 2.0 * kFmaChains * (double)iters * grid * 256.0 / (best * 1e-3);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------

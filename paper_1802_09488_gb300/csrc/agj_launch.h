@@ -18,6 +18,14 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
 int launch_join_approx_noalloc(const Index& X, const double* d_points, uint64_t n, uint32_t* d_offsets,
                                uint32_t* d_ids, uint64_t ids_capacity, uint64_t* d_status, cudaStream_t s);
 int launch_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, cudaStream_t s);
+// Aggregation mode (counts per polygon): work space size and the launch.
+uint64_t count_scratch_bytes(const Index& X, uint64_t n);
+int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, uint64_t* d_counts,
+                      uint64_t* d_status, void* scratch, uint64_t scratch_bytes, bool accumulate,
+                      cudaEvent_t const* events = nullptr);
+// FP64 fused multiply-add throughput of the current device (flop/s), from
+// an own kernel of independent FMA chains timed with events (synchronises).
+int measure_fp64_rate(cudaStream_t s, double* flops_per_s);
 // Runs the tile scan with a predecessor that never publishes (see agj.h).
 int selftest_scan_timeout(cudaStream_t s);
 

@@ -794,14 +794,20 @@ inline uint32_t refine_chunk_tiles(uint64_t n_tiles, int sms, uint64_t n_polys) 
 #ifndef AGJ_PIP_MIN_BLOCKS
 #define AGJ_PIP_MIN_BLOCKS 6
 #endif
+//
+// With kCount (aggregation mode) the candidates' results are not stored:
+// the chunk's passing candidates (all of one polygon) are counted with one
+// block reduction and added to counts[polygon] and to the pair count
+// status[0] of the chunk's job.
 constexpr int kPipSmemBand = 4096;               // band-table words staged per CTA (uint16)
-template <class Src>
+template <class Src, bool kCount = false>
 __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src src, uint32_t tile_points,
                                                                    const uint2* __restrict__ sorted,
                                                                    const uint4* __restrict__ chunk_desc,
                                                                    const uint32_t* __restrict__ n_chunks,
                                                                    uint8_t* __restrict__ pass,
-                                                                   uint32_t* __restrict__ tile_count) {
+                                                                   uint32_t* __restrict__ tile_count,
+                                                                   uint64_t* __restrict__ counts = nullptr) {
     __shared__ F2 s_lv[kPipSmemVerts];
     __shared__ uint16_t s_band[kPipSmemBand];
     const uint32_t total = *n_chunks;
@@ -830,9 +836,10 @@ __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src
         if (banded)
             for (uint32_t t = threadIdx.x; t < L.band_len; t += blockDim.x) s_band[t] = JP.X.poly_band[L.band + t];
         __syncthreads();
+        int r = 0;
         if (have) {
             const uint32_t wt = it.x / tile_points;
-            int r = -1;
+            r = -1;
             float pu, pv, dp;
             if (certified && model_uv_local(JP.X.model, pt.x, pt.y, L, &pu, &pv, &dp))
                 r = covers_certified(s_lv, V, L, banded ? s_band : nullptr, pu, pv, dp);
@@ -840,8 +847,17 @@ __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src
                 r = covers_fp64(JP.X, poly, pt.x, pt.y) ? 1 : 0;
                 atomicAdd((unsigned long long*)&src.job(src.find_tile(wt)).counters[1], 1ull);
             }
-            pass[it.y] = (uint8_t)r;
-            if (r) atomicAdd(&tile_count[wt], 1u);
+            if constexpr (!kCount) {
+                pass[it.y] = (uint8_t)r;
+                if (r) atomicAdd(&tile_count[wt], 1u);
+            }
+        }
+        if constexpr (kCount) {
+            const int passed = __syncthreads_count(r);
+            if (threadIdx.x == 0 && passed) {
+                atomicAdd((unsigned long long*)&counts[poly], (unsigned long long)passed);
+                atomicAdd((unsigned long long*)&JP.status[0], (unsigned long long)passed);
+            }
         }
     }
 }

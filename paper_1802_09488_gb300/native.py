@@ -153,6 +153,10 @@ def lib():
             "agj_server_destroy": (None, [P]),
             "agj_server_load": (i32, [P, P, P]),
             "agj_plain_load": (i32, [P, u32, P, P]),
+            "agj_count_scratch_bytes": (u64, [P, u64]),
+            "agj_join_count": (i32, [P, P, u64, P, P, i32, P, P, u64]),
+            "agj_join_count_timed": (i32, [P, P, u64, P, P, i32, P, P, u64, P]),
+            "agj_measure_fp64_rate": (i32, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -365,6 +369,59 @@ def join_host(index: Index, points: np.ndarray, pairs: Pairs, staging, h_offsets
     return int(nnz.value)
 
 
+class Counts:
+    """Aggregation-mode buffers (torch device tensors) for joins of up to n
+    points: counts (int64 per polygon, read as uint64), status (4 words) and
+    the work space."""
+
+    def __init__(self, index: Index, n: int, device=None):
+        import torch
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.n_max = int(n)
+        self.n_polys = int(index.stats()["n_polys"])
+        self.counts = torch.zeros(max(self.n_polys, 1), dtype=torch.int64, device=dev)
+        self.status = torch.zeros(4, dtype=torch.int64, device=dev)
+        self.scratch_bytes = int(lib().agj_count_scratch_bytes(index.handle, int(n)))
+        self.scratch = torch.empty(max(self.scratch_bytes, 256), dtype=torch.uint8, device=dev)
+
+    def to_host(self) -> np.ndarray:
+        """counts (uint64 per polygon) after a status check."""
+        st = self.status.cpu().numpy().view(np.uint64)
+        if st[1]:
+            raise AgjError(AGJ_EDEVICE, f"agj_join_count (device status {int(st[1])})")
+        return self.counts[: self.n_polys].cpu().numpy().view(np.uint64)
+
+    def fallbacks(self) -> int:
+        return int(self.scratch[16:24].cpu().view(torch_int64()).item())
+
+
+def join_count(index: Index, points, counts: Counts | None = None, accumulate: bool = False, stream=None,
+               events=None) -> Counts:
+    """Aggregation mode (agj_join_count): per-polygon counts of the join of
+    device points (torch float64 (n,2)) with the index."""
+    import torch
+    assert points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()
+    n = points.shape[0]
+    if counts is None or counts.n_max < n:
+        counts = Counts(index, n, device=points.device)
+    args = (index.handle, C.c_void_p(points.data_ptr()), n, _stream_ptr(stream), C.c_void_p(counts.counts.data_ptr()),
+            1 if accumulate else 0, C.c_void_p(counts.status.data_ptr()), C.c_void_p(counts.scratch.data_ptr()),
+            counts.scratch_bytes)
+    if events is None:
+        _check(lib().agj_join_count(*args), "agj_join_count")
+    else:
+        arr = (C.c_void_p * 4)(*[C.c_void_p(e.cuda_event) for e in events])
+        _check(lib().agj_join_count_timed(*args, arr), "agj_join_count_timed")
+    return counts
+
+
+def measure_fp64_rate(stream=None) -> float:
+    """FP64 FMA throughput of the current device in flop/s (agj_measure_fp64_rate)."""
+    r = C.c_double()
+    _check(lib().agj_measure_fp64_rate(_stream_ptr(stream), C.byref(r)), "agj_measure_fp64_rate")
+    return float(r.value)
+
+
 class Batch:
     """A batched-join plan (agj_batch_create) for fixed (index, point count)
     jobs; run() joins one point batch per job into one Pairs per job."""
@@ -558,10 +615,12 @@ def lut_encode(lists):
     return words[:nw.value], offs[:len(lists)]
 
 
-def cell_ids(points, stream=None):
+def cell_ids(points, stream=None, out=None):
     """Device cell ids (FP64 spec) of torch float64 (n,2) points, as int64 bit patterns."""
     import torch
-    out = torch.empty(points.shape[0], dtype=torch.int64, device=points.device)
+    if out is None:
+        out = torch.empty(points.shape[0], dtype=torch.int64, device=points.device)
+    assert out.is_cuda and out.dtype == torch.int64 and out.numel() >= points.shape[0]
     rc = lib().agj_cell_ids(C.c_void_p(points.data_ptr()), points.shape[0], C.c_void_p(out.data_ptr()),
                             _stream_ptr(stream))
     _check(rc, "agj_cell_ids")
