@@ -73,7 +73,11 @@ typedef struct {
 typedef enum {
     AGJ_APPROX = 0,   /* §III-A approximate join: candidate cells refined until
                          their diagonal is below the precision; no PIP */
-    AGJ_EXACT  = 1    /* §III-A exact join: trained index + PIP on candidates */
+    AGJ_EXACT  = 1,   /* §III-A exact join: trained index + PIP on candidates */
+    AGJ_AUTO   = 2    /* build only: §III-A's choice between the two - the
+                         approximate index if it fits memory_budget_bytes
+                         (which must be set), else the exact one trained
+                         within that budget; agj_index_stats' mode says which */
 } agj_mode;
 
 /* Build options; zero-initialise and set what you need.  0 selects the
@@ -110,8 +114,9 @@ typedef struct agj_index agj_index;
  * returning).  precision_m is used in approx mode only.
  * Ownership: *out is owned by the caller and released with agj_free.
  * Errors: AGJ_EINVAL (null, n_vertices < 3, invalid vertex, precision_m <= 0
- * in approx mode), AGJ_EUNSUPPORTED (polygon spans faces, too many
- * polygons), AGJ_EBUDGET (approx index above memory_budget_bytes),
+ * in approx mode, AGJ_AUTO without a memory budget), AGJ_EUNSUPPORTED
+ * (polygon spans faces, too many polygons), AGJ_EBUDGET (approx index above
+ * memory_budget_bytes; AGJ_AUTO then builds the exact index instead),
  * AGJ_ENOMEM, AGJ_ECUDA.
  */
 int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, agj_mode mode,
@@ -322,6 +327,26 @@ int agj_join_count_timed(const agj_index* index, const double* d_points, uint64_
                          int accumulate, uint64_t* d_status, void* d_scratch, uint64_t scratch_bytes,
                          void* const events[4]);
 
+/*
+ * Training from a point stream on the device (§III-D; the paper trains
+ * offline and leaves online training to future work).  The probe kernels
+ * walk n device points (n x {lat, lng}, 16-byte aligned) and return to the
+ * host only those that land in a cell with candidate references (the
+ * "expensive" cells training refines); the host splits those cells in
+ * descending order of hits within memory_budget_bytes of trie nodes (0: four
+ * times the current trie), as agj_build's training does, re-flattens the
+ * trie and replaces the index's device copy.  Points outside the expensive
+ * cells cannot change training, so the result is the index agj_build
+ * would produce from the same polygons and these training points.  Exact
+ * mode only.  The join results do not change (exact mode), only how many
+ * candidates need the refine step.  Synchronises the device; no join on
+ * this index may be in flight.  Errors: AGJ_EINVAL (not an exact index on
+ * the device, misaligned or null points, n >= 2^32), AGJ_EDEVICE, AGJ_ENOMEM
+ * (the index then keeps no device copy), AGJ_ECUDA.
+ */
+int agj_train_online(agj_index* index, const double* d_points, uint64_t n, uint64_t memory_budget_bytes,
+                     void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* batched form (no counterpart in the paper)                               */
 /* ---------------------------------------------------------------------- */
@@ -392,34 +417,44 @@ int agj_join_batched(const agj_index* const* indexes, const double* const* d_poi
  * A request loop over resident indexes.  The paper motivates low-latency
  * joins for streaming points but measures none; this form serves many small
  * point requests by continuous batching: a scheduler thread forms a launch
- * from the requests waiting whenever one of its n_slots slots is free and
- * runs it as one batched join (see agj_batch_create) on that slot's stream
- * while other slots' launches are in flight.  Each slot owns device and
- * pinned host buffers sized at creation: a launch admits requests while
- * their points (max_step_points), output ids and work space fit the slot.
- * Each request's result is exactly what agj_join computes for its points.
- * Request points are read by the probe kernels from the client's host
- * buffer where the device can read pageable host memory (see
- * AGJ_SERVER_STAGE_POINTS), else staged; results come back through the
- * slot's pinned buffers.
+ * from the requests waiting whenever one of its n_slots slots (streams) is
+ * free and runs it as one batched join (see agj_batch_create) on that
+ * slot's stream while other slots' launches are in flight.  Each request's
+ * result is exactly what agj_join computes for its points.  Request points
+ * are read by the probe kernels from the client's host buffer where the
+ * device can read pageable host memory (see AGJ_SERVER_STAGE_POINTS), else
+ * staged; results come back through the slot's pinned buffers.
+ *
+ * Admission by device memory: the launches in flight share one device
+ * arena of hbm_budget_bytes.  A launch takes the exact bytes of its points,
+ * outputs and join work space from the arena (first fit); the scheduler
+ * takes requests from the queue head up to max_step_points /
+ * max_step_requests and cuts the launch back until it fits a free block,
+ * and when not even the head request fits it waits for a launch in flight
+ * to finish and return its block (counted in memory_waits).  Indexes are
+ * admitted against the free device memory by agj_server_add_index.
  *
  * agj_server_create: indexes (built on the current device) are borrowed and
  * must outlive the server; requests name them by position.  opts may be
- * NULL.  With hbm_budget_bytes set, fewer slots are made to fit it
- * (AGJ_EBUDGET if one slot does not fit).  Errors: AGJ_EINVAL, AGJ_EBUDGET,
- * AGJ_ENOMEM, AGJ_ECUDA.
+ * NULL.  The arena is hbm_budget_bytes, or (0) room for n_slots launches of
+ * max_step_points points, in either case no more than the device's free
+ * memory less hbm_reserve_bytes (AGJ_EBUDGET if a given budget exceeds
+ * that).  Errors: AGJ_EINVAL, AGJ_EBUDGET, AGJ_ENOMEM, AGJ_ECUDA.
  */
 typedef struct agj_server agj_server;
 typedef struct {
     uint32_t n_slots;            /* launches in flight, 0 = 4 */
     uint32_t max_step_requests;  /* requests per launch (<= 65535), 0 = 4096 */
     uint64_t max_step_points;    /* points per launch (and per request), 0 = 2^20 */
-    uint64_t hbm_budget_bytes;   /* device memory for all slots, 0 = no limit */
+    uint64_t hbm_budget_bytes;   /* device arena for the launches in flight, 0 = see above */
     uint64_t max_pending;        /* queued requests before submit answers AGJ_EBUSY, 0 = 2^20 */
     uint32_t points_per_lane;    /* as agj_batch_opts, 0 = 2 */
     uint32_t ctas_per_sm;        /* as agj_batch_opts */
     uint32_t flags;              /* AGJ_SERVER_STAGE_POINTS */
-    uint32_t reserved;
+    uint32_t max_refs;           /* largest reference list of an index added later by
+                                    agj_server_add_index (sizes the pinned id buffers);
+                                    0 = that of the indexes given at creation */
+    uint64_t hbm_reserve_bytes;  /* free device memory admission leaves untouched, 0 = 1 GiB */
 } agj_server_opts;
 /* Where the device can read pageable host memory (GB300: NVLink-C2C with
  * the host's page tables), the probe reads each request's points straight
@@ -435,10 +470,25 @@ int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const
  * ids_capacity) the result is written there and kept until
  * agj_server_poll; with both NULL the result is discarded and only counted
  * in the statistics.  *ticket names the request.  Errors: AGJ_EINVAL,
- * AGJ_ECAPACITY (n > max_step_points), AGJ_EBUSY (max_pending queued).
+ * AGJ_ECAPACITY (n > max_step_points), AGJ_EBUDGET (the request alone
+ * would not fit the arena), AGJ_EBUSY (max_pending queued).
  */
 int agj_server_submit(agj_server* server, uint32_t index_id, const double* h_points, uint64_t n,
                       uint32_t* h_offsets, uint32_t* h_ids, uint64_t ids_capacity, uint64_t* ticket);
+
+/*
+ * Admits one more index (no counterpart in the paper): an index built with
+ * host_only = 1 is uploaded to the device (becoming as if built there; it
+ * stays resident until agj_free) if its device blob fits the device's free
+ * memory less hbm_reserve_bytes, else AGJ_EBUDGET and nothing changes; an
+ * index already on the server's device is added as it is.  *index_id
+ * receives its position for agj_server_submit.  Safe while requests are in
+ * flight.  The index must outlive the server.  Errors: AGJ_EINVAL,
+ * AGJ_EBUDGET, AGJ_ECAPACITY (its largest reference list exceeds the
+ * server's max_refs), AGJ_EUNSUPPORTED (4096 indexes), AGJ_ENOMEM,
+ * AGJ_ECUDA.
+ */
+int agj_server_add_index(agj_server* server, agj_index* index, uint32_t* index_id);
 
 typedef struct {
     int32_t  status;             /* AGJ_OK, or the request's error */
@@ -458,8 +508,13 @@ typedef struct {
     uint64_t submitted, completed, rejected, points, steps, step_requests_max;
     uint32_t n_slots;
     uint32_t host_reads;         /* 1: the probe reads request points from host memory */
-    uint64_t device_bytes;       /* device memory of the slots */
+    uint64_t device_bytes;       /* the launches' device arena */
     double p50_us, p99_us, mean_us, max_us;   /* submit-to-done latency of completed requests */
+    uint64_t memory_waits;       /* times the scheduler waited for arena memory */
+    uint64_t peak_bytes_in_use;  /* largest arena use by the launches in flight */
+    uint64_t index_bytes;        /* device bytes of the indexes agj_server_add_index uploaded */
+    uint32_t n_indexes;
+    uint32_t reserved;
 } agj_server_stats;
 /* Statistics since creation or the last reset (reset != 0 clears them). */
 int agj_server_get_stats(agj_server* server, int reset, agj_server_stats* out);

@@ -73,10 +73,18 @@ int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, ag
               const agj_build_opts* opts, void* stream, agj_index** out) {
     if (!out) return AGJ_EINVAL;
     *out = nullptr;
-    if (mode != AGJ_APPROX && mode != AGJ_EXACT) return AGJ_EINVAL;
+    if (mode != AGJ_APPROX && mode != AGJ_EXACT && mode != AGJ_AUTO) return AGJ_EINVAL;
     agj_build_opts o;
     memset(&o, 0, sizeof o);
     if (opts) o = *opts;
+    if (mode == AGJ_AUTO) {
+        // §III-A: the approximate index first; if it exceeds the memory
+        // budget, the exact index, trained until the budget is spent
+        if (!o.memory_budget_bytes) return AGJ_EINVAL;
+        const int rc = agj_build(polys, n_polys, precision_m, AGJ_APPROX, &o, stream, out);
+        if (rc != AGJ_EBUDGET) return rc;
+        return agj_build(polys, n_polys, precision_m, AGJ_EXACT, &o, stream, out);
+    }
     agj::BuildParams bp;
     bp.mode = mode;
     bp.precision_m = precision_m;
@@ -266,6 +274,66 @@ int agj_join_count_timed(const agj_index* index, const double* d_points, uint64_
     }
     return agj::launch_join_count(index->X, d_points, n, as_stream(stream), d_counts, d_status, d_scratch,
                                   scratch_bytes, accumulate != 0, ev);
+}
+
+int agj_train_online(agj_index* index, const double* d_points, uint64_t n, uint64_t memory_budget_bytes,
+                     void* stream) {
+    if (!index || !index->X.d_blob || (n && !d_points)) return AGJ_EINVAL;
+    agj::Index& X = index->X;
+    if (X.mode != AGJ_EXACT || (reinterpret_cast<uintptr_t>(d_points) & 15u) != 0 || n >= 0xFFFFFFFFull)
+        return AGJ_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    std::vector<uint64_t> ids;
+    if (n) {
+        // device pass: the points that land in expensive cells
+        char* d = nullptr;
+        const uint64_t bytes = 64 + n * 8;
+        if (cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            return AGJ_ENOMEM;
+        }
+        uint64_t* d_hdr = reinterpret_cast<uint64_t*>(d);            // [0] count, [1..4] status words
+        uint64_t* d_out = reinterpret_cast<uint64_t*>(d + 64);
+        int rc = cudaMemsetAsync(d, 0, 64, s) == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+        if (rc == AGJ_OK) rc = agj::launch_collect_expensive(X, d_points, n, d_out, d_hdr, d_hdr + 1, s);
+        uint64_t hdr[5] = {0, 0, 0, 0, 0};
+        if (rc == AGJ_OK && (cudaMemcpyAsync(hdr, d, 40, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                             cudaStreamSynchronize(s) != cudaSuccess))
+            rc = AGJ_ECUDA;
+        if (rc == AGJ_OK && (hdr[2] & 4ull)) rc = AGJ_EDEVICE;
+        if (rc == AGJ_OK) {
+            ids.resize(std::min<uint64_t>(hdr[0], n));
+            if (!ids.empty() && (cudaMemcpyAsync(ids.data(), d_out, ids.size() * 8, cudaMemcpyDeviceToHost, s) !=
+                                     cudaSuccess ||
+                                 cudaStreamSynchronize(s) != cudaSuccess))
+                rc = AGJ_ECUDA;
+        }
+        cudaFreeAsync(d, s);
+        if (rc != AGJ_OK) { cudaGetLastError(); return rc; }
+    }
+    // host: split the expensive cells, re-flatten, re-upload
+    int rc;
+    try {
+        rc = agj::retrain(&X, ids.data(), ids.size(), memory_budget_bytes, 0, 0, &g_last_error);
+    } catch (const std::bad_alloc&) {
+        rc = AGJ_ENOMEM;
+    }
+    if (rc != AGJ_OK) return rc;
+    cudaStreamSynchronize(s);
+    void* old = X.d_blob;
+    X.d_blob = nullptr;
+    rc = agj::upload_index(&X, s);
+    if (rc == AGJ_ENOMEM) {          // room for one copy only: drop the old one first
+        cudaDeviceSynchronize();
+        cudaFree(old);
+        old = nullptr;
+        rc = agj::upload_index(&X, s);
+    }
+    if (old) {
+        cudaDeviceSynchronize();
+        cudaFree(old);
+    }
+    return rc;
 }
 
 int agj_measure_fp64_rate(void* stream, double* flops_per_s) {

@@ -16,7 +16,7 @@ from . import build as _build
 
 AGJ_OK, AGJ_EINVAL, AGJ_EUNSUPPORTED, AGJ_EBUDGET, AGJ_ENOMEM, AGJ_ECUDA, AGJ_ETIMEOUT, AGJ_EBUSY, \
     AGJ_ECAPACITY, AGJ_EDEVICE = range(10)
-APPROX, EXACT = 0, 1
+APPROX, EXACT, AUTO = 0, 1, 2
 
 
 class AgjError(RuntimeError):
@@ -65,7 +65,8 @@ class Requirements(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("n_slots", C.c_uint32), ("max_step_requests", C.c_uint32), ("max_step_points", C.c_uint64),
                 ("hbm_budget_bytes", C.c_uint64), ("max_pending", C.c_uint64), ("points_per_lane", C.c_uint32),
-                ("ctas_per_sm", C.c_uint32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
+                ("ctas_per_sm", C.c_uint32), ("flags", C.c_uint32), ("max_refs", C.c_uint32),
+                ("hbm_reserve_bytes", C.c_uint64)]
 
 
 class RequestResult(C.Structure):
@@ -77,7 +78,9 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
                 ("points", C.c_uint64), ("steps", C.c_uint64), ("step_requests_max", C.c_uint64),
                 ("n_slots", C.c_uint32), ("host_reads", C.c_uint32), ("device_bytes", C.c_uint64),
-                ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double)]
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double), ("max_us", C.c_double),
+                ("memory_waits", C.c_uint64), ("peak_bytes_in_use", C.c_uint64), ("index_bytes", C.c_uint64),
+                ("n_indexes", C.c_uint32), ("reserved", C.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -147,6 +150,7 @@ def lib():
             "agj_join_batched": (i32, [P, P, P, u32, P, P]),
             "agj_server_create": (i32, [P, u32, P, P]),
             "agj_server_submit": (i32, [P, u32, P, u64, P, P, u64, P]),
+            "agj_server_add_index": (i32, [P, P, P]),
             "agj_server_poll": (i32, [P, u64, i32, P]),
             "agj_server_drain": (i32, [P]),
             "agj_server_get_stats": (i32, [P, i32, P]),
@@ -157,6 +161,7 @@ def lib():
             "agj_join_count": (i32, [P, P, u64, P, P, i32, P, P, u64]),
             "agj_join_count_timed": (i32, [P, P, u64, P, P, i32, P, P, u64, P]),
             "agj_measure_fp64_rate": (i32, [P, P]),
+            "agj_train_online": (i32, [P, P, u64, u64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -214,7 +219,7 @@ class Index:
                          C.c_void_p(0) if host_only else _stream_ptr(stream), C.byref(h))
         _check(rc, "agj_build")
         self._h = h
-        self.mode = mode
+        self.mode = self.stats()["mode"]      # AUTO resolves to APPROX or EXACT
         self.precision_m = precision_m
 
     @property
@@ -415,6 +420,14 @@ def join_count(index: Index, points, counts: Counts | None = None, accumulate: b
     return counts
 
 
+def train_online(index: Index, points, budget_bytes: int = 0, stream=None) -> None:
+    """Trains an exact index from device points (agj_train_online)."""
+    import torch
+    assert points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()
+    _check(lib().agj_train_online(index.handle, C.c_void_p(points.data_ptr()), points.shape[0], int(budget_bytes),
+                                  _stream_ptr(stream)), "agj_train_online")
+
+
 def measure_fp64_rate(stream=None) -> float:
     """FP64 FMA throughput of the current device in flop/s (agj_measure_fp64_rate)."""
     r = C.c_double()
@@ -492,15 +505,23 @@ class Server:
 
     def __init__(self, indexes, n_slots: int = 0, max_step_requests: int = 0, max_step_points: int = 0,
                  hbm_budget_bytes: int = 0, max_pending: int = 0, points_per_lane: int = 0, ctas_per_sm: int = 0,
-                 stage_points: bool = False):
+                 stage_points: bool = False, max_refs: int = 0, hbm_reserve_bytes: int = 0):
         self.indexes = list(indexes)
         hs = (C.c_void_p * len(self.indexes))(*[ix.handle for ix in self.indexes])
         o = ServerOpts(n_slots, max_step_requests, max_step_points, hbm_budget_bytes, max_pending, points_per_lane,
-                       ctas_per_sm, 1 if stage_points else 0, 0)
+                       ctas_per_sm, 1 if stage_points else 0, max_refs, hbm_reserve_bytes)
         h = C.c_void_p()
         _check(lib().agj_server_create(hs, len(self.indexes), C.byref(o), C.byref(h)), "agj_server_create")
         self._h = h
         self._live = {}
+
+    def add_index(self, index: "Index") -> int:
+        """Admits an index (agj_server_add_index): a host-only index is uploaded
+        if it fits the free device memory less the reserve.  Returns its id."""
+        k = C.c_uint32()
+        _check(lib().agj_server_add_index(self._h, index.handle, C.byref(k)), "agj_server_add_index")
+        self.indexes.append(index)
+        return int(k.value)
 
     def submit(self, index_id: int, points: np.ndarray, keep: bool = True) -> int:
         """Queues a request; with keep, its CSR is returned by poll()."""

@@ -242,3 +242,25 @@ def test_host_ids_match_oracle(agj, oracle):
     pts = np.stack([lat, lng], -1)
     pts[:5] = [[np.nan, 0], [91, 0], [0, 181], [90, 180], [-90, -180]]
     assert np.array_equal(agj.cell_ids_host(pts), oracle.cell_ids(pts))
+
+
+def test_auto_mode_picks_approx_or_exact_by_budget(agj, oracle):
+    """§III-A: the approximate index when it fits the memory budget, else the
+    exact index trained within it; AUTO needs a budget."""
+    from paper_1802_09488_gb300 import synth
+    w = synth.c1_tiny(20_000)
+    ref = agj.Index(w.polygons, agj.APPROX, w.eps_m, host_only=True)
+    bytes_approx = ref.stats()["n_nodes"] * 2048 + ref.stats()["n_lut_words"] * 4
+    roomy = agj.Index(w.polygons, agj.AUTO, w.eps_m, budget_bytes=bytes_approx, host_only=True)
+    assert roomy.mode == agj.APPROX and roomy.stats()["n_cells"] == ref.stats()["n_cells"]
+    tight = agj.Index(w.polygons, agj.AUTO, w.eps_m, budget_bytes=bytes_approx - 1, train=w.points[:5000],
+                      host_only=True)
+    st = tight.stats()
+    assert tight.mode == agj.EXACT and st["n_nodes"] * 2048 <= bytes_approx
+    cells, off, refs = tight.logical()
+    rep = oracle.PolySet(w.polygons).check_covering(cells, off, refs)
+    rep.pop("cand_ref_misses")
+    assert set(rep.values()) == {0}
+    with pytest.raises(agj.AgjError) as e:
+        agj.Index(w.polygons, agj.AUTO, w.eps_m, host_only=True)
+    assert e.value.status == 1
