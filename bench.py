@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    ap.add_argument("--extras", default="count,cellid,c1",
+                    help="comma list of extra measurements: count (aggregation mode), cellid (the FP64 cell-id "
+                         "kernel), c1 (1000 tiny joins in one graph); empty for none")
     ap.add_argument("--workload", choices=["c2", "c3", "c1"], default="c2",
                     help="c2: city (default); c3: 40 000 fine overlapping polygons; c1: 5 polygons, uniform points")
     ap.add_argument("--eps", type=float, default=None, help="approximate precision in metres (default per workload)")
@@ -176,6 +179,121 @@ def served_form(agj) -> dict:
             "speedup_points_per_s_vs_plain": r["points_per_s"] / max(p["points_per_s"], 1e-9),
             "capacity_vs_plain": sat["points_per_s"] / max(p["points_per_s"], 1e-9),
             "index_device_bytes": sum(ix.stats()["device_bytes"] for ix in idx), "prep_s": prep_s}
+
+
+def _event(torch, stream):
+    """A timing event whose CUDA handle exists (torch creates it on the first
+    record), so that the library can record it."""
+    e = torch.cuda.Event(enable_timing=True)
+    e.record(stream)
+    return e
+
+
+def count_mode(agj, torch, ia, ie, d_pts, n, peaks, steps) -> dict:
+    """Aggregation mode (count(*) group by polygon, §V) on the same resident
+    points and indexes: per-mode points/s and the count probe's roofline
+    (16 B point + 8 B per trie entry read; no per-point output)."""
+    import numpy as np
+    s = torch.cuda.current_stream()
+    out = {}
+    for name, ix in (("approx", ia), ("exact", ie)):
+        c = agj.join_count(ix, d_pts)
+        c.to_host()
+        evs = [[_event(torch, s) for _ in range(4)] for _ in range(max(steps, 3))]
+        for ev in evs:
+            agj.join_count(ix, d_pts, c, events=ev)
+        torch.cuda.synchronize()
+        counts = c.to_host()
+        st = c.status.cpu().numpy().view(np.uint64)
+        total = [ev[0].elapsed_time(ev[3]) for ev in evs]
+        probe = [ev[0].elapsed_time(ev[1]) for ev in evs]
+        g = float(st[3]) / n
+        bpp = 16 + 8 * g
+        tp = statistics.mean(probe)
+        out[name] = {"points_per_s": n / (statistics.mean(total) / 1e3), "ms": statistics.mean(total),
+                     "probe_ms": tp, "pairs_counted": int(st[0]), "polygons_nonzero": int((counts > 0).sum()),
+                     "trie_entries_read_per_point": g,
+                     "roofline_probe": {"kernel": f"k_agg_probe_{name}", "bound": "hbm",
+                                        "achieved": bpp * n / (tp / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                                        "unit": "GB/s", "frac": bpp * n / (tp / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                        "algorithmic_bytes_per_point": bpp, "peak_source": peaks["source"]}}
+    return out
+
+
+# FP64 operations per point of the cell-id kernel at source level
+# (agj_geom.cuh): two sin/cos of degrees (reduction 4, Horner 14 + 16,
+# assembly 5, squares 1: 40 each), the xyz products (2), two divisions for
+# (u, v), two quadratic st transforms (4-5 each: 9 on this site's face,
+# one coordinate negative), two scalings before the floors (2).  Each
+# division and square root counts once here, although the GPU expands
+# them into several FP64 instructions.
+CELL_ID_FP64_OPS = 95
+
+
+def cell_id_kernel(agj, torch, d_pts, n) -> dict:
+    """k_cell_ids (the FP64 spec path, bit-exact ids) on the resident points,
+    reported against the device's FP64 rate measured by the library's own
+    FMA microbenchmark."""
+    ids = torch.empty(n, dtype=torch.int64, device="cuda")
+    agj.cell_ids(d_pts, out=ids)
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        agj.cell_ids(d_pts, out=ids)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    del ids
+    fp64 = agj.measure_fp64_rate()
+    ms = statistics.median(ts)
+    achieved = CELL_ID_FP64_OPS * n / (ms / 1e3)
+    return {"kernel": "k_cell_ids", "ms": ms, "points_per_s": n / (ms / 1e3), "bound": "fp64",
+            "fp64_ops_per_point": CELL_ID_FP64_OPS, "achieved_tflops": achieved / 1e12,
+            "peak_tflops": fp64 / 1e12, "frac": achieved / fp64,
+            "peak_source": "measured by agj_measure_fp64_rate (own FMA-chain kernel, 2 flops per FMA)",
+            "note": "divisions and square roots counted as one operation each"}
+
+
+def c1_amortized(agj, torch, peaks, joins: int = 1000) -> dict:
+    """Config 1 (5 polygons, 1e5 points) is launch-bound as single joins; this
+    captures `joins` back-to-back approximate joins in one CUDA graph and
+    reports the amortized time per join against the method's bytes."""
+    import numpy as np
+    from paper_1802_09488_gb300 import synth
+    w = synth.c1_tiny(100_000)
+    ix = agj.Index(w.polygons, agj.APPROX, w.eps_m)
+    d = torch.from_numpy(w.points).cuda()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        pr = agj.join(ix, d)
+        pr.check()
+        st = pr.status.cpu().numpy().view(np.uint64)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(joins):
+                agj.join(ix, d, pr)
+        g.replay()
+        s.synchronize()
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            g.replay()
+            b.record(s)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        nnz = pr.check(stream=s)
+    ms = min(ts) / joins
+    n = len(w.points)
+    bpp = 16 + 8 * float(st[3]) / n + 4 + 4 * nnz / n
+    ach = bpp * n / (ms / 1e3) / 1e9
+    return {"workload": "c1-tiny-5polys-uniform-points-1e05, approx eps 10 m", "joins_in_graph": joins,
+            "ms_per_join": ms, "points_per_s": n / (ms / 1e3),
+            "roofline_join": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_point": bpp,
+                              "note": "inputs (1.6 MB) stay in L2 across the graph's joins: a warm-cache figure"}}
 
 
 class ClockSampler:
@@ -408,7 +526,8 @@ def main():
     nnz_a, nnz_e = pa.check(), pe.check()
     st_a = pa.status.cpu().numpy().view(np.uint64)
     st_e = pe.status.cpu().numpy().view(np.uint64)
-    gathers_per_pt = float(st_a[3]) / n
+    gathers_a = float(st_a[3]) / n          # trie entries read per point, approximate index
+    gathers_e = float(st_e[3]) / n          # ... exact (trained) index
     cands_per_pt = float(st_e[2]) / n
     fallback_a, fallback_e = pa.fallbacks(), pe.fallbacks()
     refine_fb = pe.refine_fallbacks()
@@ -473,12 +592,14 @@ def main():
 
     t_pa = mean(stages["approx"]["k_probe_approx"])
     t_pe = mean(stages["exact"]["k_probe_exact"])
-    r_pa = roof("k_probe_approx", 16 + 8 * gathers_per_pt + 8, t_pa,
-                "16 B point + 8 B per trie entry read + 8 B entry written, per point")
-    r_pe = roof("k_probe_exact", 16 + 8 * gathers_per_pt + 8 + 8 * cands_per_pt, t_pe,
-                "16 B point + 8 B per trie entry read + 8 B entry + 8 B per candidate queued, per point")
+    r_pa = roof("k_probe_approx", 16 + 8 * gathers_a, t_pa,
+                f"the method's bytes per point: 16 B point + 8 B per trie entry read (G = {gathers_a:.3f}, this "
+                f"join's own counter); the stored entry is the pipeline's intermediate and not counted")
+    r_pe = roof("k_probe_exact", 16 + 8 * gathers_e + 8 * cands_per_pt, t_pe,
+                f"16 B point + 8 B per trie entry read (G = {gathers_e:.3f}, the exact index's own counter) + 8 B "
+                f"per candidate queued, per point")
     roofline = r_pa if t_pa >= t_pe else r_pe
-    join_roof = roof("approx join (probe + scan + emit)", 16 + 8 * gathers_per_pt + 4 + 4 * k_pts, mean(approx_ms),
+    join_roof = roof("approx join (probe + scan + emit)", 16 + 8 * gathers_a + 4 + 4 * k_pts, mean(approx_ms),
                      "the method's bytes: 16 B point + 8 B per trie entry + 4 B offset + 4 B per pair")
 
     def pct(v, q):
@@ -495,10 +616,11 @@ def main():
                                 "host enqueue fell behind the device: timings include host launch gaps")),
         "modes": {
             "approx": {"points_per_s": n / (statistics.mean(approx_ms) / 1000.0), "p50_ms": pct(approx_ms, 50),
-                       "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_per_pt,
+                       "p99_ms": pct(approx_ms, 99), "nnz": nnz_a, "trie_entries_read_per_point": gathers_a,
                        "fp64_id_fallbacks": fallback_a},
             "exact": {"points_per_s": n / (statistics.mean(exact_ms) / 1000.0), "p50_ms": pct(exact_ms, 50),
                       "p99_ms": pct(exact_ms, 99), "nnz": nnz_e, "candidates_per_point": cands_per_pt,
+                      "trie_entries_read_per_point": gathers_e,
                       "fp64_id_fallbacks": fallback_e, "fp64_refine_fallbacks": refine_fb},
         },
         "index": {"approx": ia.stats(), "exact": ie.stats(), "build_s": build_s},
@@ -509,6 +631,15 @@ def main():
         "clocks": clk,
         "gpu_launches": args.steps * (LAUNCHES_PER_STEP["approx"] + LAUNCHES_PER_STEP["exact"]),
     }
+
+    extras = set(x for x in args.extras.split(",") if x)
+    if "count" in extras:
+        result["count"] = count_mode(agj, torch, ia, ie, d_pts, n, peaks, args.steps)
+    if "cellid" in extras:
+        result["cell_id_kernel"] = cell_id_kernel(agj, torch, d_pts, n)
+        torch.cuda.empty_cache()
+    if "c1" in extras and rank == 0 and args.workload == "c2":
+        result["c1_amortized_in_graph"] = c1_amortized(agj, torch, peaks)
 
     if not args.no_e2e:
         # end to end through the public host API: pinned host points in,

@@ -503,10 +503,14 @@ uint64_t count_nodes(const std::vector<uint64_t>& cells, const FacePrefix fp[6])
 // training (§III-D)
 // ---------------------------------------------------------------------------
 
-void train(const std::vector<Poly>& polys, std::vector<uint64_t>* cells, std::vector<Refs>* refs, const double* pts,
-           uint64_t n_pts, uint64_t budget_bytes, int max_level, unsigned threads) {
-    std::vector<uint64_t> pid(n_pts);
-    parallel_for(n_pts, threads, [&](size_t k, unsigned) { pid[k] = point_cell_id(pts[2 * k], pts[2 * k + 1]); });
+// Training from the training points' leaf cell ids (pid, kInvalidId for an
+// invalid point): passes of hit counting on expensive cells (those with a
+// candidate reference, below max_level) and splits in descending hit
+// count, ties by cell id, until the node budget is spent or no expensive
+// cell is hit.
+void train_ids(const std::vector<Poly>& polys, std::vector<uint64_t>* cells, std::vector<Refs>* refs,
+               const std::vector<uint64_t>& pid, uint64_t budget_bytes, int max_level, unsigned threads) {
+    const uint64_t n_pts = pid.size();
     FacePrefix fp[6];
     face_prefixes(*cells, fp);
     std::unordered_set<uint64_t> node_keys;
@@ -577,6 +581,13 @@ void train(const std::vector<Poly>& polys, std::vector<uint64_t>* cells, std::ve
         cells->swap(nc);
         refs->swap(nr);
     }
+}
+
+void train(const std::vector<Poly>& polys, std::vector<uint64_t>* cells, std::vector<Refs>* refs, const double* pts,
+           uint64_t n_pts, uint64_t budget_bytes, int max_level, unsigned threads) {
+    std::vector<uint64_t> pid(n_pts);
+    parallel_for(n_pts, threads, [&](size_t k, unsigned) { pid[k] = point_cell_id(pts[2 * k], pts[2 * k + 1]); });
+    train_ids(polys, cells, refs, pid, budget_bytes, max_level, threads);
 }
 
 // ---------------------------------------------------------------------------
@@ -831,6 +842,44 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
     X.stats.mode = (uint32_t)bp.mode;
     X.stats.n_polys = n_polys;
     X.stats.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return AGJ_OK;
+}
+
+int retrain(Index* X, const uint64_t* ids, uint64_t n_ids, uint64_t budget, uint32_t max_level, unsigned threads,
+            std::string* err) {
+    if (X->mode != AGJ_EXACT) { *err = "training refines exact-mode indexes"; return AGJ_EINVAL; }
+    threads = threads ? threads : std::max(1u, std::thread::hardware_concurrency());
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<Poly> P(X->n_polys);
+    for (uint32_t k = 0; k < X->n_polys; ++k) {
+        const double* bb = &X->poly_bbox[4 * k];
+        P[k] = Poly{X->poly_face[k], &X->poly_uv[2 * X->poly_off[k]], X->poly_off[k + 1] - X->poly_off[k],
+                    {bb[0], bb[1], bb[2], bb[3]}};
+    }
+    std::vector<uint64_t> cells = X->cells;
+    std::vector<Refs> refs(cells.size());
+    for (size_t k = 0; k < cells.size(); ++k)
+        refs[k].assign(X->refs.begin() + X->ref_off[k], X->refs.begin() + X->ref_off[k + 1]);
+    if (!budget) {
+        FacePrefix fp[6];
+        face_prefixes(cells, fp);
+        const uint64_t now = count_nodes(cells, fp) * (uint64_t)kNodeEntries * 8;
+        budget = std::max<uint64_t>(4 * now, now + (16ull << 20));
+    }
+    train_ids(P, &cells, &refs, std::vector<uint64_t>(ids, ids + n_ids), budget, (int)(max_level ? max_level : 24),
+              threads);
+    X->cells = std::move(cells);
+    X->ref_off.assign(X->cells.size() + 1, 0);
+    for (size_t k = 0; k < refs.size(); ++k) X->ref_off[k + 1] = X->ref_off[k] + refs[k].size();
+    X->refs.clear();
+    X->refs.reserve(X->ref_off.back());
+    for (auto& r : refs) X->refs.insert(X->refs.end(), r.begin(), r.end());
+    const int rc = flatten(X, err);
+    if (rc != AGJ_OK) return rc;
+    if (X->model.enabled) fit_fast_model(X, threads);
+    X->stats.fast_ids = (uint32_t)X->model.enabled;
+    X->stats.fast_err_cells = X->model.enabled ? (double)X->model.err : 0.0;
+    X->stats.build_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return AGJ_OK;
 }
 

@@ -88,6 +88,13 @@ struct BuildParams {
 int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp, Index* out,
                std::string* err_msg);
 
+// Training (§III-D) of an exact index from the leaf cell ids of training
+// points: splits its expensive cells within `budget` node bytes (0: 4x the
+// current trie) down to max_level (0: 24), then re-flattens the trie and
+// re-fits the fast cell-id model.  Host only; the device copy is not touched.
+int retrain(Index* X, const uint64_t* ids, uint64_t n_ids, uint64_t budget, uint32_t max_level, unsigned threads,
+            std::string* err);
+
 // Fits idx->model (the certified fast cell-id model) for the index's cells;
 // leaves it disabled when the cells span faces or too wide a window.
 void fit_fast_model(Index* idx, unsigned threads);

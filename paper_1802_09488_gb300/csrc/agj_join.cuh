@@ -35,7 +35,7 @@ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 //   queue (a region of tile_slots per tile), its pass bytes, its polygon
 //   order, the per-polygon cursors and the refine chunk descriptors
 struct JoinLayout {
-    uint64_t chunks = 0, pchunks = 0, pcount = 0, zero_end = 0;
+    uint64_t chunks = 0, pchunks = 0, pcount = 0, stripes = 0, zero_end = 0;
     uint64_t entries = 0, tcount = 0, tprefix = 0;
     uint64_t tcand = 0, queue = 0, pass = 0, sorted = 0, cursor = 0, cpoly = 0, total = 0;
     uint64_t n_points = 0, n_tiles = 0, n_chunks = 0, n_pchunks = 0, queue_cap = 0, n_polys = 0;
@@ -52,9 +52,11 @@ constexpr uint64_t kPolyScanPerCta = 256 * 4;
 // the tile space; exact: some job refines; tile_slots: queue slots per tile;
 // n_polys: polygons of the exact jobs.  count: the aggregation mode's work
 // space, which holds no per-point entries, tile counts, prefixes or pass
-// bytes (those offsets stay 0 and are not used).
+// bytes (those offsets stay 0 and are not used), and with n_hist_polys
+// (polygons counted in shared memory) the zeroed striped histograms.
+constexpr uint32_t kAggStripes = 64;
 inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, uint32_t tile_slots, uint64_t n_polys,
-                              bool count = false) {
+                              bool count = false, uint64_t n_hist_polys = 0) {
     JoinLayout L;
     L.n_points = n_points;
     L.n_tiles = n_tiles;
@@ -72,6 +74,11 @@ inline JoinLayout join_layout(uint64_t n_points, uint64_t n_tiles, bool exact, u
         o += align256(std::max<uint64_t>(L.n_pchunks, 1) * 8);
         L.pcount = o;
         o += align256(n_polys * 4 + 4);
+    }
+    if (count && n_hist_polys) {
+        // aggregation mode: kAggStripes striped u32 copies of the histogram
+        L.stripes = o;
+        o += align256((uint64_t)kAggStripes * n_hist_polys * 4);
     }
     L.zero_end = o;
     if (!count) {

@@ -276,15 +276,20 @@ __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ queue
 constexpr uint32_t kAggSmemPolys = 4096;       // polygons counted in shared memory (16 KB)
 constexpr uint32_t kNoPoly = 0xFFFFFFFFu;
 
-// One atomic per distinct polygon among the warp's lanes (kNoPoly: none).
+// With the global counts (many polygons), one atomic per distinct polygon
+// among the warp's lanes (kNoPoly: none); with the shared histogram, one
+// shared atomic per lane (lanes on the same polygon are serialised by the
+// shared-memory unit, which is cheaper than finding them).
 __device__ __forceinline__ void agg_add_warp(uint32_t poly, uint32_t* s_hist, uint64_t* counts) {
+    if (s_hist) {
+        if (poly != kNoPoly) atomicAdd(&s_hist[poly], 1u);
+        return;
+    }
     const uint32_t active = __ballot_sync(kFull, poly != kNoPoly);
     if (poly == kNoPoly) return;
     const uint32_t peers = __match_any_sync(active, poly);
-    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) {
-        if (s_hist) atomicAdd(&s_hist[poly], (uint32_t)__popc(peers));
-        else atomicAdd((unsigned long long*)&counts[poly], (unsigned long long)__popc(peers));
-    }
+    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1))
+        atomicAdd((unsigned long long*)&counts[poly], (unsigned long long)__popc(peers));
 }
 
 __device__ __forceinline__ void agg_add_lane(uint32_t poly, uint32_t* s_hist, uint64_t* counts) {
@@ -323,13 +328,21 @@ __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces,
         *pairs += exact ? nt : nt + nc[k];
         csum += exact ? nc[k] : 0u;
         const uint32_t tag = (uint32_t)(e[k] & 3ull);
-        // one or two inline references: warp-combined adds
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        // one or two inline references (the second round only when a lane
+        // of the warp holds two)
+        {
             uint32_t poly = kNoPoly;
-            if ((tag == 1 && r == 0) || tag == 2) {
-                const uint32_t pl = payload_of(e[k], r);
+            if (tag == 1 || tag == 2) {
+                const uint32_t pl = payload_of(e[k], 0);
                 if (pl != kInvalidPayloadDev && (!exact || (pl & 1u))) poly = pl >> 1;
+            }
+            agg_add_warp(poly, s_hist, counts);
+        }
+        if (__any_sync(kFull, tag == 2)) {
+            uint32_t poly = kNoPoly;
+            if (tag == 2) {
+                const uint32_t pl = payload_of(e[k], 1);
+                if (!exact || (pl & 1u)) poly = pl >> 1;
             }
             agg_add_warp(poly, s_hist, counts);
         }
@@ -347,42 +360,116 @@ __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces,
     if constexpr (exact) queue_tile<PPT>(J, e, nc, csum, wt, base, 0, S);
 }
 
-// Persistent CTAs stride over the warp tiles (a warp takes every
-// (gridDim.x x 8)-th tile, no CTA barrier between tiles); each CTA keeps
-// its histogram (n_polys <= kAggSmemPolys, else the global counts directly)
-// and its warps' totals until the end.
-#ifndef AGJ_AGG_PROBE_MIN_BLOCKS
-#define AGJ_AGG_PROBE_MIN_BLOCKS 4      // 64 registers: the aggregation's extra state spills at 40-48
-#endif
+// One warp per tile, eight tiles per CTA (the plain probe's grid).  With
+// n_polys <= kAggSmemPolys the CTA counts into a shared histogram and, at
+// its end, adds the non-zero counters to one of kAggStripes striped global
+// copies (the CTA's block index picks it, spreading the atomics over the
+// L2); k_agg_reduce sums the stripes.  With more polygons the warps add to
+// the global counts directly.  Pair, trie-entry and fallback totals go
+// through shared counters, one global atomic each per CTA.
 template <int PPT, int MODE>
-__global__ void __launch_bounds__(kJoinBlock, AGJ_AGG_PROBE_MIN_BLOCKS)
-    k_agg_probe(const JobDesc J, uint64_t T, const JoinScratch S, uint64_t* __restrict__ counts) {
+__global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_PROBE_MIN_BLOCKS : AGJ_PROBE_MIN_BLOCKS)
+    k_agg_probe(const JobDesc J, uint64_t T, const JoinScratch S, uint64_t* __restrict__ counts,
+                uint32_t* __restrict__ stripes) {
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
     __shared__ uint32_t s_hist[kAggSmemPolys];
-    const bool smem = J.X.n_polys <= kAggSmemPolys;
+    __shared__ uint32_t s_tot[3];
+    const bool smem = stripes != nullptr;
+    const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
     if (smem)
         for (uint32_t p = threadIdx.x; p < J.X.n_polys; p += blockDim.x) s_hist[p] = 0;
-    const uint64_t* s_root = cta_setup(&J.X, s_hlut, s_faces, s_rootbuf);
+    if (threadIdx.x < 3) s_tot[threadIdx.x] = 0;
+    cp_async_wait_all();
     __syncthreads();
-    uint32_t pairs = 0, gathers = 0, fallbacks = 0;
-    const uint64_t stride = (uint64_t)gridDim.x * kWarpsPerBlock;
-    for (uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); wt < T; wt += stride)
+    const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (wt < T) {
+        uint32_t pairs = 0, gathers = 0, fallbacks = 0;
         agg_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, S, smem ? s_hist : nullptr, counts, &pairs, &gathers,
                             &fallbacks);
-    // every warp of the CTA runs the same number of reductions here
-    const uint32_t wp = __reduce_add_sync(kFull, pairs), wg = __reduce_add_sync(kFull, gathers),
-                   wf = __reduce_add_sync(kFull, fallbacks);
-    if ((threadIdx.x & 31) == 0) {
-        if (wp) atomicAdd((unsigned long long*)&J.status[0], (unsigned long long)wp);
-        if (wg) atomicAdd((unsigned long long*)&J.status[3], (unsigned long long)wg);
-        if (wf) atomicAdd((unsigned long long*)&J.counters[0], (unsigned long long)wf);
+        const uint32_t wp = __reduce_add_sync(kFull, pairs), wg = __reduce_add_sync(kFull, gathers),
+                       wf = __reduce_add_sync(kFull, fallbacks);
+        if ((threadIdx.x & 31) == 0) {
+            if (wp) atomicAdd(&s_tot[0], wp);
+            if (wg) atomicAdd(&s_tot[1], wg);
+            if (wf) atomicAdd(&s_tot[2], wf);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_tot[0]) atomicAdd((unsigned long long*)&J.status[0], (unsigned long long)s_tot[0]);
+        if (s_tot[1]) atomicAdd((unsigned long long*)&J.status[3], (unsigned long long)s_tot[1]);
+        if (s_tot[2]) atomicAdd((unsigned long long*)&J.counters[0], (unsigned long long)s_tot[2]);
     }
     if (smem) {
-        __syncthreads();
+        uint32_t* stripe = stripes + (uint64_t)(blockIdx.x % kAggStripes) * J.X.n_polys;
         for (uint32_t p = threadIdx.x; p < J.X.n_polys; p += blockDim.x)
-            if (s_hist[p]) atomicAdd((unsigned long long*)&counts[p], (unsigned long long)s_hist[p]);
+            if (s_hist[p]) atomicAdd(&stripe[p], s_hist[p]);
+    }
+}
+
+// counts[p] += the sum of the stripes' counters of polygon p.
+__global__ void __launch_bounds__(256) k_agg_reduce(const uint32_t* __restrict__ stripes, uint32_t n_polys,
+                                                    uint64_t* __restrict__ counts) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_polys) return;
+    uint64_t s = 0;
+    for (uint32_t k = 0; k < kAggStripes; ++k) s += stripes[(uint64_t)k * n_polys + p];
+    if (s) counts[p] += s;
+}
+
+// ---------------------------------------------------------------------------
+// online training: the device pass
+// ---------------------------------------------------------------------------
+// Training (§III-D) splits the cells that hold candidate references, in the
+// order of how many training points hit them.  Only points inside such
+// cells can hit one in any pass (splitting a cell partitions its points), so
+// the device walks the whole stream and hands the host just those points'
+// FP64 leaf ids (the spec the host trainer uses), compacted by warp ballot
+// with one atomic per warp and point slot.
+__global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
+    k_collect_expensive(const JobDesc J, uint64_t T, uint64_t* __restrict__ out,
+                        unsigned long long* __restrict__ count, uint64_t cap) {
+    __shared__ __align__(16) uint16_t s_hlut[1024];
+    __shared__ __align__(16) uint64_t s_rootbuf[256];
+    __shared__ DevFace s_faces[6];
+    const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const bool active = wt < T;
+    const uint64_t base = wt * (32 * kJoinPPT);
+    PointIJ pij[kJoinPPT];
+    bool ok[kJoinPPT];
+#pragma unroll
+    for (int k = 0; k < kJoinPPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        ok[k] = false;
+        if (active && p < J.n) {
+            const double2 q = __ldcs(J.pts + p);
+            ok[k] = point_ij(J.X.model, q.x, q.y, false, pij[k]);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (!active) return;
+    uint64_t e[kJoinPPT];
+    uint32_t fallbacks = 0;
+    probe_cells<kJoinPPT>(J.X, s_faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], &fallbacks);
+#pragma unroll
+    for (int k = 0; k < kJoinPPT; ++k) {
+        uint32_t nt, nc;
+        entry_counts(J.X, e[k], &nt, &nc);
+        const uint32_t mask = __ballot_sync(kFull, nc > 0);
+        if (!mask) continue;
+        unsigned long long o = 0;
+        if (lane == 0) o = atomicAdd(count, (unsigned long long)__popc(mask));
+        o = __shfl_sync(kFull, o, 0);
+        if (nc > 0) {
+            const uint64_t idx = o + __popc(mask & ((1u << lane) - 1u));
+            const double2 q = J.pts[base + lane + 32 * k];
+            if (idx < cap) out[idx] = point_cell_id(q.x, q.y);
+        }
     }
 }
 
@@ -492,20 +579,43 @@ DevIndex make_dev_index(const Index& X) {
     return D;
 }
 
+namespace {
+
+// Byte offsets of the sections of an index's device blob (256-byte aligned).
+struct BlobLayout {
+    uint64_t nodes, lut, uv, vkey, ukey, poff, bbox, face, plocal, pluv, pband, total;
+};
+
+BlobLayout blob_layout(const Index& X) {
+    const uint64_t nv = X.poly_off.empty() ? 0 : X.poly_off.back();
+    BlobLayout B;
+    uint64_t o = 0;
+    B.nodes = o; o += align256(X.nodes.size() * 8 + 8);
+    B.lut = o; o += align256(X.lut.size() * 4 + 4);
+    B.uv = o; o += align256(nv * 16 + 16);
+    B.vkey = o; o += align256(nv * 8 + 8);
+    B.ukey = o; o += align256(nv * 8 + 8);
+    B.poff = o; o += align256(X.poly_off.size() * 4 + 4);
+    B.bbox = o; o += align256((uint64_t)X.n_polys * 32 + 32);
+    B.face = o; o += align256((uint64_t)X.n_polys + 1);
+    B.plocal = o; o += align256((uint64_t)X.n_polys * sizeof(PolyLocal) + 16);
+    B.pluv = o; o += align256(nv * sizeof(F2) + 16);
+    B.pband = o; o += align256(X.poly_band.size() * 2 + 16);
+    B.total = o;
+    return B;
+}
+
+}  // namespace
+
+uint64_t index_device_bytes(const Index& X) { return blob_layout(X).total; }
+
 int upload_index(Index* X, cudaStream_t s) {
     const uint64_t nv = X->poly_off.empty() ? 0 : X->poly_off.back();
-    uint64_t o = 0;
-    X->off_nodes = o; o += align256(X->nodes.size() * 8 + 8);
-    X->off_lut = o; o += align256(X->lut.size() * 4 + 4);
-    X->off_uv = o; o += align256(nv * 16 + 16);
-    X->off_vkey = o; o += align256(nv * 8 + 8);
-    X->off_ukey = o; o += align256(nv * 8 + 8);
-    X->off_poff = o; o += align256(X->poly_off.size() * 4 + 4);
-    X->off_bbox = o; o += align256((uint64_t)X->n_polys * 32 + 32);
-    X->off_face = o; o += align256((uint64_t)X->n_polys + 1);
-    X->off_plocal = o; o += align256((uint64_t)X->n_polys * sizeof(PolyLocal) + 16);
-    X->off_pluv = o; o += align256(nv * sizeof(F2) + 16);
-    X->off_pband = o; o += align256(X->poly_band.size() * 2 + 16);
+    const BlobLayout B = blob_layout(*X);
+    X->off_nodes = B.nodes; X->off_lut = B.lut; X->off_uv = B.uv; X->off_vkey = B.vkey; X->off_ukey = B.ukey;
+    X->off_poff = B.poff; X->off_bbox = B.bbox; X->off_face = B.face; X->off_plocal = B.plocal;
+    X->off_pluv = B.pluv; X->off_pband = B.pband;
+    const uint64_t o = B.total;
     X->blob_bytes = o;
     std::vector<unsigned char> host(o, 0);
     auto put = [&](uint64_t off, const void* src, size_t bytes) {
@@ -617,7 +727,7 @@ JoinLayout count_layout(const Index& X, uint64_t n) {
     const bool exact = X.mode == AGJ_EXACT;
     return join_layout(tiles * 32 * kJoinPPT, tiles, exact,
                        exact ? 32u * kJoinPPT * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
-                       exact ? X.n_polys : 0, true);
+                       exact ? X.n_polys : 0, true, X.n_polys <= kAggSmemPolys ? X.n_polys : 0);
 }
 
 }  // namespace
@@ -655,12 +765,13 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
     none.status = d_status;
     const JobDesc J = make_job(X, d_points, n, &none, reinterpret_cast<uint64_t*>(sc) + kHdrIdFallbacks);
     const bool exact = X.mode == AGJ_EXACT;
+    uint32_t* stripes = L.stripes ? reinterpret_cast<uint32_t*>(sc + L.stripes) : nullptr;
     if (L.n_tiles) {
-        const uint64_t ctas = (L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        const int per_sm = AGJ_AGG_PROBE_MIN_BLOCKS;
-        const int grid = (int)std::min<uint64_t>(ctas, (uint64_t)sms * per_sm);
-        if (exact) k_agg_probe<kJoinPPT, kModeExact><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts);
-        else k_agg_probe<kJoinPPT, kModeApprox><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts);
+        const int grid = (int)((L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        if (exact) k_agg_probe<kJoinPPT, kModeExact><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
+        else k_agg_probe<kJoinPPT, kModeApprox><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
+        if (stripes)
+            k_agg_reduce<<<(X.n_polys + 255) / 256, 256, 0, s>>>(stripes, X.n_polys, d_counts);
     }
     mark(1);
     if (exact && L.n_tiles && L.n_polys) {
@@ -684,6 +795,19 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
     }
     mark(2);
     mark(3);
+    return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+}
+
+int launch_collect_expensive(const Index& X, const double* d_points, uint64_t n, uint64_t* d_out,
+                             uint64_t* d_count, uint64_t* d_status, cudaStream_t s) {
+    if (n == 0) return AGJ_OK;
+    const uint64_t tiles = (n + 32 * kJoinPPT - 1) / (32 * kJoinPPT);
+    agj_pairs none;
+    memset(&none, 0, sizeof none);
+    none.status = d_status;
+    const JobDesc J = make_job(X, d_points, n, &none, d_status + 2);    // diagnostics land in status[2..3]
+    k_collect_expensive<<<(unsigned)((tiles + kWarpsPerBlock - 1) / kWarpsPerBlock), kJoinBlock, 0, s>>>(
+        J, tiles, d_out, reinterpret_cast<unsigned long long*>(d_count), n);
     return cudaGetLastError() == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
 

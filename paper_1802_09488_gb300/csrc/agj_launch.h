@@ -9,6 +9,8 @@ namespace agj {
 
 // Copies the flattened index and the polygons to one device allocation.
 int upload_index(Index* X, cudaStream_t s);
+// Size of that allocation (what upload_index would take).
+uint64_t index_device_bytes(const Index& X);
 int join_requirements(const Index& X, uint64_t n, agj_requirements* r);
 // events: null, or 4 events recorded at the stage boundaries (see agj_join_timed).
 int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, agj_pairs* out,
@@ -23,6 +25,12 @@ uint64_t count_scratch_bytes(const Index& X, uint64_t n);
 int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, uint64_t* d_counts,
                       uint64_t* d_status, void* scratch, uint64_t scratch_bytes, bool accumulate,
                       cudaEvent_t const* events = nullptr);
+// Online training's device pass: the FP64 leaf ids of the points (n, device)
+// whose cell holds a candidate reference go to d_out[0 .. *d_count) (d_out
+// holds n ids; *d_count must start at 0; d_status: 4 zeroed words whose [1]
+// collects device-side error bits).
+int launch_collect_expensive(const Index& X, const double* d_points, uint64_t n, uint64_t* d_out,
+                             uint64_t* d_count, uint64_t* d_status, cudaStream_t s);
 // FP64 fused multiply-add throughput of the current device (flop/s), from
 // an own kernel of independent FMA chains timed with events (synchronises).
 int measure_fp64_rate(cudaStream_t s, double* flops_per_s);

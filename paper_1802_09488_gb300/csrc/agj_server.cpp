@@ -4,11 +4,16 @@
 // points) requests at any time; a scheduler thread forms a launch ("step")
 // from the requests waiting whenever one of its slots is free, and runs it
 // as one batched join (step_enqueue) on that slot's stream while the other
-// slots' steps are in flight.  A slot owns fixed device and pinned host
-// buffers sized at creation (admission: a step takes requests while their
-// points, output ids and work space fit the slot), so no allocation happens
-// per request.  Results land in the client's host buffers with submit,
-// start and completion times.
+// slots' steps are in flight.  Admission is by device memory: the steps in
+// flight share one device arena (a first-fit free list over a single
+// allocation, sized to the HBM budget), each step taking exactly the bytes
+// of its points, outputs and work space; a step that does not fit waits for
+// earlier steps to return theirs.  Indexes are admitted against the free
+// device memory (agj_server_add_index uploads a host-built index when it
+// fits, leaving a reserve).  A slot's pinned host buffers are sized at
+// creation for the largest step, so no allocation happens per request.
+// Results land in the client's host buffers with submit, start and
+// completion times.
 //
 // Also here: a Poisson load generator for the served form and the same
 // arrivals served by one plain join per request, for comparison.
@@ -21,6 +26,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <random>
@@ -43,6 +49,8 @@ uint64_t now_ns() {
 
 uint64_t round256(uint64_t x) { return (x + 255) & ~255ull; }
 
+constexpr uint32_t kMaxServerIndexes = 4096;
+
 struct Request {
     uint64_t ticket = 0;
     uint32_t index_id = 0;
@@ -59,7 +67,9 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    char* d_mem = nullptr;         // [points][offsets][status][ids][work]
+    // the running step's block of the device arena: [points][offsets][status][ids][work]
+    char* d_mem = nullptr;
+    uint64_t block = 0, block_bytes = 0;
     uint64_t off_pts = 0, off_off = 0, off_status = 0, off_ids = 0, off_work = 0, work_bytes = 0;
     char* h_mem = nullptr;         // pinned: [points][offsets][status][ids][tables]
     uint64_t h_off_pts = 0, h_off_off = 0, h_off_status = 0, h_off_ids = 0, h_off_stage = 0, stage_bytes = 0;
@@ -72,14 +82,21 @@ struct Slot {
 }  // namespace
 
 struct agj_server {
-    std::vector<const agj::Index*> X;
+    std::vector<const agj::Index*> X;   // capacity reserved at creation: never reallocated
     int device = 0;
     int ppt = 2, ctas = 0;
     bool host_reads = false;       // kernels read request points from host memory
-    uint32_t n_slots = 4, max_req = 4096;
+    uint32_t n_slots = 4, max_req = 4096, max_refs = 1;
     uint64_t max_pts = 1ull << 20, max_ids = 0, max_pending = 1ull << 20;
     std::vector<Slot> slots;
-    uint64_t device_bytes = 0;
+    // device arena of the steps in flight (scheduler thread only)
+    char* arena = nullptr;
+    uint64_t arena_bytes = 0, in_use = 0, peak_in_use = 0, memory_waits = 0;
+    std::map<uint64_t, uint64_t> free_blocks;   // offset -> size, coalesced
+    uint64_t single_bound = 0;     // arena bytes a step of one largest request may need
+    uint64_t reserve = 1ull << 30; // free device memory index admission leaves untouched
+    uint64_t index_bytes = 0;      // device bytes of the indexes this server uploaded
+    uint64_t device_bytes = 0;     // arena bytes
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -101,10 +118,74 @@ void free_slots(agj_server* S) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
-        if (sl.d_mem) cudaFree(sl.d_mem);
         if (sl.h_mem) cudaFreeHost(sl.h_mem);
     }
     S->slots.clear();
+    if (S->arena) cudaFree(S->arena);
+    S->arena = nullptr;
+}
+
+// First-fit allocation of `bytes` (a multiple of 256) from the arena;
+// returns false when no free block is large enough.
+bool arena_alloc(agj_server* S, uint64_t bytes, uint64_t* off) {
+    for (auto it = S->free_blocks.begin(); it != S->free_blocks.end(); ++it) {
+        if (it->second < bytes) continue;
+        *off = it->first;
+        const uint64_t rest = it->second - bytes, at = it->first + bytes;
+        S->free_blocks.erase(it);
+        if (rest) S->free_blocks[at] = rest;
+        S->in_use += bytes;
+        S->peak_in_use = std::max(S->peak_in_use, S->in_use);
+        return true;
+    }
+    return false;
+}
+
+void arena_free(agj_server* S, uint64_t off, uint64_t bytes) {
+    if (!bytes) return;
+    S->in_use -= bytes;
+    auto next = S->free_blocks.lower_bound(off);
+    if (next != S->free_blocks.end() && off + bytes == next->first) {
+        bytes += next->second;
+        next = S->free_blocks.erase(next);
+    }
+    if (next != S->free_blocks.begin()) {
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            prev->second += bytes;
+            return;
+        }
+    }
+    S->free_blocks[off] = bytes;
+}
+
+uint64_t largest_free(const agj_server* S) {
+    uint64_t m = 0;
+    for (auto& kv : S->free_blocks) m = std::max(m, kv.second);
+    return m;
+}
+
+// Arena bytes of a step over requests r[0 .. m): staged points, offsets,
+// status words, ids at each request's worst case, and the batched join's
+// work space (exact, from the jobs' shape).
+int step_arena_bytes(const agj_server* S, Request* const* r, uint32_t m, uint64_t* total, uint64_t* work) {
+    std::vector<const agj::Index*> xs(m);
+    std::vector<uint64_t> ns(m);
+    uint64_t pts = 0, offs = 0, ids = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+        xs[j] = S->X[r[j]->index_id];
+        ns[j] = r[j]->n;
+        const bool direct = S->host_reads && (reinterpret_cast<uintptr_t>(r[j]->h_points) & 15u) == 0;
+        if (!direct) pts += r[j]->n * 16;
+        offs += r[j]->n + 1;
+        ids += r[j]->n * std::max<uint64_t>(xs[j]->stats.max_refs, 1);
+    }
+    uint64_t w = 0, tb = 0;
+    const int rc = agj::step_bytes(xs.data(), ns.data(), m, S->ppt, &w, &tb);
+    if (rc != AGJ_OK) return rc;
+    *work = round256(w);
+    *total = round256(pts) + round256(offs * 4) + round256((uint64_t)m * 32) + round256(ids * 4 + 4) + *work;
+    return AGJ_OK;
 }
 
 // Copies a finished step's results out to its requests.
@@ -143,11 +224,32 @@ void finalize(agj_server* S, Slot& sl) {
     sl.reqs.clear();
     sl.busy = false;
     S->cv_done.notify_all();
+    arena_free(S, sl.block, sl.block_bytes);       // the scheduler thread owns the arena
+    sl.block_bytes = 0;
 }
 
-// Forms and launches one step on a free slot from the waiting requests.
-// Returns false if nothing was waiting.
-bool launch_step(agj_server* S, Slot& sl) {
+enum StepOutcome { kStepLaunched, kStepNothing, kStepNoMemory };
+
+// Fails requests that never ran with status rc.
+void fail_requests(agj_server* S, const std::vector<Request*>& take, int rc) {
+    std::lock_guard<std::mutex> lock(S->mu);
+    for (Request* r : take) {
+        r->res.status = rc;
+        r->res.t_done_ns = now_ns();
+        r->done = true;
+        ++S->completed;
+        if (!r->keep) delete r;
+    }
+    S->cv_done.notify_all();
+}
+
+// Forms and launches one step on a free slot from the waiting requests:
+// requests are taken from the queue head while they fit a slot's buffers,
+// then the step is cut back from its tail until its exact device bytes fit
+// a free block of the arena (the requests cut go back to the queue head, in
+// order).  kStepNoMemory: not even the head request fits now; it waits for
+// a step in flight to return its block.
+StepOutcome launch_step(agj_server* S, Slot& sl) {
     std::vector<Request*> take;
     {
         std::lock_guard<std::mutex> lock(S->mu);
@@ -162,9 +264,52 @@ bool launch_step(agj_server* S, Slot& sl) {
             S->pending.pop_front();
         }
     }
-    if (take.empty()) return false;
+    if (take.empty()) return kStepNothing;
+    // admission by device memory
+    uint64_t bytes = 0, work = 0, off = 0;
+    const uint64_t avail = largest_free(S);
+    int rc = AGJ_OK;
+    for (;;) {
+        rc = step_arena_bytes(S, take.data(), (uint32_t)take.size(), &bytes, &work);
+        if (rc != AGJ_OK || bytes <= avail || take.size() == 1) break;
+        // cut the step to about what fits (the bytes grow with the points)
+        size_t keep = (size_t)((double)take.size() * (double)avail / (double)bytes);
+        keep = std::max<size_t>(1, std::min(keep, take.size() - 1));
+        std::lock_guard<std::mutex> lock(S->mu);
+        while (take.size() > keep) {
+            S->pending.push_front(take.back());
+            take.pop_back();
+        }
+    }
+    if (rc != AGJ_OK) {
+        fail_requests(S, take, rc);
+        return kStepLaunched;
+    }
+    if (!arena_alloc(S, bytes, &off)) {
+        std::lock_guard<std::mutex> lock(S->mu);
+        for (auto it = take.rbegin(); it != take.rend(); ++it) S->pending.push_front(*it);
+        ++S->memory_waits;
+        return kStepNoMemory;
+    }
+    sl.block = off;
+    sl.block_bytes = bytes;
+    sl.d_mem = S->arena + off;
     const uint64_t t_start = now_ns();
     const uint32_t m = (uint32_t)take.size();
+    // the step's block: [points][offsets][status][ids][work]
+    uint64_t staged = 0, n_off = 0, n_ids = 0;
+    for (Request* r : take) {
+        const bool direct = S->host_reads && (reinterpret_cast<uintptr_t>(r->h_points) & 15u) == 0;
+        if (!direct) staged += r->n * 16;
+        n_off += r->n + 1;
+        n_ids += r->n * std::max<uint64_t>(S->X[r->index_id]->stats.max_refs, 1);
+    }
+    sl.off_pts = 0;
+    sl.off_off = round256(staged);
+    sl.off_status = sl.off_off + round256(n_off * 4);
+    sl.off_ids = sl.off_status + round256((uint64_t)m * 32);
+    sl.off_work = sl.off_ids + round256(n_ids * 4 + 4);
+    sl.work_bytes = work;
     sl.reqs = take;
     sl.pofs.resize(m);
     sl.oofs.resize(m);
@@ -201,7 +346,6 @@ bool launch_step(agj_server* S, Slot& sl) {
         io += o.ids_capacity;
     }
     cudaStream_t st = sl.stream;
-    int rc = AGJ_OK;
     if (po && cudaMemcpyAsync(d_pts, sl.h_mem + sl.h_off_pts, po, cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = AGJ_ECUDA;
     if (rc == AGJ_OK)
@@ -218,24 +362,20 @@ bool launch_step(agj_server* S, Slot& sl) {
         rc = AGJ_ECUDA;
     if (rc != AGJ_OK) {
         cudaGetLastError();
-        // the step never ran: its requests fail
-        std::lock_guard<std::mutex> lock(S->mu);
-        for (Request* r : take) {
-            r->res.status = rc;
-            r->res.t_done_ns = now_ns();
-            r->done = true;
-            ++S->completed;
-            if (!r->keep) delete r;
-        }
+        // the step never ran (or its launch failed): its requests fail; the
+        // block is returned once the stream has passed whatever was enqueued
+        cudaStreamSynchronize(st);
+        arena_free(S, sl.block, sl.block_bytes);
+        sl.block_bytes = 0;
         sl.reqs.clear();
-        S->cv_done.notify_all();
-        return true;
+        fail_requests(S, take, rc);
+        return kStepLaunched;
     }
     std::lock_guard<std::mutex> lock(S->mu);
     sl.busy = true;
     sl.step = ++S->steps;
     S->step_req_max = std::max<uint64_t>(S->step_req_max, m);
-    return true;
+    return kStepLaunched;
 }
 
 void run(agj_server* S) {
@@ -258,10 +398,21 @@ void run(agj_server* S) {
             if (sl.busy && (!oldest || sl.step < oldest->step)) oldest = &sl;
         }
         if (waiting && free_slot) {
-            launch_step(S, *free_slot);
-            continue;
+            const StepOutcome o = launch_step(S, *free_slot);
+            if (o != kStepNoMemory) continue;
+            if (!oldest) {                 // cannot happen: submit refuses requests beyond the arena
+                std::vector<Request*> head;
+                {
+                    std::lock_guard<std::mutex> lock(S->mu);
+                    head.push_back(S->pending.front());
+                    S->pending.pop_front();
+                }
+                fail_requests(S, head, AGJ_EBUDGET);
+                continue;
+            }
+            // fall through: wait for the oldest step to return its memory
         }
-        if (waiting && oldest) {           // every slot busy: wait for the oldest step
+        if (waiting && oldest) {           // every slot busy, or no memory: wait for the oldest step
             const uint64_t t0 = now_ns();
             cudaEventSynchronize(oldest->done);
             S->busy_s += (now_ns() - t0) * 1e-9;
@@ -297,14 +448,18 @@ int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const
     agj_server* S = new (std::nothrow) agj_server();
     if (!S) return AGJ_ENOMEM;
     S->device = dev;
-    uint32_t max_refs = 1;
+    agj_server_opts o{};
+    if (opts) o = *opts;
+    if (n_indexes > kMaxServerIndexes) { delete S; return AGJ_EUNSUPPORTED; }
+    S->X.reserve(kMaxServerIndexes);
+    uint32_t max_refs = std::max<uint32_t>(1, o.max_refs);
     for (uint32_t k = 0; k < n_indexes; ++k) {
         if (!indexes[k] || !indexes[k]->X.d_blob || indexes[k]->X.device != dev) { delete S; return AGJ_EINVAL; }
         S->X.push_back(&indexes[k]->X);
         max_refs = std::max<uint32_t>(max_refs, indexes[k]->X.stats.max_refs);
     }
-    agj_server_opts o{};
-    if (opts) o = *opts;
+    S->max_refs = max_refs;
+    if (o.hbm_reserve_bytes) S->reserve = o.hbm_reserve_bytes;
     if (o.n_slots) S->n_slots = o.n_slots;
     if (o.max_step_requests) S->max_req = o.max_step_requests;
     if (o.max_step_points) S->max_pts = o.max_step_points;
@@ -321,39 +476,52 @@ int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const
     }
     if (S->n_slots > 64 || S->max_req > 65535 || S->max_pts >= (1ull << 31)) { delete S; return AGJ_EINVAL; }
     S->max_ids = S->max_pts * max_refs;
-    // work space of the largest step a slot admits
-    uint64_t work = 0, stage = 0;
+    // bounds of the largest step (any index, up to max_step_points points
+    // in max_step_requests requests) and of the largest single request
+    uint64_t work = 0, stage = 0, work1 = 0, stage1 = 0;
     {
         uint32_t mcr = 1;
-        uint64_t all_polys = 0;
-        bool any_exact = false;
+        uint64_t all_polys = 0, max_polys = 0;
         for (auto* x : S->X) {
-            if (x->mode != AGJ_EXACT) continue;
-            any_exact = true;
             mcr = std::max<uint32_t>(mcr, x->stats.max_cand_refs);
+            if (x->mode != AGJ_EXACT) continue;
             all_polys += x->n_polys;
+            max_polys = std::max<uint64_t>(max_polys, x->n_polys);
         }
-        const int rc = agj::step_bound(S->max_pts, S->max_req, S->ppt, mcr, all_polys, any_exact, &work, &stage);
+        int rc = agj::step_bound(S->max_pts, S->max_req, S->ppt, mcr, all_polys, true, &work, &stage);
+        if (rc == AGJ_OK) rc = agj::step_bound(S->max_pts, 1, S->ppt, mcr, max_polys, true, &work1, &stage1);
         if (rc != AGJ_OK) { delete S; return rc; }
     }
     const uint64_t pts_bytes = round256(S->max_pts * 16 + (uint64_t)S->max_req * 16);
     const uint64_t off_bytes = round256((S->max_pts + S->max_req) * 4);
     const uint64_t st_bytes = round256((uint64_t)S->max_req * 32);
     const uint64_t ids_bytes = round256(S->max_ids * 4 + 4);
-    const uint64_t per_slot = pts_bytes + off_bytes + st_bytes + ids_bytes + round256(work);
-    if (o.hbm_budget_bytes && per_slot * S->n_slots > o.hbm_budget_bytes) {
-        // fewer slots in flight to fit the device-memory budget
-        S->n_slots = (uint32_t)std::max<uint64_t>(1, o.hbm_budget_bytes / per_slot);
-        if (per_slot > o.hbm_budget_bytes) { delete S; return AGJ_EBUDGET; }
+    const uint64_t per_step = pts_bytes + off_bytes + st_bytes + ids_bytes + round256(work);
+    S->single_bound = round256(S->max_pts * 16) + round256((S->max_pts + 1) * 4) + 256 +
+                      round256(S->max_pts * max_refs * 4 + 4) + round256(work1);
+    // the arena: the budget, else n_slots largest steps, within the free
+    // device memory less the reserve
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); delete S; return AGJ_ECUDA; }
+        const uint64_t avail = free_b > S->reserve ? free_b - S->reserve : 0;
+        uint64_t want = o.hbm_budget_bytes ? o.hbm_budget_bytes : per_step * S->n_slots;
+        if (want > avail) {
+            if (o.hbm_budget_bytes) { delete S; return AGJ_EBUDGET; }
+            want = avail;
+        }
+        S->arena_bytes = want & ~255ull;
+        if (S->arena_bytes < 256) { delete S; return AGJ_EBUDGET; }
     }
+    if (cudaMalloc(&S->arena, S->arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return AGJ_ENOMEM;
+    }
+    S->free_blocks[0] = S->arena_bytes;
+    S->device_bytes = S->arena_bytes;
     S->slots.resize(S->n_slots);
     for (Slot& sl : S->slots) {
-        sl.off_pts = 0;
-        sl.off_off = pts_bytes;
-        sl.off_status = sl.off_off + off_bytes;
-        sl.off_ids = sl.off_status + st_bytes;
-        sl.off_work = sl.off_ids + ids_bytes;
-        sl.work_bytes = round256(work);
         sl.h_off_pts = 0;
         sl.h_off_off = pts_bytes;
         sl.h_off_status = sl.h_off_off + off_bytes;
@@ -362,14 +530,12 @@ int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const
         sl.stage_bytes = round256(stage);
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&sl.d_mem, per_slot) != cudaSuccess ||
             cudaMallocHost(&sl.h_mem, sl.h_off_stage + sl.stage_bytes) != cudaSuccess) {
             cudaGetLastError();
             free_slots(S);
             delete S;
             return AGJ_ENOMEM;
         }
-        S->device_bytes += per_slot;
     }
     S->worker = std::thread(run, S);
     *out = S;
@@ -378,10 +544,31 @@ int agj_server_create(const agj_index* const* indexes, uint32_t n_indexes, const
 
 int agj_server_submit(agj_server* S, uint32_t index_id, const double* h_points, uint64_t n, uint32_t* h_offsets,
                       uint32_t* h_ids, uint64_t ids_capacity, uint64_t* ticket) {
-    if (!S || index_id >= S->X.size() || (n && !h_points) || (h_ids && !h_offsets)) return AGJ_EINVAL;
+    if (!S || (n && !h_points) || (h_ids && !h_offsets)) return AGJ_EINVAL;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (index_id >= S->X.size()) return AGJ_EINVAL;
+    }
     if (n > S->max_pts) return AGJ_ECAPACITY;
     Request* r = new (std::nothrow) Request();
     if (!r) return AGJ_ENOMEM;
+    r->index_id = index_id;
+    r->h_points = h_points;
+    r->n = n;
+    uint64_t single_bound;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        single_bound = S->single_bound;
+    }
+    if (single_bound > S->arena_bytes) {
+        // a small arena: this request alone must fit it
+        uint64_t bytes = 0, work = 0;
+        const int rc = step_arena_bytes(S, &r, 1, &bytes, &work);
+        if (rc != AGJ_OK || bytes > S->arena_bytes) {
+            delete r;
+            return rc != AGJ_OK ? rc : AGJ_EBUDGET;
+        }
+    }
     r->index_id = index_id;
     r->h_points = h_points;
     r->n = n;
@@ -406,6 +593,46 @@ int agj_server_submit(agj_server* S, uint32_t index_id, const double* h_points, 
         if (ticket) *ticket = r->ticket;
     }
     S->cv_work.notify_one();
+    return AGJ_OK;
+}
+
+int agj_server_add_index(agj_server* S, agj_index* index, uint32_t* index_id) {
+    if (!S || !index || !index_id) return AGJ_EINVAL;
+    agj::Index& X = index->X;
+    if (X.stats.max_refs > S->max_refs) return AGJ_ECAPACITY;     // the slots' pinned id buffers
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (S->X.size() >= kMaxServerIndexes) return AGJ_EUNSUPPORTED;
+    }
+    if (cudaSetDevice(S->device) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
+    if (!X.d_blob) {
+        // admission by free device memory: the index's blob must fit what is
+        // free beyond the reserve
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
+        const uint64_t need = agj::index_device_bytes(X);
+        if (free_b <= S->reserve || free_b - S->reserve < need) return AGJ_EBUDGET;
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return AGJ_ECUDA; }
+        const int rc = agj::upload_index(&X, st);
+        cudaStreamDestroy(st);
+        if (rc != AGJ_OK) return rc;
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->index_bytes += X.blob_bytes;
+    } else if (X.device != S->device) {
+        return AGJ_EINVAL;
+    }
+    // the bound of one request of this index (a small arena checks requests at submit)
+    uint64_t work1 = 0, stage1 = 0;
+    const int rc = agj::step_bound(S->max_pts, 1, S->ppt, std::max<uint32_t>(1, X.stats.max_cand_refs),
+                                   X.mode == AGJ_EXACT ? X.n_polys : 0, X.mode == AGJ_EXACT, &work1, &stage1);
+    if (rc != AGJ_OK) return rc;
+    const uint64_t one = round256(S->max_pts * 16) + round256((S->max_pts + 1) * 4) + 256 +
+                         round256(S->max_pts * std::max<uint64_t>(X.stats.max_refs, 1) * 4 + 4) + round256(work1);
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->single_bound = std::max(S->single_bound, one);
+    S->X.push_back(&X);
+    *index_id = (uint32_t)(S->X.size() - 1);
     return AGJ_OK;
 }
 
@@ -445,6 +672,10 @@ int agj_server_get_stats(agj_server* S, int reset, agj_server_stats* out) {
     out->n_slots = S->n_slots;
     out->host_reads = S->host_reads ? 1u : 0u;
     out->device_bytes = S->device_bytes;
+    out->memory_waits = S->memory_waits;
+    out->peak_bytes_in_use = S->peak_in_use;
+    out->index_bytes = S->index_bytes;
+    out->n_indexes = (uint32_t)S->X.size();
     std::vector<double> v;
     v.reserve(S->latencies.size());
     double sum = 0, mx = 0;
@@ -458,6 +689,7 @@ int agj_server_get_stats(agj_server* S, int reset, agj_server_stats* out) {
     out->p50_us = percentile(v, 0.50);
     out->p99_us = percentile(v, 0.99);
     if (reset) {
+        S->memory_waits = 0;
         S->latencies.clear();
         S->submitted -= S->completed;
         S->completed = 0;

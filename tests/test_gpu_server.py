@@ -150,3 +150,90 @@ def test_server_and_plain_load(torch, agj, sets):
                                 exact_fraction=0.1, seed=5, warmup_requests=50)
     p = agj.plain_load(idx, spec_small)
     assert p["requests"] == 450 and p["p50_us"] > 0
+
+
+def test_server_admission_by_device_memory(torch, agj, sets):
+    """A device arena too small for more than a couple of launches: the
+    scheduler cuts launches back and waits for memory, yet every request's
+    result equals its plain join; a request that could never fit the arena
+    is refused at submit with AGJ_EBUDGET."""
+    idx = _indexes(sets)
+    roomy = agj.Server(idx, n_slots=4, max_step_requests=256, max_step_points=1 << 16)
+    full = roomy.stats()["device_bytes"]
+    roomy.close()
+    budget = full // 6                                      # less than one largest launch of four slots' worth
+    srv = agj.Server(idx, n_slots=4, max_step_requests=256, max_step_points=1 << 16, hbm_budget_bytes=budget,
+                     stage_points=True)
+    assert srv.stats()["device_bytes"] <= budget
+    # large requests (10 000 - 20 000 points): only a few fit the arena at once
+    rng = np.random.default_rng(3)
+    reqs = []
+    for k in range(120):
+        s_ = int(rng.integers(0, len(sets)))
+        n = int(rng.integers(10_000, 20_001))
+        start = int(rng.integers(0, sets[s_][1].shape[0] - n))
+        reqs.append((s_ + (len(sets) if k % 3 == 2 else 0), sets[s_][1][start:start + n]))
+    tickets, refused = [], 0
+    for i, p in reqs:
+        try:
+            tickets.append((srv.submit(i, p), i, p))
+        except agj.AgjError as e:
+            assert e.status == 3                            # AGJ_EBUDGET: alone it would not fit
+            refused += 1
+    outs = [(srv.poll(t), i, p) for t, i, p in tickets]
+    st = srv.stats()
+    assert refused == 0 and st["memory_waits"] > 0 and 0 < st["peak_bytes_in_use"] <= st["device_bytes"]
+    assert st["completed"] == len(tickets)
+    for (off, ids, res), i, p in outs:
+        ref = _plain(torch, agj, idx[i], p)
+        assert np.array_equal(off, ref[0]) and np.array_equal(ids, ref[1])
+    srv.close()
+    # an arena below one request of max_step_points: large requests refused, small ones served
+    tiny = agj.Server(idx, n_slots=2, max_step_requests=64, max_step_points=1 << 16, hbm_budget_bytes=4 << 20,
+                      stage_points=True)
+    with pytest.raises(agj.AgjError) as e:
+        tiny.submit(3, sets[1][1][:60_000])
+    assert e.value.status == 3
+    off, ids, _ = tiny.poll(tiny.submit(3, sets[1][1][:500]))
+    ref = _plain(torch, agj, idx[3], sets[1][1][:500])
+    assert np.array_equal(off, ref[0]) and np.array_equal(ids, ref[1])
+    tiny.close()
+    # a budget above the free device memory is refused at creation
+    free, _ = torch.cuda.mem_get_info()
+    with pytest.raises(agj.AgjError) as e:
+        agj.Server(idx, hbm_budget_bytes=free + (1 << 30))
+    assert e.value.status == 3
+
+
+def test_server_admits_indexes_by_free_memory(torch, agj, sets):
+    """agj_server_add_index uploads a host-built index when it fits the free
+    device memory less the reserve (requests to it then equal the plain
+    join), and refuses it with AGJ_EBUDGET when the reserve leaves no room,
+    while requests in flight keep running."""
+    from paper_1802_09488_gb300 import synth
+    idx = _indexes(sets)
+    polys = synth.voronoi_tiling(40, synth.BOX_CITY, seed=71, vmin=20, vmax=120)
+    pts = synth.points_mixture(50_000, synth.BOX_CITY, seed=72)
+    srv = agj.Server(idx, n_slots=2, max_step_points=1 << 16)
+    busy = [srv.submit(1, sets[1][1][k * 5000:(k + 1) * 5000]) for k in range(20)]   # in flight meanwhile
+    host_a = agj.Index(polys, agj.APPROX, 4.0, host_only=True)
+    host_e = agj.Index(polys, agj.EXACT, 0, train=pts[:5000], host_only=True)
+    ka, ke = srv.add_index(host_a), srv.add_index(host_e)
+    st = srv.stats()
+    assert (ka, ke) == (len(idx), len(idx) + 1) and st["n_indexes"] == len(idx) + 2 and st["index_bytes"] > 0
+    for k in (ka, ke):
+        off, ids, _ = srv.poll(srv.submit(k, pts))
+        ref = _plain(torch, agj, srv.indexes[k], pts)       # now resident: joinable directly too
+        assert np.array_equal(off, ref[0]) and np.array_equal(ids, ref[1])
+    for t in busy:
+        srv.poll(t)
+    srv.close()
+    # a reserve as large as the free memory: no index fits
+    free, _ = torch.cuda.mem_get_info()
+    srv = agj.Server(idx, n_slots=1, max_step_requests=4, max_step_points=1 << 12,
+                     hbm_reserve_bytes=free - (16 << 20))     # a small arena, then ~14 MB beyond the reserve
+    assert agj.Index(polys, agj.APPROX, 4.0, host_only=True).stats()["n_nodes"] * 2048 > 16 << 20
+    with pytest.raises(agj.AgjError) as e:
+        srv.add_index(agj.Index(polys, agj.APPROX, 4.0, host_only=True))
+    assert e.value.status == 3 and srv.stats()["n_indexes"] == len(idx)
+    srv.close()
