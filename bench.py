@@ -59,10 +59,14 @@ def parse():
     ap.add_argument("--workload", choices=["c2", "c3", "c1"], default="c2",
                     help="c2: city (default); c3: 40 000 fine overlapping polygons; c1: 5 polygons, uniform points")
     ap.add_argument("--eps", type=float, default=None, help="approximate precision in metres (default per workload)")
-    ap.add_argument("--only", choices=["batched", "served"], default=None,
-                    help="run only that form and print its JSON object (for profiling)")
+    ap.add_argument("--only", choices=["batched", "served", "sort-study"], default=None,
+                    help="run only that form (or the sort-prepass study) and print its JSON object")
     ap.add_argument("--form-reps", type=int, default=10, help="timed repetitions of the batched form")
     ap.add_argument("--batched-tiling", default=None, help="points_per_lane,ctas_per_sm: skip the autotuner")
+    ap.add_argument("--c4-polys", default=None,
+                    help="lo,hi polygons per set of the batched form (default 5,300; the workload's own range is "
+                         "5,40000)")
+    ap.add_argument("--c4-jobs", type=int, default=None, help="jobs of the batched form (default 64)")
     return ap.parse_args()
 
 
@@ -78,13 +82,15 @@ C5 = {"sets": 16, "polys": (300, 1500), "rate": 2e5, "requests": 300_000, "warmu
       "max_points": 65536, "exact_fraction": 0.1, "plain_requests": 5_000, "saturate_rate": 4e6}
 
 
-def batched_form(agj, torch, reps: int = 10, tiling=None) -> dict:
+def batched_form(agj, torch, reps: int = 10, tiling=None, polys=None, m=None) -> dict:
     """64 plain joins in sequence vs one batched plan (graph replay) over the
     same jobs, with the autotuned tiling; outputs compared job by job."""
     import numpy as np
     from paper_1802_09488_gb300 import autotune, synth
     t0 = time.perf_counter()
-    jobs = synth.batched_jobs(m=C4["m"], seed=C4["seed"], polys=C4["polys"], points=C4["points"])
+    polys = polys or C4["polys"]
+    m = m or C4["m"]
+    jobs = synth.batched_jobs(m=m, seed=C4["seed"], polys=polys, points=C4["points"])
     idx = [agj.Index(j.polygons, agj.EXACT, 0, train=j.train) if j.exact else agj.Index(j.polygons, agj.APPROX, j.eps_m)
            for j in jobs]
     prep_s = time.perf_counter() - t0
@@ -122,7 +128,8 @@ def batched_form(agj, torch, reps: int = 10, tiling=None) -> dict:
     bp = plan.pairs()
     batch_ms = time_it(lambda: plan.run(pts, bp))
     same = all(np.array_equal(a[0], b.to_host()[0]) and np.array_equal(a[1], b.to_host()[1]) for a, b in zip(ref, bp))
-    out = {"workload": (f"c4-reduced: {C4['m']} jobs, polygons log-uniform {C4['polys'][0]}-{C4['polys'][1]}, "
+    out = {"workload": (f"c4{'' if polys == (5, 40_000) else '-reduced'}: {m} jobs, polygons log-uniform "
+                        f"{polys[0]}-{polys[1]}, "
                         f"points log-uniform {C4['points'][0]:.0e}-{C4['points'][1]:.0e}, every 2nd job exact"),
            "points": N, "plain_ms": plain_ms, "batched_ms": batch_ms,
            "plain_points_per_s": N / (plain_ms / 1e3), "batched_points_per_s": N / (batch_ms / 1e3),
@@ -294,6 +301,64 @@ def c1_amortized(agj, torch, peaks, joins: int = 1000) -> dict:
             "roofline_join": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_point": bpp,
                               "note": "inputs (1.6 MB) stay in L2 across the graph's joins: a warm-cache figure"}}
+
+
+def sort_study(agj, torch, workload_name: str, n: int, reps: int = 5) -> dict:
+    """What a sort-points-by-cell prepass could gain: the probe on points
+    already sorted by cell id (the prepass's best case, its own cost left
+    out) against the same points in stream order, and the prepass's cost
+    itself (FP64 cell ids, a radix sort of (id, position) by the library,
+    the gather of the points and the scatter of the results back to stream
+    order, 12 B per point), on the workload's resident points."""
+    polys, pts_np, train = workload(workload_name, n, 0)
+    eps = WORKLOADS[workload_name]["eps"]
+    out = {"workload": f"{WORKLOADS[workload_name]['name']}-{n:.0e}".replace("+", "")}
+    d = torch.from_numpy(pts_np).cuda()
+    ev = [_event(torch, torch.cuda.current_stream()) for _ in range(4)]
+
+    def probe_ms(ix, pts, pr):
+        ts = []
+        for _ in range(reps + 1):
+            agj.join_timed(ix, pts, pr, ev)
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+        return statistics.median(ts[1:])
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            a, b = _event(torch, torch.cuda.current_stream()), _event(torch, torch.cuda.current_stream())
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts[1:])
+
+    ids = agj.cell_ids(d)
+    order = torch.sort(ids, stable=True).indices
+    d_sorted = d[order].contiguous()
+    results = torch.empty(n, dtype=torch.int64, device="cuda")
+    src = torch.empty(n, dtype=torch.int64, device="cuda")
+
+    def prepass():
+        k = agj.cell_ids(d, out=ids)
+        o = torch.sort(k, stable=True).indices
+        torch.index_select(d, 0, o, out=d_sorted)
+        results.index_copy_(0, o, src)            # the results' way back to stream order
+
+    out["prepass_ms"] = timed(prepass)
+    for mode_name, mode in (("approx", agj.APPROX), ("exact", agj.EXACT)):
+        ix = agj.Index(polys, mode, eps, train=train if mode == agj.EXACT else None)
+        pr = agj.Pairs(ix, n)
+        t_stream = probe_ms(ix, d, pr)
+        t_sorted = probe_ms(ix, d_sorted, pr)
+        out[mode_name] = {"probe_stream_order_ms": t_stream, "probe_sorted_ms": t_sorted,
+                          "gain_ms": t_stream - t_sorted,
+                          "net_ms_with_prepass": t_sorted + out["prepass_ms"] - t_stream}
+        del pr, ix
+        torch.cuda.empty_cache()
+    return out
 
 
 class ClockSampler:
@@ -490,7 +555,11 @@ def main():
         torch.cuda.set_device(local)
         if args.only == "batched":
             tiling = tuple(int(x) for x in args.batched_tiling.split(",")) if args.batched_tiling else None
-            print(json.dumps(batched_form(agj, torch, reps=args.form_reps, tiling=tiling)), flush=True)
+            c4p = tuple(int(x) for x in args.c4_polys.split(",")) if args.c4_polys else None
+            print(json.dumps(batched_form(agj, torch, reps=args.form_reps, tiling=tiling, polys=c4p, m=args.c4_jobs)),
+                  flush=True)
+        elif args.only == "sort-study":
+            print(json.dumps(sort_study(agj, torch, args.workload, args.n_points)), flush=True)
         else:
             print(json.dumps(served_form(agj)), flush=True)
         return

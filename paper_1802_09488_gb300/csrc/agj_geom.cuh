@@ -240,26 +240,28 @@ AGJ_HD void face_uv_to_xyz(int face, double u, double v, double p[3]) {
 
 constexpr int kFastHiTerms = 18;   // coefficients of degrees 2..5
 
+// The two coordinates' coefficients are interleaved (X, Y), (X, Y), ... so
+// that the device evaluates both as one pair of FP32 lanes (model_eval_xy).
 struct FastModel {
     int32_t enabled;
     int32_t face;
     int32_t path;                   // 1: each coordinate in one binade (raw-bit offsets); 2: general
     int32_t n0x, n0y;               // integer parts of the constant terms (level-30 cells)
-    float f0x, f0y;                 // their fractional parts
     float err;                      // bound on |model - spec| incl. rounding allowances (cells)
+    alignas(8) float f0xy[2];       // fractional parts of the constant terms (X, Y)
     int64_t wlat_lo, wlat_hi, wlng_lo, wlng_hi;   // window: path 1 raw bits, path 2 order keys
     int64_t lat0, lng0;             // centre: path 1 raw bits, path 2 units of 2^-47 degree
     int32_t split;                  // bits in the low part of an offset (23 path 1, 24 path 2)
     float sa_hi, sa_lo, sb_hi, sb_lo;   // scales of the offsets' two parts (powers of two)
-    float xl[4], yl[4];             // first order: c10 hi, c10 lo, c01 hi, c01 lo
-    float xh[kFastHiTerms], yh[kFastHiTerms];     // degrees 2..5 (layout in model_eval)
+    alignas(8) float xyl[8];        // first order: c10 hi, c10 lo, c01 hi, c01 lo, each (X, Y)
+    alignas(8) float xyh[2 * kFastHiTerms];   // degrees 2..5 (layout in model_eval), each (X, Y)
     // the same kind of model for U = 2^30 u and V = 2^30 v (the refine step)
     int32_t uv_enabled;
     int32_t n0u, n0v;
-    float f0u, f0v;
     float err_uv;                   // bound on |model - 2^30 (u,v)|, same units
-    float ul[4], vl[4];
-    float uh[kFastHiTerms], vh[kFastHiTerms];
+    alignas(8) float f0uv[2];
+    alignas(8) float uvl[8];
+    alignas(8) float uvh[2 * kFastHiTerms];
 };
 
 AGJ_HD int64_t double_bits(double x) {
@@ -347,27 +349,28 @@ AGJ_HD bool model_offsets(const FastModel& M, int64_t blat, int64_t blng, float*
 
 // Model value minus its integer constant, as th + tl (floats; th carries the
 // large first-order and polynomial terms, tl the small remainder and the
-// constant's fraction f0).  Coefficients h: b^0: a^2..a^5 (h0..h3); b^1:
-// a^1..a^4 (h4..h7); b^2: a^0..a^3 (h8..h11); b^3: a^0..a^2 (h12..h14);
-// b^4: a^0, a^1 (h15, h16); b^5: h17.
-AGJ_HD void model_eval(const float l[4], const float h[kFastHiTerms], float f0, float ah, float al, float bh, float bl,
-                       float* th, float* tl) {
-    const float p1 = l[0] * ah;
-    const float e1 = model_fma(l[0], ah, -p1);
-    const float p2 = l[2] * bh;
-    const float e2 = model_fma(l[2], bh, -p2);
+// constant's fraction f0).  Coefficient k of one coordinate is L[2k] (first
+// order) or H[2k] (higher terms; the other coordinate's sit between).
+// H: b^0: a^2..a^5 (h0..h3); b^1: a^1..a^4 (h4..h7); b^2: a^0..a^3
+// (h8..h11); b^3: a^0..a^2 (h12..h14); b^4: a^0, a^1 (h15, h16); b^5: h17.
+AGJ_HD void model_eval(const float* L, const float* H, float f0, float ah, float al, float bh, float bl, float* th,
+                       float* tl) {
+    const float p1 = L[0] * ah;
+    const float e1 = model_fma(L[0], ah, -p1);
+    const float p2 = L[4] * bh;
+    const float e2 = model_fma(L[4], bh, -p2);
     float corr = e1 + e2;
-    corr = model_fma(l[0], al, corr);
-    corr = model_fma(l[1], ah, corr);
-    corr = model_fma(l[2], bl, corr);
-    corr = model_fma(l[3], bh, corr);
+    corr = model_fma(L[0], al, corr);
+    corr = model_fma(L[2], ah, corr);
+    corr = model_fma(L[4], bl, corr);
+    corr = model_fma(L[6], bh, corr);
     const float a = ah + al, b = bh + bl;
-    const float q0 = (a * a) * model_fma(a, model_fma(a, model_fma(a, h[3], h[2]), h[1]), h[0]);
-    const float q1 = a * model_fma(a, model_fma(a, model_fma(a, h[7], h[6]), h[5]), h[4]);
-    const float q2 = model_fma(a, model_fma(a, model_fma(a, h[11], h[10]), h[9]), h[8]);
-    const float q3 = model_fma(a, model_fma(a, h[14], h[13]), h[12]);
-    const float q4 = model_fma(a, h[16], h[15]);
-    float t = model_fma(b, h[17], q4);
+    const float q0 = (a * a) * model_fma(a, model_fma(a, model_fma(a, H[6], H[4]), H[2]), H[0]);
+    const float q1 = a * model_fma(a, model_fma(a, model_fma(a, H[14], H[12]), H[10]), H[8]);
+    const float q2 = model_fma(a, model_fma(a, model_fma(a, H[22], H[20]), H[18]), H[16]);
+    const float q3 = model_fma(a, model_fma(a, H[28], H[26]), H[24]);
+    const float q4 = model_fma(a, H[32], H[30]);
+    float t = model_fma(b, H[34], q4);
     t = model_fma(b, t, q3);
     t = model_fma(b, t, q2);
     t = model_fma(b, t, q1);
@@ -377,6 +380,89 @@ AGJ_HD void model_eval(const float l[4], const float h[kFastHiTerms], float f0, 
     two_sum(s1, poly, &s2, &r2);
     *th = s2;
     *tl = ((r1 + r2) + corr) + f0;
+}
+
+#ifdef __CUDA_ARCH__
+// Paired FP32 lanes (fma/mul/add/sub .rn.f32x2: two independent
+// round-to-nearest operations), for evaluating the two coordinates at once.
+typedef unsigned long long f32x2_t;
+__device__ __forceinline__ f32x2_t f2_pair(float x, float y) {
+    f32x2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void f2_split(f32x2_t v, float* x, float* y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(*x), "=f"(*y) : "l"(v));
+}
+__device__ __forceinline__ f32x2_t f2_fma(f32x2_t a, f32x2_t b, f32x2_t c) {
+    f32x2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_mul(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_add(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_sub(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+#endif
+
+// model_eval of both coordinates (interleaved coefficients L, H, f0): on the
+// device as paired FP32 lanes with model_eval's operation order, so each
+// lane's result equals model_eval's; on the host twice in turn.
+AGJ_HD void model_eval_xy(const float* L, const float* H, const float* f0, float ah, float al, float bh, float bl,
+                          float* xth, float* xtl, float* yth, float* ytl) {
+#ifdef __CUDA_ARCH__
+    const f32x2_t* Lp = reinterpret_cast<const f32x2_t*>(L);
+    const f32x2_t* Hp = reinterpret_cast<const f32x2_t*>(H);
+    const f32x2_t AH = f2_pair(ah, ah), AL = f2_pair(al, al), BH = f2_pair(bh, bh), BL = f2_pair(bl, bl);
+    const f32x2_t NEG = f2_pair(-1.0f, -1.0f);
+    const f32x2_t p1 = f2_mul(Lp[0], AH);
+    const f32x2_t e1 = f2_fma(Lp[0], AH, f2_mul(p1, NEG));
+    const f32x2_t p2 = f2_mul(Lp[2], BH);
+    const f32x2_t e2 = f2_fma(Lp[2], BH, f2_mul(p2, NEG));
+    f32x2_t corr = f2_add(e1, e2);
+    corr = f2_fma(Lp[0], AL, corr);
+    corr = f2_fma(Lp[1], AH, corr);
+    corr = f2_fma(Lp[2], BL, corr);
+    corr = f2_fma(Lp[3], BH, corr);
+    const float a = ah + al, b = bh + bl;
+    const f32x2_t A = f2_pair(a, a), B = f2_pair(b, b), AA = f2_pair(a * a, a * a);
+    const f32x2_t q0 = f2_mul(AA, f2_fma(A, f2_fma(A, f2_fma(A, Hp[3], Hp[2]), Hp[1]), Hp[0]));
+    const f32x2_t q1 = f2_mul(A, f2_fma(A, f2_fma(A, f2_fma(A, Hp[7], Hp[6]), Hp[5]), Hp[4]));
+    const f32x2_t q2 = f2_fma(A, f2_fma(A, f2_fma(A, Hp[11], Hp[10]), Hp[9]), Hp[8]);
+    const f32x2_t q3 = f2_fma(A, f2_fma(A, Hp[14], Hp[13]), Hp[12]);
+    const f32x2_t q4 = f2_fma(A, Hp[16], Hp[15]);
+    f32x2_t t = f2_fma(B, Hp[17], q4);
+    t = f2_fma(B, t, q3);
+    t = f2_fma(B, t, q2);
+    t = f2_fma(B, t, q1);
+    const f32x2_t poly = f2_fma(B, t, q0);
+    // the two error-free sums of model_eval, lane by lane
+    const f32x2_t s1 = f2_add(p1, p2);
+    const f32x2_t bv1 = f2_sub(s1, p1);
+    const f32x2_t av1 = f2_sub(s1, bv1);
+    const f32x2_t r1 = f2_add(f2_sub(p1, av1), f2_sub(p2, bv1));
+    const f32x2_t s2 = f2_add(s1, poly);
+    const f32x2_t bv2 = f2_sub(s2, s1);
+    const f32x2_t av2 = f2_sub(s2, bv2);
+    const f32x2_t r2 = f2_add(f2_sub(s1, av2), f2_sub(poly, bv2));
+    const f32x2_t tl = f2_add(f2_add(f2_add(r1, r2), corr), *reinterpret_cast<const f32x2_t*>(f0));
+    f2_split(s2, xth, yth);
+    f2_split(tl, xtl, ytl);
+#else
+    model_eval(L, H, f0[0], ah, al, bh, bl, xth, xtl);
+    model_eval(L + 1, H + 1, f0[1], ah, al, bh, bl, yth, ytl);
+#endif
 }
 
 // floor(n0 + th + tl - err) and floor(n0 + th + tl + err) for small |tl|
@@ -412,8 +498,7 @@ AGJ_HD int model_ij(const FastModel& M, double lat, double lng, uint32_t* i, uin
     float ah, al, bh, bl;
     if (!model_offsets(M, double_bits(lat), double_bits(lng), &ah, &al, &bh, &bl)) return 0;
     float xth, xtl, yth, ytl;
-    model_eval(M.xl, M.xh, M.f0x, ah, al, bh, bl, &xth, &xtl);
-    model_eval(M.yl, M.yh, M.f0y, ah, al, bh, bl, &yth, &ytl);
+    model_eval_xy(M.xyl, M.xyh, M.f0xy, ah, al, bh, bl, &xth, &xtl, &yth, &ytl);
     int32_t ilo, ihi, jlo, jhi;
     model_cells(M.n0x, xth, xtl, M.err, &ilo, &ihi);
     model_cells(M.n0y, yth, ytl, M.err, &jlo, &jhi);
@@ -594,8 +679,7 @@ AGJ_HD bool model_uv_local(const FastModel& M, double lat, double lng, const Pol
     float ah, al, bh, bl;
     if (!M.uv_enabled || !model_offsets(M, double_bits(lat), double_bits(lng), &ah, &al, &bh, &bl)) return false;
     float uth, utl, vth, vtl;
-    model_eval(M.ul, M.uh, M.f0u, ah, al, bh, bl, &uth, &utl);
-    model_eval(M.vl, M.vh, M.f0v, ah, al, bh, bl, &vth, &vtl);
+    model_eval_xy(M.uvl, M.uvh, M.f0uv, ah, al, bh, bl, &uth, &utl, &vth, &vtl);
     const float xu = ((float)(M.n0u - P.ru) + uth) + utl;
     const float xv = ((float)(M.n0v - P.rv) + vth) + vtl;
     *pu = xu;

@@ -259,33 +259,34 @@ void fit_fast_model(Index* idx, unsigned threads) {
     const double X0 = Xc + cx[0], Y0 = Yc + cy[0];
     F.n0x = (int32_t)std::floor(X0);
     F.n0y = (int32_t)std::floor(Y0);
-    F.f0x = (float)(X0 - F.n0x);
-    F.f0y = (float)(Y0 - F.n0y);
+    F.f0xy[0] = (float)(X0 - F.n0x);
+    F.f0xy[1] = (float)(Y0 - F.n0y);
+    // coefficient k of coordinate c (0: X or U, 1: Y or V) at [2 k + c]
     auto split = [](double c, float* hi, float* lo) {
         *hi = (float)c;
         *lo = (float)(c - (double)*hi);
     };
-    split(cx[1], &F.xl[0], &F.xl[1]);
-    split(cx[2], &F.xl[2], &F.xl[3]);
-    split(cy[1], &F.yl[0], &F.yl[1]);
-    split(cy[2], &F.yl[2], &F.yl[3]);
+    split(cx[1], &F.xyl[0], &F.xyl[2]);
+    split(cx[2], &F.xyl[4], &F.xyl[6]);
+    split(cy[1], &F.xyl[1], &F.xyl[3]);
+    split(cy[2], &F.xyl[5], &F.xyl[7]);
     for (int k = 0; k < kFastHiTerms; ++k) {
-        F.xh[k] = (float)cx[3 + k];
-        F.yh[k] = (float)cy[3 + k];
+        F.xyh[2 * k] = (float)cx[3 + k];
+        F.xyh[2 * k + 1] = (float)cy[3 + k];
     }
     if (have_uv) {
         const double U0 = uc * 1073741824.0 + cu[0], V0 = vc * 1073741824.0 + cv[0];
         F.n0u = (int32_t)std::floor(U0);
         F.n0v = (int32_t)std::floor(V0);
-        F.f0u = (float)(U0 - F.n0u);
-        F.f0v = (float)(V0 - F.n0v);
-        split(cu[1], &F.ul[0], &F.ul[1]);
-        split(cu[2], &F.ul[2], &F.ul[3]);
-        split(cv[1], &F.vl[0], &F.vl[1]);
-        split(cv[2], &F.vl[2], &F.vl[3]);
+        F.f0uv[0] = (float)(U0 - F.n0u);
+        F.f0uv[1] = (float)(V0 - F.n0v);
+        split(cu[1], &F.uvl[0], &F.uvl[2]);
+        split(cu[2], &F.uvl[4], &F.uvl[6]);
+        split(cv[1], &F.uvl[1], &F.uvl[3]);
+        split(cv[2], &F.uvl[5], &F.uvl[7]);
         for (int k = 0; k < kFastHiTerms; ++k) {
-            F.uh[k] = (float)cu[3 + k];
-            F.vh[k] = (float)cv[3 + k];
+            F.uvh[2 * k] = (float)cu[3 + k];
+            F.uvh[2 * k + 1] = (float)cv[3 + k];
         }
     }
     // sampled bound with the device-identical arithmetic: an (N+1) x (N+1)
@@ -303,16 +304,14 @@ void fit_fast_model(Index* idx, unsigned threads) {
             float ah, al, bh, bl;
             if (!model_offsets(F, double_bits(lat), double_bits(lng), &ah, &al, &bh, &bl)) { bad[ia] = 1; continue; }
             float xth, xtl, yth, ytl;
-            model_eval(F.xl, F.xh, F.f0x, ah, al, bh, bl, &xth, &xtl);
-            model_eval(F.yl, F.yh, F.f0y, ah, al, bh, bl, &yth, &ytl);
+            model_eval_xy(F.xyl, F.xyh, F.f0xy, ah, al, bh, bl, &xth, &xtl, &yth, &ytl);
             const double dx = model_value(F.n0x, xth, xtl) - uv_to_st(u) * 1073741824.0;
             const double dy = model_value(F.n0y, yth, ytl) - uv_to_st(v) * 1073741824.0;
             w = std::max(w, std::max(std::fabs(dx), std::fabs(dy)));
             wb = std::max(wb, (double)std::max(std::fabs((xth - model_floor(xth)) + xtl), std::fabs((yth - model_floor(yth)) + ytl)));
             if (have_uv) {
                 float uth, utl, vth, vtl;
-                model_eval(F.ul, F.uh, F.f0u, ah, al, bh, bl, &uth, &utl);
-                model_eval(F.vl, F.vh, F.f0v, ah, al, bh, bl, &vth, &vtl);
+                model_eval_xy(F.uvl, F.uvh, F.f0uv, ah, al, bh, bl, &uth, &utl, &vth, &vtl);
                 // the model's real value n0 + th + tl (exact in double) against 2^30 (u, v)
                 const double du = ((double)F.n0u + (double)uth + (double)utl) - u * 1073741824.0;
                 const double dv = ((double)F.n0v + (double)vth + (double)vtl) - v * 1073741824.0;

@@ -153,37 +153,36 @@ def test_server_and_plain_load(torch, agj, sets):
 
 
 def test_server_admission_by_device_memory(torch, agj, sets):
-    """A device arena too small for more than a couple of launches: the
-    scheduler cuts launches back and waits for memory, yet every request's
-    result equals its plain join; a request that could never fit the arena
-    is refused at submit with AGJ_EBUDGET."""
+    """An arena of 1.3 times the largest request's launch bytes: no two
+    requests fit it together, so every launch holds one request and the
+    peak use stays within the budget, while the four slots keep trying to
+    launch the next request before the previous one has returned its
+    memory (the scheduler waits); every result equals its plain join.  A
+    request that could never fit the arena is refused at submit."""
     idx = _indexes(sets)
-    roomy = agj.Server(idx, n_slots=4, max_step_requests=256, max_step_points=1 << 16)
-    full = roomy.stats()["device_bytes"]
-    roomy.close()
-    budget = full // 6                                      # less than one largest launch of four slots' worth
+    rng = np.random.default_rng(3)
+    reqs = []
+    for k in range(60):              # 15 000 - 20 000 points: any two exceed 1.3 x the largest
+        s_ = int(rng.integers(0, len(sets)))
+        n = int(rng.integers(15_000, 20_001))
+        start = int(rng.integers(0, sets[s_][1].shape[0] - n))
+        reqs.append((s_ + (len(sets) if k % 3 == 2 else 0), sets[s_][1][start:start + n]))
+    # the launch bytes of the largest request: one slot, one request per launch
+    probe = agj.Server(idx, n_slots=1, max_step_requests=1, max_step_points=1 << 15, stage_points=True)
+    for t in [probe.submit(i, p) for i, p in reqs]:
+        probe.poll(t)
+    one = probe.stats()["peak_bytes_in_use"]
+    probe.close()
+    assert one > 0
+    budget = int(1.3 * one)
     srv = agj.Server(idx, n_slots=4, max_step_requests=256, max_step_points=1 << 16, hbm_budget_bytes=budget,
                      stage_points=True)
     assert srv.stats()["device_bytes"] <= budget
-    # large requests (10 000 - 20 000 points): only a few fit the arena at once
-    rng = np.random.default_rng(3)
-    reqs = []
-    for k in range(120):
-        s_ = int(rng.integers(0, len(sets)))
-        n = int(rng.integers(10_000, 20_001))
-        start = int(rng.integers(0, sets[s_][1].shape[0] - n))
-        reqs.append((s_ + (len(sets) if k % 3 == 2 else 0), sets[s_][1][start:start + n]))
-    tickets, refused = [], 0
-    for i, p in reqs:
-        try:
-            tickets.append((srv.submit(i, p), i, p))
-        except agj.AgjError as e:
-            assert e.status == 3                            # AGJ_EBUDGET: alone it would not fit
-            refused += 1
+    tickets = [(srv.submit(i, p), i, p) for i, p in reqs]
     outs = [(srv.poll(t), i, p) for t, i, p in tickets]
     st = srv.stats()
-    assert refused == 0 and st["memory_waits"] > 0 and 0 < st["peak_bytes_in_use"] <= st["device_bytes"]
-    assert st["completed"] == len(tickets)
+    assert st["steps"] == len(reqs) and st["step_requests_max"] == 1
+    assert 0 < st["peak_bytes_in_use"] <= budget and st["memory_waits"] > 0
     for (off, ids, res), i, p in outs:
         ref = _plain(torch, agj, idx[i], p)
         assert np.array_equal(off, ref[0]) and np.array_equal(ids, ref[1])
