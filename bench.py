@@ -39,8 +39,9 @@ LAUNCHES_PER_STEP = {"approx": 4, "exact": 8}
 # from one `ncu --set full` capture of a 16e6-point join of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the points); a full
 # launch's traffic scales with its points (the trie gathers per point do not
-# depend on n).  Must be re-captured whenever a probe kernel changes.
-PROBE_DRAM_BYTES_PER_POINT = {"k_probe_approx": 24.93, "k_probe_exact": 25.22}
+# depend on n).  Re-captured whenever a probe kernel changes (empty: the
+# kernels changed since the last capture, traffic reported as null).
+PROBE_DRAM_BYTES_PER_POINT = {}
 
 
 def parse():

@@ -372,6 +372,33 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
     return x;
 }
 
+// The first queue slot of each lane's candidates within its tile (lane-major,
+// then point k: the lane's slots are the exclusive warp prefix of its
+// candidate total csum) and the tile's total.  Nearly every candidate point
+// has one candidate reference, so when no point of the warp has more, the
+// prefix is a popcount of two ballots per point slot; otherwise a warp scan.
+template <int PPT>
+__device__ __forceinline__ uint32_t tile_slot_base(const uint32_t* nc, uint32_t csum, uint32_t* total) {
+    bool multi = false;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) multi |= nc[k] > 1;
+    if (__any_sync(kFull, multi)) {
+        const uint32_t x = warp_incl_scan(csum);
+        *total = __shfl_sync(kFull, x, 31);
+        return x - csum;
+    }
+    const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
+    uint32_t base = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint32_t m = __ballot_sync(kFull, nc[k] != 0);
+        base += __popc(m & lt);
+        tot += __popc(m);
+    }
+    *total = tot;
+    return base;
+}
+
 // Per-CTA setup shared by the probe kernels: the Hilbert table in shared
 // memory and, when every tile of the CTA probes the same index X (else
 // null), its face table and, with the fast model, the model face's root
@@ -560,8 +587,8 @@ template <int PPT>
 __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, const uint32_t* nc, uint32_t csum,
                                            uint64_t wt, uint64_t gbase, uint32_t gpoly0, const JoinScratch& S) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t x = warp_incl_scan(csum);
-    const uint32_t wtotal = __shfl_sync(kFull, x, 31);
+    uint32_t wtotal;
+    const uint32_t first = tile_slot_base<PPT>(nc, csum, &wtotal);
     if (lane == 0) {
         S.tile_cand[wt] = wtotal;
         if (wtotal) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
@@ -571,7 +598,7 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
         if (lane == 0) atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrQueueOverflow);
         return;
     }
-    uint64_t q = wt * S.tile_slots + x - csum;
+    uint64_t q = wt * S.tile_slots + first;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (!nc[k]) continue;
@@ -652,13 +679,14 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
     }
     warp_count2(gathers, fallbacks, &J.status[3], &J.counters[0]);
     const bool exact = job_exact<MODE>(J);
-    uint32_t nc[PPT], csum = 0, tsum = 0;
+    uint32_t nc[PPT], csum = 0, tsum = 0;    // nc: candidates the point queues (none for approximate jobs)
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        uint32_t nt;
-        entry_counts(J.X, e[k], &nt, &nc[k]);
-        tsum += exact ? nt : nt + nc[k];
-        csum += exact ? nc[k] : 0u;
+        uint32_t nt, n_cand;
+        entry_counts(J.X, e[k], &nt, &n_cand);
+        tsum += exact ? nt : nt + n_cand;
+        nc[k] = exact ? n_cand : 0u;
+        csum += nc[k];
         S.entries[gbase + lane + 32 * k] = e[k];        // 0 for padding lanes
     }
     tsum = __reduce_add_sync(kFull, tsum);
@@ -898,7 +926,8 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
             mx = nc[k] > mx ? nc[k] : mx;
             pm[k] = 0;
         }
-        const uint32_t q0 = warp_incl_scan(csum) - csum;
+        uint32_t unused_total;
+        const uint32_t q0 = tile_slot_base<PPT>(nc, csum, &unused_total);
         mx = __reduce_max_sync(kFull, mx);
         direct = mx > 32;
         uint32_t qq = q0;
