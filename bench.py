@@ -54,9 +54,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
-    ap.add_argument("--extras", default="count,cellid,c1",
+    ap.add_argument("--extras", default="count,cellid,c1,onepass",
                     help="comma list of extra measurements: count (aggregation mode), cellid (the FP64 cell-id "
-                         "kernel), c1 (1000 tiny joins in one graph); empty for none")
+                         "kernel), c1 (1000 tiny joins in one graph), onepass (the one-pass approximate join "
+                         "against the three-kernel one); empty for none")
     ap.add_argument("--workload", choices=["c2", "c3", "c1"], default="c2",
                     help="c2: city (default); c3: 40 000 fine overlapping polygons; c1: 5 polygons, uniform points")
     ap.add_argument("--eps", type=float, default=None, help="approximate precision in metres (default per workload)")
@@ -236,6 +237,55 @@ def count_mode(agj, torch, ia, ie, d_pts, n, peaks, steps) -> dict:
 # division and square root counts once here, although the GPU expands
 # them into several FP64 instructions.
 CELL_ID_FP64_OPS = 95
+
+
+def one_pass(agj, torch, ia, d_pts, reps: int = 10) -> dict:
+    """The one-pass approximate join (probe, per-tile look-back scan and emit
+    in one kernel; the allocation-free entry point, at most 2^24 points)
+    against the three-kernel join (probe, scan, emit) on the same first
+    2^24 - 1 resident points, both into device outputs."""
+    import ctypes as C
+    import numpy as np
+    n = min(int(d_pts.shape[0]), (1 << 24) - 1)
+    pts = d_pts[:n]
+    L = agj.lib()
+    fn = L.agj_join_approx_noalloc
+    fn.restype = C.c_int
+    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
+    cap = n * max(ia.stats()["max_refs"], 1)
+    off = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+    st = torch.empty(4, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def run_one():
+        rc = fn(ia.handle, C.c_void_p(pts.data_ptr()), n, C.c_void_p(off.data_ptr()), C.c_void_p(ids.data_ptr()), cap,
+                C.c_void_p(st.data_ptr()), C.c_void_p(s.cuda_stream))
+        assert rc == 0
+
+    pr = agj.Pairs(ia, n)
+
+    def timed(fn_):
+        fn_()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = _event(torch, s), _event(torch, s)
+            a.record(s)
+            fn_()
+            b.record(s)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t1 = timed(run_one)
+    t3 = timed(lambda: agj.join(ia, pts, pr))
+    o3, i3 = pr.to_host()
+    same = bool(np.array_equal(off.cpu().numpy().view(np.uint32), o3) and
+                np.array_equal(ids[:len(i3)].cpu().numpy().view(np.uint32), i3))
+    return {"points": n, "one_pass_ms": t1, "three_kernel_ms": t3, "identical_output": same,
+            "note": "one-pass: k_join_approx (4 points per lane, a look-back per warp tile); three-kernel: "
+                    "k_probe, k_scan_counts, k_emit"}
 
 
 def cell_id_kernel(agj, torch, d_pts, n) -> dict:
@@ -705,6 +755,8 @@ def main():
     extras = set(x for x in args.extras.split(",") if x)
     if "count" in extras:
         result["count"] = count_mode(agj, torch, ia, ie, d_pts, n, peaks, args.steps)
+    if "onepass" in extras:
+        result["one_pass_vs_three_kernels"] = one_pass(agj, torch, ia, d_pts)
     if "cellid" in extras:
         result["cell_id_kernel"] = cell_id_kernel(agj, torch, d_pts, n)
         torch.cuda.empty_cache()

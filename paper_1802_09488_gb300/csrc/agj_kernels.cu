@@ -303,7 +303,8 @@ __device__ __forceinline__ void agg_add_lane(uint32_t poly, uint32_t* s_hist, ui
 template <int PPT, int MODE>
 __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
                                          const uint64_t* s_root, uint64_t wt, const JoinScratch& S, uint32_t* s_hist,
-                                         uint64_t* counts, uint32_t* pairs, uint32_t* gathers, uint32_t* fallbacks) {
+                                         uint64_t* counts, uint32_t* pairs, uint32_t* gathers, uint32_t* fallbacks,
+                                         uint32_t* s_cand) {
     constexpr bool exact = MODE == kModeExact;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t base = wt * (32 * PPT);
@@ -357,7 +358,7 @@ __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces,
             }
         }
     }
-    if constexpr (exact) queue_tile<PPT>(J, e, nc, csum, wt, base, 0, S);
+    if constexpr (exact) queue_tile<PPT>(J, e, nc, csum, wt, base, 0, S, s_cand);
 }
 
 // One warp per tile, eight tiles per CTA (the plain probe's grid).  With
@@ -375,19 +376,19 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
     __shared__ uint32_t s_hist[kAggSmemPolys];
-    __shared__ uint32_t s_tot[3];
+    __shared__ uint32_t s_tot[4];           // pairs, trie entries read, FP64 fallbacks; [3] candidates (queue_tile [2])
     const bool smem = stripes != nullptr;
     const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
     if (smem)
         for (uint32_t p = threadIdx.x; p < J.X.n_polys; p += blockDim.x) s_hist[p] = 0;
-    if (threadIdx.x < 3) s_tot[threadIdx.x] = 0;
+    if (threadIdx.x < 4) s_tot[threadIdx.x] = 0;
     cp_async_wait_all();
     __syncthreads();
     const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (wt < T) {
         uint32_t pairs = 0, gathers = 0, fallbacks = 0;
         agg_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, S, smem ? s_hist : nullptr, counts, &pairs, &gathers,
-                            &fallbacks);
+                            &fallbacks, s_tot + 1);
         const uint32_t wp = __reduce_add_sync(kFull, pairs), wg = __reduce_add_sync(kFull, gathers),
                        wf = __reduce_add_sync(kFull, fallbacks);
         if ((threadIdx.x & 31) == 0) {
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
         if (s_tot[0]) atomicAdd((unsigned long long*)&J.status[0], (unsigned long long)s_tot[0]);
         if (s_tot[1]) atomicAdd((unsigned long long*)&J.status[3], (unsigned long long)s_tot[1]);
         if (s_tot[2]) atomicAdd((unsigned long long*)&J.counters[0], (unsigned long long)s_tot[2]);
+        if (s_tot[3]) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)s_tot[3]);
     }
     if (smem) {
         uint32_t* stripe = stripes + (uint64_t)(blockIdx.x % kAggStripes) * J.X.n_polys;

@@ -583,15 +583,21 @@ __global__ void k_zero(uint64_t* __restrict__ a, uint64_t na, uint64_t* __restri
 // Exact jobs: the tile's candidate references (nc[k] of point k, csum of
 // the lane) go to the tile's own queue region, in point order (lane-major,
 // then k), so no reservation is shared between tiles.
+// The candidates queued are added to s_cnt[2] (a CTA's shared counter,
+// flushed once per CTA) or, without one, to the job's status[2].
 template <int PPT>
 __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, const uint32_t* nc, uint32_t csum,
-                                           uint64_t wt, uint64_t gbase, uint32_t gpoly0, const JoinScratch& S) {
+                                           uint64_t wt, uint64_t gbase, uint32_t gpoly0, const JoinScratch& S,
+                                           uint32_t* s_cnt = nullptr) {
     const uint32_t lane = threadIdx.x & 31;
     uint32_t wtotal;
     const uint32_t first = tile_slot_base<PPT>(nc, csum, &wtotal);
     if (lane == 0) {
         S.tile_cand[wt] = wtotal;
-        if (wtotal) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
+        if (wtotal) {
+            if (s_cnt) atomicAdd(&s_cnt[2], wtotal);
+            else atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)wtotal);
+        }
     }
     if (wtotal == 0) return;
     if (wtotal > S.tile_slots) {    // cannot happen: a point has at most the index's candidate references
@@ -636,10 +642,16 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
 // every thread of the CTA calls this (active false: a warp past the last
 // tile), and the wait and barrier come after the cell ids, before the first
 // table read.
+// With s_cnt (a CTA's shared counters: trie entries read, FP64 fallbacks,
+// candidates queued; zeroed before the CTA's barrier) the tile adds its
+// counts there and the kernel flushes them once per CTA (flush_cta_counts):
+// per-tile global atomics on the job's status words all hit one 32-byte
+// sector and serialise in its L2 slice.  Without it they go to the job's
+// status words directly.
 template <int PPT, int MODE, bool kAsync = false>
 __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
                                            const uint64_t* s_root, uint64_t wt, uint64_t lt, uint32_t gpoly0,
-                                           const JoinScratch& S, bool active = true) {
+                                           const JoinScratch& S, bool active = true, uint32_t* s_cnt = nullptr) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t base = lt * (32 * PPT);
     const uint64_t gbase = wt * (32 * PPT);
@@ -677,7 +689,15 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
         gathers = probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, J.pts + base + lane, valid, e,
                                     &J.status[1], &fallbacks);
     }
-    warp_count2(gathers, fallbacks, &J.status[3], &J.counters[0]);
+    if (s_cnt) {
+        const uint32_t g = __reduce_add_sync(kFull, gathers), f = __reduce_add_sync(kFull, fallbacks);
+        if (lane == 0) {
+            if (g) atomicAdd(&s_cnt[0], g);
+            if (f) atomicAdd(&s_cnt[1], f);
+        }
+    } else {
+        warp_count2(gathers, fallbacks, &J.status[3], &J.counters[0]);
+    }
     const bool exact = job_exact<MODE>(J);
     uint32_t nc[PPT], csum = 0, tsum = 0;    // nc: candidates the point queues (none for approximate jobs)
 #pragma unroll
@@ -692,9 +712,20 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
     tsum = __reduce_add_sync(kFull, tsum);
     if (lane == 0) S.tile_count[wt] = tsum;
     if constexpr (MODE != kModeApprox) {
-        if (S.tile_cand) queue_tile<PPT>(J, e, nc, csum, wt, gbase, gpoly0, S);
+        if (S.tile_cand) queue_tile<PPT>(J, e, nc, csum, wt, gbase, gpoly0, S, s_cnt);
     } else {
         if (S.tile_cand && lane == 0) S.tile_cand[wt] = 0;      // a batched plan's approximate tile
+    }
+}
+
+// Adds a CTA's shared counters (see probe_tile) to job J's status words
+// and diagnostics; called by every thread after the CTA's tiles.
+__device__ __forceinline__ void flush_cta_counts(const JobDesc& J, const uint32_t* s_cnt) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_cnt[0]) atomicAdd((unsigned long long*)&J.status[3], (unsigned long long)s_cnt[0]);
+        if (s_cnt[1]) atomicAdd((unsigned long long*)&J.counters[0], (unsigned long long)s_cnt[1]);
+        if (s_cnt[2]) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)s_cnt[2]);
     }
 }
 
@@ -731,20 +762,25 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
+    __shared__ uint32_t s_cnt[3];
     const uint32_t warp = threadIdx.x >> 5;
     if constexpr (Src::kSingle) {
+        if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
         const uint64_t* s_root = cta_setup_async(src.job(0).X, s_hlut, s_faces, s_rootbuf);
         const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
-        probe_tile<PPT, MODE, true>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S, wt < T);
+        probe_tile<PPT, MODE, true>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S, wt < T, s_cnt);
+        flush_cta_counts(src.job(0), s_cnt);
     } else {
         const uint64_t g0 = src.t0 / kWarpsPerBlock;
         if constexpr (!kPersist) {                                  // one CTA per 8 tiles of one job
             const uint64_t g = g0 + blockIdx.x;
             if (g * kWarpsPerBlock >= T) return;
+            if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
             const JobDesc& J = src.job(src.find_tile(g * kWarpsPerBlock));
             const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
             const uint64_t wt = g * kWarpsPerBlock + warp;
-            probe_tile<PPT, MODE, true>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S);
+            probe_tile<PPT, MODE, true>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S, true, s_cnt);
+            flush_cta_counts(J, s_cnt);
         } else {                                                    // persistent grid
             cta_setup(nullptr, s_hlut, s_faces, s_rootbuf);
             uint32_t cur = 0xFFFFFFFFu;
