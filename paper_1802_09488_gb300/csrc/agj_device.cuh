@@ -13,6 +13,12 @@ struct DevFace {
     uint32_t root;          // node index, 0xFFFFFFFF = no cells on this face
     uint32_t prefix_bits;   // key bits after the face bits (multiple of 8)
     uint64_t prefix;        // right-aligned
+    // The prefix as a cell: a leaf (i, j) lies in it iff ((i ^ pi) | (j ^ pj))
+    // & pmask == 0 (pi, pj: the cell's coordinates at level prefix_bits / 2,
+    // shifted up to level 30); o_row: the Hilbert orientation after the
+    // prefix levels, times 512 (the byte offset of its row in the walk's
+    // lookup table of 2-byte entries).
+    uint32_t pi, pj, pmask, o_row;
 };
 
 // Everything a kernel needs from one index; passed by value.

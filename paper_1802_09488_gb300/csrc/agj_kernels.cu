@@ -304,7 +304,7 @@ template <int PPT, int MODE>
 __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
                                          const uint64_t* s_root, uint64_t wt, const JoinScratch& S, uint32_t* s_hist,
                                          uint64_t* counts, uint32_t* pairs, uint32_t* gathers, uint32_t* fallbacks,
-                                         uint32_t* s_cand) {
+                                         uint32_t* s_cand, uint4* tail) {
     constexpr bool exact = MODE == kModeExact;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t base = wt * (32 * PPT);
@@ -320,7 +320,8 @@ __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces,
         }
     }
     uint64_t e[PPT];
-    *gathers += probe_cells<PPT>(J.X, faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], fallbacks);
+    *gathers += probe_cells<PPT>(J.X, faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], fallbacks,
+                                 tail);
     uint32_t nc[PPT], csum = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
@@ -377,6 +378,7 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
     __shared__ DevFace s_faces[6];
     __shared__ uint32_t s_hist[kAggSmemPolys];
     __shared__ uint32_t s_tot[4];           // pairs, trie entries read, FP64 fallbacks; [3] candidates (queue_tile [2])
+    __shared__ uint4 s_tail[kWarpsPerBlock][32 * PPT];
     const bool smem = stripes != nullptr;
     const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
     if (smem)
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
     if (wt < T) {
         uint32_t pairs = 0, gathers = 0, fallbacks = 0;
         agg_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, S, smem ? s_hist : nullptr, counts, &pairs, &gathers,
-                            &fallbacks, s_tot + 1);
+                            &fallbacks, s_tot + 1, s_tail[threadIdx.x >> 5]);
         const uint32_t wp = __reduce_add_sync(kFull, pairs), wg = __reduce_add_sync(kFull, gathers),
                        wf = __reduce_add_sync(kFull, fallbacks);
         if ((threadIdx.x & 31) == 0) {
@@ -436,6 +438,7 @@ __global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
+    __shared__ uint4 s_tail[kWarpsPerBlock][32 * kJoinPPT];
     const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -457,7 +460,8 @@ __global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
     if (!active) return;
     uint64_t e[kJoinPPT];
     uint32_t fallbacks = 0;
-    probe_cells<kJoinPPT>(J.X, s_faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], &fallbacks);
+    probe_cells<kJoinPPT>(J.X, s_faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], &fallbacks,
+                          s_tail[threadIdx.x >> 5]);
 #pragma unroll
     for (int k = 0; k < kJoinPPT; ++k) {
         uint32_t nt, nc;
@@ -490,6 +494,7 @@ __global__ void __launch_bounds__(kJoinBlock, kNoAllocMinBlocks) k_join_approx(
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
     __shared__ uint32_t s_cta;
+    __shared__ uint4 s_tail[kWarpsPerBlock][32 * PPT];
     const uint64_t* s_root = cta_setup(&X, s_hlut, s_faces, s_rootbuf);
     if (threadIdx.x == 0) s_cta = atomicAdd(tile_counter, 1u);
     __syncthreads();
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(kJoinBlock, kNoAllocMinBlocks) k_join_approx(
     uint64_t e[PPT];
     uint32_t fallbacks = 0;
     warp_count(probe_points<PPT>(X, s_faces, s_hlut, s_root, lat, lng, pts + base + lane, valid, e, &status[1],
-                                 &fallbacks),
+                                 &fallbacks, s_tail[threadIdx.x >> 5]),
                &status[3]);
     warp_count(fallbacks, fallback_counter);
     uint32_t c[PPT], ex[PPT], run = 0;
@@ -557,6 +562,34 @@ int sm_count() {
     return n;
 }
 
+// Face table entry with the prefix decoded into its cell: the quadrant of
+// each prefix level is the one whose Hilbert digit (under the orientation
+// so far) matches the prefix's.
+DevFace dev_face(int face, const FaceRoot& F) {
+    DevFace d{F.root, F.prefix_bits, F.prefix, 0u, 0u, 0u, ((uint32_t)face & 1u) << 9};
+    if (F.root == kNoRootDev) return d;
+    const int L = (int)(F.prefix_bits / 2);
+    uint32_t o = (uint32_t)face & 1u, pi = 0, pj = 0;
+    for (int l = 0; l < L; ++l) {
+        const uint32_t digit = (uint32_t)(F.prefix >> (2 * (L - 1 - l))) & 3u;
+        for (uint32_t q = 0; q < 4; ++q) {
+            uint32_t o2 = o;
+            if (hilbert_digit(q >> 1, q & 1u, &o2) == digit) {
+                pi = (pi << 1) | (q >> 1);
+                pj = (pj << 1) | (q & 1u);
+                o = o2;
+                break;
+            }
+        }
+    }
+    const int sh = kLevels - L;
+    d.pi = L ? pi << sh : 0u;
+    d.pj = L ? pj << sh : 0u;
+    d.pmask = L ? (0x3FFFFFFFu >> sh) << sh : 0u;
+    d.o_row = o << 9;
+    return d;
+}
+
 DevIndex make_dev_index(const Index& X) {
     DevIndex D;
     memset(&D, 0, sizeof D);
@@ -576,7 +609,7 @@ DevIndex make_dev_index(const Index& X) {
     D.n_lut = X.lut.size();
     D.n_polys = X.n_polys;
     D.max_depth = X.stats.max_depth;
-    for (int f = 0; f < 6; ++f) D.faces[f] = DevFace{X.faces[f].root, X.faces[f].prefix_bits, X.faces[f].prefix};
+    for (int f = 0; f < 6; ++f) D.faces[f] = dev_face(f, X.faces[f]);
     D.model = X.model;
     return D;
 }

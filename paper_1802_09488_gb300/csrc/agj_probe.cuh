@@ -21,15 +21,22 @@
 namespace agj {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-static __device__ __align__(16) const HilbertLut g_hilbert_lut = make_hilbert_lut();
+// The walk's Hilbert table: the 4-level table of make_hilbert_lut with each
+// entry rearranged to (next orientation << 9) | position byte: the next row's
+// byte offset in the table and the key byte are one mask each.
+constexpr HilbertLut make_walk_lut() {
+    HilbertLut H = make_hilbert_lut(), W{};
+    for (uint32_t idx = 0; idx < 1024; ++idx) W.v[idx] = (uint16_t)(((H.v[idx] & 3u) << 9) | (H.v[idx] >> 2));
+    return W;
+}
+static __device__ __align__(16) const HilbertLut g_hilbert_lut = make_walk_lut();
 constexpr uint32_t kSpinLimit = 1u << 22;
 // Resident CTAs per SM the probe kernels are compiled for (a register cap:
 // 65536 / (256 x blocks) per thread).  The probe is latency-bound (dependent
 // trie gathers), so more resident warps pay while the registers last: at 5
-// CTAs (40 warps, 48 registers) the exact probes, single-job and batched,
-// beat 3 and 4 CTAs on the city workload (at 6 the exact probe spills and
-// slows); the approximate probes, which queue no candidates, run at 6 CTAs
-// (48 warps, 40 registers).
+// CTAs (40 warps, 48 registers) the probes, single-job and batched, need no
+// spills and beat 4 CTAs on the city workload; at 6 (40 registers) the walk
+// spills.
 #ifndef AGJ_PROBE_MIN_BLOCKS
 #define AGJ_PROBE_MIN_BLOCKS 5
 #endif
@@ -37,7 +44,12 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 #define AGJ_BATCH_PROBE_MIN_BLOCKS 5
 #endif
 #ifndef AGJ_APPROX_PROBE_MIN_BLOCKS
-#define AGJ_APPROX_PROBE_MIN_BLOCKS 6     // approximate probes (single-job and batched): 40 registers pay there
+#define AGJ_APPROX_PROBE_MIN_BLOCKS 5
+#endif
+// Each CTA of the plain join's probe prefetches into the L2 the points of
+// the CTA one grid of resident CTAs ahead (1) or not (0).
+#ifndef AGJ_PREFETCH_AHEAD
+#define AGJ_PREFETCH_AHEAD 1
 #endif
 constexpr int kJoinBlock = 256;
 constexpr int kJoinPPT = 2;                    // points per lane of the plain join
@@ -131,20 +143,21 @@ __device__ __forceinline__ uint64_t lookback(uint64_t* tiles, uint32_t tile, uin
 // holds levels 4b+1 .. 4b+4).
 struct Walk {
     uint32_t i32, j32;      // (i, j) << (2 + 4 b): the next byte's 4 levels on top; 0 padding below
-    uint32_t o;             // Hilbert orientation before byte b, << 8 (the table's row)
-    uint32_t b;             // next key byte
+    uint32_t o;             // Hilbert orientation before byte b, << 9 (its row's byte offset in the table)
     uint32_t node;          // current trie node
-    int32_t cert;           // key bytes whose levels are all certified
+    int32_t left;           // certified key bytes left, from byte b on
     int32_t st;             // 0 done, 1 walking, 2 needs the FP64 cell id
 };
 
+// The next key byte (levels 4b+1 .. 4b+4) from the walk's Hilbert table.
 __device__ __forceinline__ uint32_t next_byte(const uint16_t* lut, Walk& w) {
-    const uint32_t e = lut[w.o | ((w.i32 >> 24) & 0xF0u) | (w.j32 >> 28)];
+    const uint32_t off = w.o | ((w.i32 >> 23) & 0x1E0u) | ((w.j32 >> 27) & 0x1Eu);
+    const uint32_t t = *reinterpret_cast<const uint16_t*>(reinterpret_cast<const char*>(lut) + off);
     w.i32 <<= 4;
     w.j32 <<= 4;
-    w.o = (e & 3u) << 8;
-    ++w.b;
-    return e >> 2;
+    w.o = t & 0x600u;
+    --w.left;
+    return t & 0xFFu;
 }
 
 // Leaf cell of a point: face, (i, j) and the leading levels certified.
@@ -175,28 +188,24 @@ __device__ __forceinline__ bool point_ij(const FastModel& M, double lat, double 
 
 // Face/prefix stage (§IV-B stage 1) for one point's leaf cell.  Leaves
 // w.st = 0 when the point joins nothing, 1 when the walk can start at
-// w.node, 2 when an uncertified level decides the prefix.
-__device__ __forceinline__ void start_walk(const DevFace* faces, const uint16_t* lut, const PointIJ& p, Walk& w) {
-    const uint32_t i = p.i, j = p.j;
-    const int lc = p.lc, face = p.face;
+// w.node, 2 when an uncertified level decides the prefix.  The prefix is
+// compared as a cell (its level-30 bounds in i and j), which equals
+// comparing the key's prefix bytes; the walk then starts at the prefix's
+// orientation with the next key byte.
+__device__ __forceinline__ void start_walk(const DevFace* faces, const uint16_t*, const PointIJ& p, Walk& w) {
     w.st = 0;
-    w.b = 0;
-    const DevFace fr = faces[face];
+    w.o = 0;
+    const DevFace fr = faces[p.face];
     if (fr.root == kNoRootDev) return;
-    w.i32 = i << 2;
-    w.j32 = j << 2;
-    w.o = ((uint32_t)face & 1u) << 8;
-    w.b = 0;
-    w.cert = lc >> 2;
-    const uint32_t nb = fr.prefix_bits >> 3;
-    for (uint32_t q = 0; q < nb; ++q) {
-        const uint32_t byte = next_byte(lut, w);
-        if (byte != (uint32_t)((fr.prefix >> (8 * (nb - 1 - q))) & 0xFFu)) {
-            w.st = (int32_t)q < w.cert ? 0 : 2;                     // certain mismatch: no cell
-            return;
-        }
-    }
-    if ((int32_t)nb > w.cert) { w.st = 2; return; }
+    const int32_t nb = (int32_t)(fr.prefix_bits >> 3);
+    const int32_t left = (p.lc >> 2) - nb;
+    if (left < 0) { w.st = 2; return; }
+    if (((p.i ^ fr.pi) | (p.j ^ fr.pj)) & fr.pmask) return;
+    const uint32_t sh = 2u + 4u * (uint32_t)nb;
+    w.i32 = p.i << sh;
+    w.j32 = p.j << sh;
+    w.o = fr.o_row;
+    w.left = left;
     w.node = fr.root;
     w.st = 1;
 }
@@ -205,109 +214,163 @@ __device__ __forceinline__ void begin_walk(const DevIndex& X, const DevFace* fac
                                            double lng, bool exact, Walk& w) {
     PointIJ p;
     w.st = 0;
-    w.b = 0;
+    w.o = 0;
     if (point_ij(X.model, lat, lng, exact, p)) start_walk(faces, lut, p, w);
+}
+
+// Trie levels every walk of a warp takes in step before the unfinished ones
+// are compacted (root + two levels: nearly every walk of the city-scale
+// indexes needs them, about one in eight needs more).
+#ifndef AGJ_LOCK_LEVELS
+#define AGJ_LOCK_LEVELS 3
+#endif
+constexpr int kLockLevels = AGJ_LOCK_LEVELS;
+
+// One level of a walk (Listing "Probe Adaptive Cell Trie"), without
+// branches: a live walk whose next key byte is certified reads that byte's
+// entry (from the shared copy of the root with kRoot) into v and either
+// descends or ends there; one whose next byte is not certified is marked
+// for the FP64 id (st 2).  v keeps the last entry read, which is the walk's
+// result once it ends.  Finished walks step along harmlessly (their key
+// state is not used again).  Child entries hold node << 11 with 0 < node <
+// n_nodes (node 0 is a root, never a child), so one unsigned compare of
+// (v >> 11) - 1 with nn1 = n_nodes - 1 keeps every read in bounds; a walk
+// that ends on a tag-0 entry other than the sentinel (a child out of range)
+// is caught by walk_end_bad.  Returns whether an entry was read.
+template <bool kRoot>
+__device__ __forceinline__ uint32_t walk_step(const uint64_t* nodes, const uint64_t* root, const uint16_t* lut,
+                                              Walk& w, uint64_t& v, uint32_t nn1) {
+    const bool live = w.st == 1;
+    const bool go = live && w.left > 0;
+    const uint32_t byte = next_byte(lut, w);
+    if (go) v = kRoot ? root[byte] : __ldg(nodes + (size_t)w.node * 256u + byte);
+    const uint32_t lo = (uint32_t)v, child = (uint32_t)(v >> 11);
+    const bool ptr = (lo & 3u) == 0u && child - 1u < nn1;
+    if (go && ptr) w.node = child;
+    if (live) w.st = go ? (ptr ? 1 : 0) : 2;
+    return go ? 1u : 0u;
+}
+
+// A walk that ended (st 0) on a tag-0 entry other than the sentinel read a
+// child pointer outside the node array.
+__device__ __forceinline__ bool walk_end_bad(const Walk& w, uint64_t v) {
+    return w.st == 0 && ((uint32_t)v & 3u) == 0u && v != 0ull;
 }
 
 // Walks of PPT points (w, after their face/prefix stage) advance level by
 // level together, so their gathers (Listing "Probe Adaptive Cell Trie") are
-// in flight at the same time.  Points whose walk needs an uncertified key
-// byte get their FP64 id and walk again alone (counted in *fallbacks); they
-// reload their coordinates from pts[32 k] (the lane's points), so lat/lng
-// need no registers during the walk.  Returns the trie entries read.
+// in flight at the same time.  After kLockLevels levels the walks still
+// unfinished in the warp (tail: the warp's 32 PPT-entry shared buffer) are
+// packed one per lane, so the deep levels of a few walks do not hold the
+// whole warp for PPT slots each; their results come back through the same
+// buffer.  Without a buffer the walks go on in step.  Points whose walk
+// needs an uncertified key byte get their FP64 id and walk again alone
+// (counted in *fallbacks); they reload their coordinates from pts[32 k]
+// (the lane's points), so lat/lng need no registers during the walk.
+// Returns the trie entries read.
 template <int PPT>
 __device__ __forceinline__ uint32_t walk_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
                                                 const uint64_t* s_root, Walk* w, const double2* pts, uint64_t e[PPT],
-                                                uint64_t* err, uint32_t* fallbacks) {
-    uint32_t gathers = 0;
+                                                uint64_t* err, uint32_t* fallbacks, uint4* tail) {
+    uint32_t gathers = 0, bad = 0;
+    const uint64_t* nodes = X.nodes;
+    const uint32_t nn1 = (uint32_t)min(X.n_nodes, (uint64_t)0xFFFFFFFFu) - 1u;   // an index with walks has nodes
+    uint64_t v[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) e[k] = 0;
-    uint32_t prefix_bytes[PPT];
+    for (int k = 0; k < PPT; ++k) v[k] = 0;
+    if (s_root) {
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) prefix_bytes[k] = w[k].b;
-    const uint32_t n_nodes32 = (uint32_t)min(X.n_nodes, (uint64_t)0xFFFFFFFFu);
-#pragma unroll 1
-    for (int d = 0; d < 8; ++d) {
-        uint64_t v[PPT];
-        if (d == 0 && s_root) {
-            // with the fast model every walk starts at the model face's root,
-            // which each CTA holds in shared memory
+        for (int k = 0; k < PPT; ++k) gathers += walk_step<true>(nodes, s_root, lut, w[k], v[k], nn1);
+    } else {
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                v[k] = 0;
-                if (w[k].st == 1) {
-                    if (w[k].b >= (uint32_t)w[k].cert) w[k].st = 2;
-                    else v[k] = s_root[next_byte(lut, w[k])];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                v[k] = 0;
-                if (w[k].st == 1) {
-                    if (w[k].b >= (uint32_t)w[k].cert) {
-                        w[k].st = 2;
-                    } else {
-                        const uint32_t byte = next_byte(lut, w[k]);
-                        const uint64_t* row = X.nodes + (size_t)w[k].node * 256u;
-                        v[k] = __ldg(row + byte);
-                    }
-                }
-            }
-        }
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            if (w[k].st != 1) continue;
-            // child entries hold node << 11 with node < 2^32, so the low 32 bits
-            // of (v >> 11) name the node; checking them keeps every read in bounds
-            const uint32_t child = (uint32_t)(v[k] >> 11);
-            if ((v[k] & 3ull) != 0ull || v[k] == 0ull) {
-                e[k] = v[k];
-                w[k].st = 0;
-            } else if (child >= n_nodes32) {
-                atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
-                w[k].st = 0;
-            } else {
-                w[k].node = child;
-                any = true;
-            }
-        }
-        if (!any) break;
+        for (int k = 0; k < PPT; ++k) gathers += walk_step<false>(nodes, nullptr, lut, w[k], v[k], nn1);
     }
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) gathers += w[k].b - prefix_bytes[k];
+    for (int d = 1; d < kLockLevels; ++d) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) gathers += walk_step<false>(nodes, nullptr, lut, w[k], v[k], nn1);
+    }
+    uint32_t m[PPT], any = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
+        m[k] = __ballot_sync(kFull, w[k].st == 1);
+        any |= m[k];
+    }
+    if (any) {
+        if (tail) {
+            const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+            uint32_t rank[PPT], n_tail = 0;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                rank[k] = n_tail + __popc(m[k] & lt);
+                n_tail += __popc(m[k]);
+                if (w[k].st == 1)
+                    tail[rank[k]] = make_uint4(w[k].i32, w[k].j32, w[k].node, w[k].o | ((uint32_t)w[k].left << 11));
+            }
+            __syncwarp();
+            for (uint32_t r0 = 0; r0 < n_tail; r0 += 32) {      // warp-uniform: one round unless > 32 walks
+                const uint32_t r = r0 + lane;
+                Walk x;
+                x.st = 0;
+                x.o = 0;
+                x.i32 = x.j32 = x.node = 0;
+                x.left = 0;
+                uint64_t vx = 0;
+                if (r < n_tail) {
+                    const uint4 q = tail[r];
+                    x.i32 = q.x;
+                    x.j32 = q.y;
+                    x.node = q.z;
+                    x.o = q.w & 0x600u;
+                    x.left = (int32_t)(q.w >> 11);
+                    x.st = 1;
+                }
+                while (__any_sync(kFull, x.st == 1)) gathers += walk_step<false>(nodes, nullptr, lut, x, vx, nn1);
+                if (walk_end_bad(x, vx)) bad = 1u;
+                if (r < n_tail) tail[r] = make_uint4((uint32_t)vx, (uint32_t)(vx >> 32), (uint32_t)x.st, 0u);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (w[k].st == 1) {
+                    const uint4 q = tail[rank[k]];
+                    v[k] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+                    w[k].st = (int32_t)q.z;
+                }
+            }
+            __syncwarp();      // the buffer is free for the warp's next tile
+        } else {
+            // every walk ends within 8 key bytes (its certified bytes run out)
+            bool more = true;
+            for (int d = kLockLevels; d < 8 && more; ++d) {
+                more = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    gathers += walk_step<false>(nodes, nullptr, lut, w[k], v[k], nn1);
+                    more |= w[k].st == 1;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (walk_end_bad(w[k], v[k])) bad = 1u;
+        e[k] = w[k].st == 0 ? v[k] : 0ull;
         if (w[k].st == 1) {
-            atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
-            e[k] = 0;
+            bad = 1u;
         } else if (w[k].st == 2) {
             ++*fallbacks;
             Walk x;
             const double2 q = pts[32 * k];
             begin_walk(X, faces, lut, q.x, q.y, true, x);
-            e[k] = 0;
-            while (x.st == 1) {
-                if (x.b >= 8u) {
-                    atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
-                    break;
-                }
-                const uint32_t byte = next_byte(lut, x);
-                const uint64_t v = __ldg(X.nodes + (((uint64_t)x.node) << 8) + byte);
-                ++gathers;
-                if ((v & 3ull) != 0ull || v == 0ull) {
-                    e[k] = v;
-                    break;
-                }
-                if ((v >> 11) >= X.n_nodes) {
-                    atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
-                    break;
-                }
-                x.node = (uint32_t)(v >> 11);
-            }
+            uint64_t vx = 0;
+            while (x.st == 1) gathers += walk_step<false>(nodes, nullptr, lut, x, vx, nn1);
+            // the FP64 id certifies every byte: a walk that uses them all up is corrupt
+            if (x.st == 2 || walk_end_bad(x, vx)) bad = 1u;
+            e[k] = x.st == 0 ? vx : 0ull;
         }
     }
+    if (bad) atomicOr((unsigned long long*)err, (unsigned long long)kErrTrieBounds);
     return gathers;
 }
 
@@ -317,15 +380,15 @@ template <int PPT>
 __device__ __forceinline__ uint32_t probe_cells(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
                                                 const uint64_t* s_root, const PointIJ* p, const bool* ok,
                                                 const double2* pts, uint64_t e[PPT], uint64_t* err,
-                                                uint32_t* fallbacks) {
+                                                uint32_t* fallbacks, uint4* tail) {
     Walk w[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         w[k].st = 0;
-        w[k].b = 0;
+        w[k].o = 0;
         if (ok[k]) start_walk(faces, lut, p[k], w[k]);
     }
-    return walk_points<PPT>(X, faces, lut, s_root, w, pts, e, err, fallbacks);
+    return walk_points<PPT>(X, faces, lut, s_root, w, pts, e, err, fallbacks, tail);
 }
 
 // The probe of PPT points from their coordinates (valid[k] false: padding
@@ -334,15 +397,15 @@ template <int PPT>
 __device__ __forceinline__ uint32_t probe_points(const DevIndex& X, const DevFace* faces, const uint16_t* lut,
                                                  const uint64_t* s_root, const double* lat, const double* lng,
                                                  const double2* pts, const bool* valid, uint64_t e[PPT],
-                                                 uint64_t* err, uint32_t* fallbacks) {
+                                                 uint64_t* err, uint32_t* fallbacks, uint4* tail) {
     Walk w[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         w[k].st = 0;
-        w[k].b = 0;
+        w[k].o = 0;
         if (valid[k]) begin_walk(X, faces, lut, lat[k], lng[k], false, w[k]);
     }
-    return walk_points<PPT>(X, faces, lut, s_root, w, pts, e, err, fallbacks);
+    return walk_points<PPT>(X, faces, lut, s_root, w, pts, e, err, fallbacks, tail);
 }
 
 // Adds two per-thread counts (a < 2^15, b < 2^7 per thread) to two device
@@ -423,6 +486,14 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Bulk L2 prefetch of points p0 .. p0 + count - 1 (clipped to n; 16 bytes
+// each, so the range is 16-byte aligned and a multiple of 16 bytes).
+__device__ __forceinline__ void prefetch_points_l2(const double2* pts, uint64_t n, uint64_t p0, uint64_t count) {
+    if (p0 >= n) return;
+    const uint64_t c = min(count, n - p0);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pts + p0), "r"((uint32_t)(c * 16)) : "memory");
+}
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -651,44 +722,31 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
 template <int PPT, int MODE, bool kAsync = false>
 __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
                                            const uint64_t* s_root, uint64_t wt, uint64_t lt, uint32_t gpoly0,
-                                           const JoinScratch& S, bool active = true, uint32_t* s_cnt = nullptr) {
+                                           const JoinScratch& S, bool active = true, uint32_t* s_cnt = nullptr,
+                                           uint4* tail = nullptr) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t base = lt * (32 * PPT);
     const uint64_t gbase = wt * (32 * PPT);
     uint64_t e[PPT];
     uint32_t fallbacks = 0;
-    uint32_t gathers;
-    if constexpr (kAsync) {
-        PointIJ pij[PPT];
-        bool ok[PPT];
+    PointIJ pij[PPT];
+    bool ok[PPT];
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const uint64_t p = base + lane + 32 * k;
-            ok[k] = false;
-            if (active && p < J.n) {
-                const double2 q = __ldcs(J.pts + p);     // streamed once
-                ok[k] = point_ij(J.X.model, q.x, q.y, false, pij[k]);
-            }
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = base + lane + 32 * k;
+        ok[k] = false;
+        if (active && p < J.n) {
+            const double2 q = __ldcs(J.pts + p);     // streamed once
+            ok[k] = point_ij(J.X.model, q.x, q.y, false, pij[k]);
         }
+    }
+    if constexpr (kAsync) {
         cp_async_wait_all();
         __syncthreads();
-        if (!active) return;
-        gathers = probe_cells<PPT>(J.X, faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1],
-                                   &fallbacks);
-    } else {
-        double lat[PPT], lng[PPT];
-        bool valid[PPT];
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const uint64_t p = base + lane + 32 * k;
-            valid[k] = p < J.n;
-            const double2 q = valid[k] ? __ldcs(J.pts + p) : make_double2(0.0, 0.0);   // streamed once
-            lat[k] = q.x;
-            lng[k] = q.y;
-        }
-        gathers = probe_points<PPT>(J.X, faces, s_hlut, s_root, lat, lng, J.pts + base + lane, valid, e,
-                                    &J.status[1], &fallbacks);
     }
+    if (!active) return;
+    const uint32_t gathers = probe_cells<PPT>(J.X, faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e,
+                                              &J.status[1], &fallbacks, tail);
     if (s_cnt) {
         const uint32_t g = __reduce_add_sync(kFull, gathers), f = __reduce_add_sync(kFull, fallbacks);
         if (lane == 0) {
@@ -763,12 +821,22 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
     __shared__ uint32_t s_cnt[3];
+    __shared__ uint4 s_tail[kWarpsPerBlock][32 * PPT];
     const uint32_t warp = threadIdx.x >> 5;
     if constexpr (Src::kSingle) {
         if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
         const uint64_t* s_root = cta_setup_async(src.job(0).X, s_hlut, s_faces, s_rootbuf);
+        if (threadIdx.x == 32) {
+            // the points of the CTA one full grid of resident CTAs ahead go
+            // to the L2 now, so that CTA finds them there
+            uint32_t nsm;
+            asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+            const uint64_t group_pts = (uint64_t)kWarpsPerBlock * 32 * PPT;
+            const uint64_t ahead = (uint64_t)nsm * (MODE == kModeApprox ? AGJ_APPROX_PROBE_MIN_BLOCKS : AGJ_PROBE_MIN_BLOCKS);
+            if (AGJ_PREFETCH_AHEAD) prefetch_points_l2(src.job(0).pts, src.job(0).n, (blockIdx.x + ahead) * group_pts, group_pts);
+        }
         const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
-        probe_tile<PPT, MODE, true>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S, wt < T, s_cnt);
+        probe_tile<PPT, MODE, true>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S, wt < T, s_cnt, s_tail[warp]);
         flush_cta_counts(src.job(0), s_cnt);
     } else {
         const uint64_t g0 = src.t0 / kWarpsPerBlock;
@@ -779,7 +847,8 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
             const JobDesc& J = src.job(src.find_tile(g * kWarpsPerBlock));
             const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
             const uint64_t wt = g * kWarpsPerBlock + warp;
-            probe_tile<PPT, MODE, true>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S, true, s_cnt);
+            probe_tile<PPT, MODE, true>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S, true, s_cnt,
+                                        s_tail[warp]);
             flush_cta_counts(J, s_cnt);
         } else {                                                    // persistent grid
             cta_setup(nullptr, s_hlut, s_faces, s_rootbuf);
@@ -793,7 +862,8 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
                     cur = j;
                 }
                 const uint64_t wt = g * kWarpsPerBlock + warp;
-                probe_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S);
+                probe_tile<PPT, MODE>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S, true, nullptr,
+                                      s_tail[warp]);
             }
         }
     }
