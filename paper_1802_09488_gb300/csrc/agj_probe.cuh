@@ -675,29 +675,25 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
         if (lane == 0) atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrQueueOverflow);
         return;
     }
-    uint64_t q = wt * S.tile_slots + first;
+    uint2* q = S.queue + wt * S.tile_slots + first;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        if (!nc[k]) continue;
         const uint32_t g = (uint32_t)(gbase + lane + 32 * k);     // global point index
         const uint64_t ek = e[k];
         const uint32_t tag = (uint32_t)(ek & 3ull);
-        const uint32_t* Cc = nullptr;
-        if (tag == 3) {
+        if (tag != 3) {
+            // inline references (nearly every candidate): candidate = interior bit clear
+            const uint32_t p0 = payload_of(ek, 0), p1 = payload_of(ek, 1);
+            const bool c0 = nc[k] != 0 && (p0 & 1u) == 0u;
+            const bool c1 = tag == 2 && (p1 & 1u) == 0u;
+            if (c0) *q = make_uint2(g, gpoly0 + (p0 >> 1));
+            if (c1) q[c0 ? 1 : 0] = make_uint2(g, gpoly0 + (p1 >> 1));
+            q += nc[k];
+        } else if (nc[k]) {
             const uint32_t off = payload_of(ek, 0);
-            Cc = J.X.lut + off + 2 + __ldg(J.X.lut + off);
-        }
-        for (uint32_t t = 0, r = 0; t < nc[k]; ++r) {
-            uint32_t poly;
-            if (tag == 3) {
-                poly = __ldg(Cc + r);
-            } else {
-                const uint32_t pl = payload_of(ek, (int)r);
-                if (pl & 1u) continue;          // a true reference
-                poly = pl >> 1;
-            }
-            ++t;
-            S.queue[q++] = make_uint2(g, gpoly0 + poly);
+            const uint32_t* Cc = J.X.lut + off + 2 + __ldg(J.X.lut + off);
+            for (uint32_t r = 0; r < nc[k]; ++r) q[r] = make_uint2(g, gpoly0 + __ldg(Cc + r));
+            q += nc[k];
         }
     }
 }
@@ -1050,12 +1046,20 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
         const uint8_t* sp = s_pass + (threadIdx.x & ~31u);
         const uint8_t* gp = S.pass + wt * S.tile_slots;
         if (!direct) {
+            // inline entries queue at most two candidates: their two result
+            // bytes unrolled; longer lists (lookup-table cells) in a loop
 #pragma unroll
-            for (int k = 0; k < PPT; ++k)
-                for (uint32_t t = 0; t < nc[k]; ++t) {
+            for (int k = 0; k < PPT; ++k) {
+#pragma unroll
+                for (uint32_t t = 0; t < 2; ++t) {
+                    const uint32_t idx = qb[k] + t;
+                    if (t < nc[k] && (idx < 32 ? sp[idx] : gp[idx])) pm[k] |= 1u << t;
+                }
+                for (uint32_t t = 2; t < nc[k]; ++t) {
                     const uint32_t idx = qb[k] + t;
                     if (idx < 32 ? sp[idx] : gp[idx]) pm[k] |= 1u << t;
                 }
+            }
         }
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -1104,11 +1108,19 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
         const uint8_t* pd = S.pass + wt * S.tile_slots + qb[k];     // the results themselves (direct)
         uint64_t w = o;
         uint32_t ci = 0;
-        if (tag == 1 || tag == 2) {
+        if ((tag == 1 || tag == 2) && !direct) {
+            // a true reference is kept, a candidate when its result bit is
+            // set (bit 0 for the first candidate, bit 1 for a second)
+            const uint32_t p0 = payload_of(ek, 0), p1 = payload_of(ek, 1);
+            const bool keep0 = (p0 & 1u) || (ps & 1u);
+            const bool keep1 = tag == 2 && ((p1 & 1u) || ((ps >> ((p0 & 1u) ? 0 : 1)) & 1u));
+            if (keep0) J.ids[w] = p0 >> 1;
+            if (keep1) J.ids[w + (keep0 ? 1 : 0)] = p1 >> 1;
+        } else if (tag == 1 || tag == 2) {
             for (int t = 0; t < (int)tag; ++t) {
                 const uint32_t pl = payload_of(ek, t);
                 if (pl & 1u) J.ids[w++] = pl >> 1;
-                else if (direct ? pd[ci++] : (ps >> ci++) & 1u) J.ids[w++] = pl >> 1;
+                else if (pd[ci++]) J.ids[w++] = pl >> 1;
             }
         } else if (tag == 3) {
             const uint32_t off = payload_of(ek, 0);
