@@ -92,22 +92,25 @@ __device__ __forceinline__ uint64_t walk_exact(const DevIndex& X, const DevFace*
     return 0;
 }
 
-// Number of references (true + candidate) an entry holds: tag 1 one inline
-// reference (none with the invalid payload), tag 2 two, tag 3 the lookup
-// table's lists; the inline cases without branches.
+// Number of references (true + candidate) an entry holds.
 __device__ __forceinline__ void entry_counts(const DevIndex& X, uint64_t e, uint32_t* n_true, uint32_t* n_cand) {
     const uint32_t tag = (uint32_t)(e & 3ull);
-    const uint32_t p1 = (uint32_t)(e >> 2) & 0x7FFFFFFFu, p2 = (uint32_t)(e >> 33) & 0x7FFFFFFFu;
-    const uint32_t has1 = (tag == 2u || (tag == 1u && p1 != kInvalidPayloadDev)) ? 1u : 0u;
-    const uint32_t has2 = tag == 2u ? 1u : 0u;
-    uint32_t nt = (has1 & p1) + (has2 & p2);
-    uint32_t nc = has1 + has2 - nt;
-    if (tag == 3u) {
-        nt = __ldg(X.lut + p1);
-        nc = __ldg(X.lut + p1 + 1 + nt);
+    *n_true = 0;
+    *n_cand = 0;
+    if (tag == 1) {
+        const uint32_t p = (uint32_t)(e >> 2) & 0x7FFFFFFFu;
+        if (p == kInvalidPayloadDev) return;
+        if (p & 1u) *n_true = 1; else *n_cand = 1;
+    } else if (tag == 2) {
+        const uint32_t p1 = (uint32_t)(e >> 2) & 0x7FFFFFFFu, p2 = (uint32_t)(e >> 33) & 0x7FFFFFFFu;
+        *n_true = (p1 & 1u) + (p2 & 1u);
+        *n_cand = 2 - *n_true;
+    } else if (tag == 3) {
+        const uint32_t off = (uint32_t)(e >> 2) & 0x7FFFFFFFu;
+        const uint32_t nt = __ldg(X.lut + off);
+        *n_true = nt;
+        *n_cand = __ldg(X.lut + off + 1 + nt);
     }
-    *n_true = nt;
-    *n_cand = nc;
 }
 
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
