@@ -62,6 +62,8 @@ def _load():
             "or_uv_dist_m": (d, [i32, d, d, d, d]),
             "or_cell_diag_m": (d, [u64]),
             "or_ring_covers_uv": (i32, [P, i64, d, d]),
+            "or_ring_relate_uv": (i32, [P, i64, d, d]),
+            "or_polyset_set_contains": (None, [P, i32]),
             "or_polyset_new": (P, [P, P, i64, i32]),
             "or_polyset_free": (None, [P]),
             "or_polyset_face": (i32, [P, i64]),
@@ -165,6 +167,12 @@ def ring_covers_uv(uv: np.ndarray, pu: float, pv: float) -> bool:
     return bool(_load().or_ring_covers_uv(_ptr(a), len(a), float(pu), float(pv)))
 
 
+def ring_relate_uv(uv: np.ndarray, pu: float, pv: float) -> int:
+    """0 exterior, 1 on the boundary, 2 interior of the ring."""
+    a = np.ascontiguousarray(uv, dtype=np.float64).reshape(-1, 2)
+    return int(_load().or_ring_relate_uv(_ptr(a), len(a), float(pu), float(pv)))
+
+
 def flatten_polygons(polys) -> tuple[np.ndarray, np.ndarray]:
     """list of (V,2) (lat,lng) arrays -> (latlng (N,2) f64, offsets (P+1,) i64)."""
     off = np.zeros(len(polys) + 1, dtype=np.int64)
@@ -180,11 +188,14 @@ def flatten_polygons(polys) -> tuple[np.ndarray, np.ndarray]:
 class PolySet:
     """Polygons prepared in face (u,v) with a uniform-grid prefilter."""
 
-    def __init__(self, polys, grid_n: int = 64):
+    def __init__(self, polys, grid_n: int = 64, contains: bool = False):
+        """contains: join by ST_Contains (boundary points excluded) instead of
+        ST_Covers (= ST_Intersects for a point)."""
         self._lib = _load()
         self.latlng, self.off = flatten_polygons(polys)
         self.n = len(polys)
         self._h = self._lib.or_polyset_new(_ptr(self.latlng), _ptr(self.off), self.n, int(grid_n))
+        self._lib.or_polyset_set_contains(self._h, 1 if contains else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -377,7 +377,19 @@ static double or_angle_point_arc(const double p[3], const double a[3], const dou
  *     (b.v <= p.v < a.v and o < 0)                     -> toggle
  *   odd number of toggles -> covered.
  */
+int or_ring_relate_uv(const double *uv, int64_t n, double pu, double pv);
 int or_ring_covers_uv(const double *uv, int64_t n, double pu, double pv) {
+    return or_ring_relate_uv(uv, n, pu, pv) != 0;
+}
+
+/* Where the point lies relative to the ring: 0 exterior, 1 on the boundary
+ * (the on-edge case of the ring rule above), 2 interior (odd crossings and
+ * on no edge).  ST_Covers (and ST_Intersects, which for a point and a
+ * polygon is the same predicate) holds for 1 and 2; ST_Contains, which
+ * excludes the boundary, for 2 only (§II: the paper's predicate is
+ * ST_Covers; other predicates "can be implemented with similar
+ * techniques"). */
+int or_ring_relate_uv(const double *uv, int64_t n, double pu, double pv) {
     int inside = 0;
     for (int64_t k = 0; k < n; ++k) {
         const double *a = uv + 2 * k;
@@ -389,7 +401,7 @@ int or_ring_covers_uv(const double *uv, int64_t n, double pu, double pv) {
         if ((a[1] <= pv && pv < b[1] && o > 0.0) || (b[1] <= pv && pv < a[1] && o < 0.0))
             inside = !inside;
     }
-    return inside;
+    return inside ? 2 : 0;
 }
 
 /* A polygon set: vertices in (lat, lng) degrees, ring k spans
@@ -406,6 +418,7 @@ typedef struct {
     int g_used[6];
     int64_t *g_start[6];   /* grid_n*grid_n + 1 */
     int32_t *g_items[6];
+    int contains;          /* 0: ST_Covers / ST_Intersects, 1: ST_Contains (boundary excluded) */
 } or_polyset;
 
 static int or_cmp_i32(const void *a, const void *b) {
@@ -512,14 +525,26 @@ or_polyset *or_polyset_new(const double *latlng, const int64_t *off, int64_t n_p
 
 int or_polyset_face(const or_polyset *ps, int64_t k) { return ps->face[k]; }
 
-/* ST_Covers(P_k, p): same face, inside the closed uv bbox, ring rule. */
+/* Selects the join predicate of the set: 0 ST_Covers (ST_Intersects is the
+ * same predicate for a point), 1 ST_Contains. */
+void or_polyset_set_contains(or_polyset *ps, int contains) { ps->contains = contains ? 1 : 0; }
+
+/* The set's predicate for a point already in face (u,v) on the polygon's
+ * face. */
+static int or_pred_uv(const or_polyset *ps, int64_t k, double u, double v) {
+    const double *bb = ps->bbox + 4 * k;
+    if (!(u >= bb[0] && u <= bb[1] && v >= bb[2] && v <= bb[3])) return 0;
+    int rel = or_ring_relate_uv(ps->uv + 2 * ps->off[k], ps->off[k + 1] - ps->off[k], u, v);
+    return ps->contains ? rel == 2 : rel != 0;
+}
+
+/* ST_Covers(P_k, p) (or ST_Contains with the set's predicate): same face,
+ * inside the closed uv bbox, ring rule. */
 int or_polygon_covers(const or_polyset *ps, int64_t k, double lat, double lng) {
     double u, v;
     int f = or_face_uv(lat, lng, &u, &v);
     if (f < 0 || f != ps->face[k]) return 0;
-    const double *bb = ps->bbox + 4 * k;
-    if (!(u >= bb[0] && u <= bb[1] && v >= bb[2] && v <= bb[3])) return 0;
-    return or_ring_covers_uv(ps->uv + 2 * ps->off[k], ps->off[k + 1] - ps->off[k], u, v);
+    return or_pred_uv(ps, k, u, v);
 }
 
 /* Candidate polygons for a point via the grid (ascending ids).  Returns the
@@ -544,9 +569,7 @@ static int64_t or_point_hits(const or_polyset *ps, double lat, double lng, uint3
     int64_t cnt = 0;
     for (int64_t t = 0; t < m; ++t) {
         int32_t k = items[t];
-        const double *bb = ps->bbox + 4 * k;
-        if (!(u >= bb[0] && u <= bb[1] && v >= bb[2] && v <= bb[3])) continue;
-        if (or_ring_covers_uv(ps->uv + 2 * ps->off[k], ps->off[k + 1] - ps->off[k], u, v)) {
+        if (or_pred_uv(ps, k, u, v)) {
             if (out) out[cnt] = (uint32_t)k;
             ++cnt;
         }
