@@ -80,6 +80,21 @@ typedef enum {
                          within that budget; agj_index_stats' mode says which */
 } agj_mode;
 
+/* Join predicate of the exact join (§II).  The paper joins by ST_Covers and
+ * notes that other predicates, naming ST_Intersects, follow with similar
+ * techniques.  The index is the same for all three: its true-hit cells lie
+ * strictly inside their polygons, so only the refine test of candidate
+ * pairs differs, and only for points exactly on a polygon's edge or vertex.
+ * The approximate join is the same for every predicate (its extra pairs lie
+ * within precision_m, §III-A). */
+typedef enum {
+    AGJ_COVERS = 0,      /* ST_Covers: points on an edge or vertex are inside (default) */
+    AGJ_INTERSECTS = 1,  /* ST_Intersects: a point meets a polygon iff the polygon covers
+                            it, so the result equals AGJ_COVERS */
+    AGJ_CONTAINS = 2     /* ST_Contains: the interior only; points on an edge or vertex
+                            are outside */
+} agj_predicate;
+
 /* Build options; zero-initialise and set what you need.  0 selects the
  * default noted beside each field. */
 typedef struct {
@@ -99,7 +114,8 @@ typedef struct {
                                      FP32 model); results are identical, only slower */
     uint32_t no_pip_bands;        /* 1: the certified refine test scans every edge
                                      instead of the point's band; identical results */
-    uint32_t reserved;
+    uint32_t predicate;           /* agj_predicate of the exact join, 0 -> AGJ_COVERS;
+                                     another value is AGJ_EINVAL */
 } agj_build_opts;
 
 typedef struct agj_index agj_index;
@@ -114,7 +130,7 @@ typedef struct agj_index agj_index;
  * returning).  precision_m is used in approx mode only.
  * Ownership: *out is owned by the caller and released with agj_free.
  * Errors: AGJ_EINVAL (null, n_vertices < 3, invalid vertex, precision_m <= 0
- * in approx mode, AGJ_AUTO without a memory budget), AGJ_EUNSUPPORTED
+ * in approx mode, AGJ_AUTO without a memory budget, unknown predicate), AGJ_EUNSUPPORTED
  * (polygon spans faces, too many polygons), AGJ_EBUDGET (approx index above
  * memory_budget_bytes; AGJ_AUTO then builds the exact index instead),
  * AGJ_ENOMEM, AGJ_ECUDA.
@@ -139,7 +155,7 @@ typedef struct {
     uint32_t max_level;        /* finest cell level */
     double   build_seconds;
     uint32_t fast_ids;         /* 1: certified FP32 cell-id model in use */
-    uint32_t reserved;
+    uint32_t predicate;        /* agj_predicate the index joins by */
     double   fast_err_cells;   /* its error bound, in level-30 cells */
 } agj_stats;
 

@@ -77,6 +77,7 @@ int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, ag
     agj_build_opts o;
     memset(&o, 0, sizeof o);
     if (opts) o = *opts;
+    if (o.predicate > AGJ_CONTAINS) return AGJ_EINVAL;
     if (mode == AGJ_AUTO) {
         // §III-A: the approximate index first; if it exceeds the memory
         // budget, the exact index, trained until the budget is spent
@@ -106,6 +107,10 @@ int agj_build(const agj_polygon* polys, uint32_t n_polys, double precision_m, ag
         rc = agj::build_host(polys, n_polys, bp, &h->X, &g_last_error);
     } catch (const std::bad_alloc&) {
         rc = AGJ_ENOMEM;
+    }
+    if (rc == AGJ_OK) {
+        h->X.stats.predicate = o.predicate;
+        h->X.contains = o.predicate == AGJ_CONTAINS;
     }
     if (rc == AGJ_OK && !o.host_only) rc = agj::upload_index(&h->X, as_stream(stream));
     if (rc != AGJ_OK) {

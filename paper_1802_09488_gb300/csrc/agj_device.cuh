@@ -38,6 +38,7 @@ struct DevIndex {
     uint64_t n_lut;
     uint32_t n_polys;
     uint32_t max_depth;
+    uint32_t contains;          // 1: the refine test excludes the boundary (ST_Contains)
     DevFace faces[6];
     FastModel model;            // certified fast cell ids (enabled == 0: FP64 ids)
 };

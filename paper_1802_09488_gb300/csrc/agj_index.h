@@ -43,6 +43,7 @@ struct FaceRoot {
 struct Index {
     agj_mode mode = AGJ_APPROX;
     uint32_t n_polys = 0;
+    bool contains = false;      // exact join by ST_Contains (boundary points excluded) instead of ST_Covers
     double precision_m = 0;
     // logical index (super covering)
     std::vector<uint64_t> cells;

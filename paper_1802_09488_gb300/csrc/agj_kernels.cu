@@ -609,6 +609,7 @@ DevIndex make_dev_index(const Index& X) {
     D.n_lut = X.lut.size();
     D.n_polys = X.n_polys;
     D.max_depth = X.stats.max_depth;
+    D.contains = X.contains ? 1u : 0u;
     for (int f = 0; f < 6; ++f) D.faces[f] = dev_face(f, X.faces[f]);
     D.model = X.model;
     return D;

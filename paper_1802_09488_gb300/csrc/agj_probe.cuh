@@ -546,7 +546,11 @@ __device__ __forceinline__ void emit_all(const DevIndex& X, uint64_t e, uint32_t
 
 // ST_Covers in FP64 exactly as the spec (the certified test's fallback):
 // same face, closed (u,v) bbox, ring rule with integer keys for the range
-// tests and FP64 orientation, vertices read from global memory.
+// tests and FP64 orientation, vertices read from global memory.  With
+// X.contains (ST_Contains) a point on an edge or vertex is outside instead.
+// The certified FP32 test never decides such a point (its orientation or a
+// vertex lies within the error bounds), so this is the only place where the
+// predicates differ.
 __device__ __forceinline__ bool covers_fp64(const DevIndex& X, uint32_t poly, double lat, double lng) {
     if (!point_valid(lat, lng)) return false;
     double pu, pv;
@@ -566,7 +570,7 @@ __device__ __forceinline__ bool covers_fp64(const DevIndex& X, uint32_t poly, do
         const double o = (B.x - A.x) * (pv - A.y) - (B.y - A.y) * (pu - A.x);
         if (o == 0.0) {
             const int64_t au = X.poly_ukey[a], bu = X.poly_ukey[b];
-            if (puk >= (au < bu ? au : bu) && puk <= (au < bu ? bu : au)) return true;
+            if (puk >= (au < bu ? au : bu) && puk <= (au < bu ? bu : au)) return X.contains == 0u;
         }
         if ((av <= pvk && pvk < bv && o > 0.0) || (bv <= pvk && pvk < av && o < 0.0)) inside = !inside;
     }

@@ -17,6 +17,7 @@ from . import build as _build
 AGJ_OK, AGJ_EINVAL, AGJ_EUNSUPPORTED, AGJ_EBUDGET, AGJ_ENOMEM, AGJ_ECUDA, AGJ_ETIMEOUT, AGJ_EBUSY, \
     AGJ_ECAPACITY, AGJ_EDEVICE = range(10)
 APPROX, EXACT, AUTO = 0, 1, 2
+COVERS, INTERSECTS, CONTAINS = 0, 1, 2          # join predicates of the exact join (agj_predicate)
 
 
 class AgjError(RuntimeError):
@@ -39,7 +40,7 @@ class BuildOpts(C.Structure):
                 ("max_interior_cells", C.c_uint32), ("max_interior_level", C.c_uint32),
                 ("memory_budget_bytes", C.c_uint64), ("train_latlng", C.c_void_p), ("n_train", C.c_uint64),
                 ("max_train_level", C.c_uint32), ("n_threads", C.c_uint32), ("host_only", C.c_uint32),
-                ("no_fast_ids", C.c_uint32), ("no_pip_bands", C.c_uint32), ("reserved", C.c_uint32)]
+                ("no_fast_ids", C.c_uint32), ("no_pip_bands", C.c_uint32), ("predicate", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -47,7 +48,7 @@ class Stats(C.Structure):
                 ("n_cand_cells", C.c_uint64), ("n_nodes", C.c_uint64), ("n_lut_words", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("max_refs", C.c_uint32), ("max_cand_refs", C.c_uint32),
                 ("max_depth", C.c_uint32), ("max_level", C.c_uint32), ("build_seconds", C.c_double),
-                ("fast_ids", C.c_uint32), ("reserved", C.c_uint32), ("fast_err_cells", C.c_double)]
+                ("fast_ids", C.c_uint32), ("predicate", C.c_uint32), ("fast_err_cells", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -193,7 +194,7 @@ class Index:
     def __init__(self, polygons, mode: int = APPROX, precision_m: float = 10.0, train=None,
                  budget_bytes: int = 0, threads: int = 0, max_cover_cells: int = 0, max_interior_cells: int = 0,
                  max_interior_level: int = 0, host_only: bool = False, fast_ids: bool = True, pip_bands: bool = True,
-                 stream=None):
+                 predicate: int = COVERS, stream=None):
         L = lib()
         self._polys = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 2) for p in polygons]
         arr = (Polygon * max(len(self._polys), 1))()
@@ -209,6 +210,7 @@ class Index:
         opts.host_only = 1 if host_only else 0
         opts.no_fast_ids = 0 if fast_ids else 1
         opts.no_pip_bands = 0 if pip_bands else 1
+        opts.predicate = int(predicate)
         self._train = None
         if train is not None:
             self._train = np.ascontiguousarray(train, dtype=np.float64).reshape(-1, 2)
