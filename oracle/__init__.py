@@ -63,8 +63,10 @@ def _load():
             "or_cell_diag_m": (d, [u64]),
             "or_ring_covers_uv": (i32, [P, i64, d, d]),
             "or_ring_relate_uv": (i32, [P, i64, d, d]),
+            "or_rings_relate_uv": (i32, [P, P, i64, d, d]),
             "or_polyset_set_contains": (None, [P, i32]),
             "or_polyset_new": (P, [P, P, i64, i32]),
+            "or_polyset_new_rings": (P, [P, P, P, i64, i32]),
             "or_polyset_free": (None, [P]),
             "or_polyset_face": (i32, [P, i64]),
             "or_polygon_covers": (i32, [P, i64, d, d]),
@@ -173,8 +175,28 @@ def ring_relate_uv(uv: np.ndarray, pu: float, pv: float) -> int:
     return int(_load().or_ring_relate_uv(_ptr(a), len(a), float(pu), float(pv)))
 
 
+def _rings(p):
+    """A polygon as a list of (V,2) rings: an array is one ring, a list or
+    tuple of arrays is the outer ring followed by its holes."""
+    if isinstance(p, (list, tuple)):
+        return [np.asarray(r, dtype=np.float64).reshape(-1, 2) for r in p]
+    return [np.asarray(p, dtype=np.float64).reshape(-1, 2)]
+
+
+def rings_relate_uv(rings, pu: float, pv: float) -> int:
+    """Relation of a point to a polygon given as uv rings [outer, hole, ...]:
+    0 exterior, 1 boundary (on an edge of any ring), 2 interior."""
+    rs = [np.asarray(r, dtype=np.float64).reshape(-1, 2) for r in rings]
+    uv = np.ascontiguousarray(np.concatenate(rs))
+    off = np.zeros(len(rs) + 1, dtype=np.int64)
+    for q, r in enumerate(rs):
+        off[q + 1] = off[q] + len(r)
+    return int(_load().or_rings_relate_uv(_ptr(uv), _ptr(off), len(rs), float(pu), float(pv)))
+
+
 def flatten_polygons(polys) -> tuple[np.ndarray, np.ndarray]:
-    """list of (V,2) (lat,lng) arrays -> (latlng (N,2) f64, offsets (P+1,) i64)."""
+    """list of (V,2) (lat,lng) arrays -> (latlng (N,2) f64, offsets (P+1,) i64).
+    Every polygon must be a single ring (see flatten_rings for holes)."""
     off = np.zeros(len(polys) + 1, dtype=np.int64)
     for k, p in enumerate(polys):
         off[k + 1] = off[k] + len(p)
@@ -185,16 +207,33 @@ def flatten_polygons(polys) -> tuple[np.ndarray, np.ndarray]:
     return ll, off
 
 
+def flatten_rings(polys) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Polygons (each an array = one ring, or a list [outer, hole, ...]) ->
+    (latlng (N,2), ring vertex offsets (R+1,), polygon ring offsets (P+1,))."""
+    rings = [_rings(p) for p in polys]
+    pr = np.zeros(len(polys) + 1, dtype=np.int64)
+    for k, rs in enumerate(rings):
+        pr[k + 1] = pr[k] + len(rs)
+    flat = [r for rs in rings for r in rs]
+    rv = np.zeros(len(flat) + 1, dtype=np.int64)
+    for q, r in enumerate(flat):
+        rv[q + 1] = rv[q] + len(r)
+    ll = np.ascontiguousarray(np.concatenate(flat)) if flat else np.zeros((0, 2), dtype=np.float64)
+    return ll, rv, pr
+
+
 class PolySet:
     """Polygons prepared in face (u,v) with a uniform-grid prefilter."""
 
     def __init__(self, polys, grid_n: int = 64, contains: bool = False):
-        """contains: join by ST_Contains (boundary points excluded) instead of
-        ST_Covers (= ST_Intersects for a point)."""
+        """polys: each an (V,2) (lat,lng) ring or a list [outer, hole, ...] of
+        rings.  contains: join by ST_Contains (boundary points excluded)
+        instead of ST_Covers (= ST_Intersects for a point)."""
         self._lib = _load()
-        self.latlng, self.off = flatten_polygons(polys)
+        self.latlng, self.ring_off, self.poly_ring_off = flatten_rings(polys)
         self.n = len(polys)
-        self._h = self._lib.or_polyset_new(_ptr(self.latlng), _ptr(self.off), self.n, int(grid_n))
+        self._h = self._lib.or_polyset_new_rings(_ptr(self.latlng), _ptr(self.ring_off), _ptr(self.poly_ring_off),
+                                                 self.n, int(grid_n))
         self._lib.or_polyset_set_contains(self._h, 1 if contains else 0)
 
     def __del__(self):

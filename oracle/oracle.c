@@ -19,6 +19,10 @@
  *   - ST_Covers of a point by a simple polygon (§II: points on edges or
  *     vertices are inside; "PIP": ray-crossing, odd count = inside), with
  *     geodesic edges, i.e. straight lines in the polygon's face (u,v) plane;
+ *     polygons may have holes (rings after the outer one: the point is on
+ *     the boundary if on any ring's edge, else inside if inside an odd
+ *     number of rings), and ST_Contains (boundary excluded) is the interior
+ *     of the same relation;
  *   - the exact join {(p, P) : P covers p} by brute force (bbox + uniform
  *     grid prefilter, then the full predicate) — §III-A: the exact join is
  *     the filter-and-refine result, which does not depend on the index;
@@ -378,6 +382,7 @@ static double or_angle_point_arc(const double p[3], const double a[3], const dou
  *   odd number of toggles -> covered.
  */
 int or_ring_relate_uv(const double *uv, int64_t n, double pu, double pv);
+int or_rings_relate_uv(const double *uv, const int64_t *ring_off, int64_t n_rings, double pu, double pv);
 int or_ring_covers_uv(const double *uv, int64_t n, double pu, double pv) {
     return or_ring_relate_uv(uv, n, pu, pv) != 0;
 }
@@ -404,11 +409,16 @@ int or_ring_relate_uv(const double *uv, int64_t n, double pu, double pv) {
     return inside ? 2 : 0;
 }
 
-/* A polygon set: vertices in (lat, lng) degrees, ring k spans
- * latlng[2*off[k] .. 2*off[k+1]).  Prepared into face uv once. */
+/* A polygon set: vertices in (lat, lng) degrees.  Polygon k has the rings
+ * pr[k] .. pr[k+1]-1 (the outer boundary first, then its holes), ring r the
+ * vertices rv[r] .. rv[r+1]-1, each ring implicitly closed; a polygon's
+ * vertices are contiguous, off[k] .. off[k+1]-1.  Prepared into face uv
+ * once. */
 typedef struct {
     int64_t n_polys;
     int64_t *off;          /* n_polys + 1 */
+    int64_t *pr;           /* n_polys + 1 */
+    int64_t *rv;           /* rings + 1 */
     double *uv;            /* 2 * off[n_polys] */
     int *face;             /* -1 if the polygon is not on a single face */
     double *bbox;          /* 4 per polygon: umin umax vmin vmax */
@@ -428,16 +438,23 @@ static int or_cmp_i32(const void *a, const void *b) {
 
 void or_polyset_free(or_polyset *ps) {
     if (!ps) return;
-    free(ps->off); free(ps->uv); free(ps->face); free(ps->bbox);
+    free(ps->off); free(ps->pr); free(ps->rv); free(ps->uv); free(ps->face); free(ps->bbox);
     for (int f = 0; f < 6; ++f) { free(ps->g_start[f]); free(ps->g_items[f]); }
     free(ps);
 }
 
-or_polyset *or_polyset_new(const double *latlng, const int64_t *off, int64_t n_polys, int grid_n) {
+or_polyset *or_polyset_new_rings(const double *latlng, const int64_t *ring_off, const int64_t *poly_ring_off,
+                                 int64_t n_polys, int grid_n) {
     or_polyset *ps = (or_polyset *)calloc(1, sizeof(or_polyset));
     ps->n_polys = n_polys;
+    int64_t n_rings = poly_ring_off[n_polys];
+    ps->pr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_polys + 1));
+    memcpy(ps->pr, poly_ring_off, sizeof(int64_t) * (size_t)(n_polys + 1));
+    ps->rv = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_rings + 1));
+    memcpy(ps->rv, ring_off, sizeof(int64_t) * (size_t)(n_rings + 1));
     ps->off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_polys + 1));
-    memcpy(ps->off, off, sizeof(int64_t) * (size_t)(n_polys + 1));
+    for (int64_t k = 0; k <= n_polys; ++k) ps->off[k] = ring_off[poly_ring_off[k]];
+    const int64_t *off = ps->off;
     int64_t nv = off[n_polys];
     ps->uv = (double *)malloc(sizeof(double) * 2 * (size_t)(nv > 0 ? nv : 1));
     ps->face = (int *)malloc(sizeof(int) * (size_t)(n_polys > 0 ? n_polys : 1));
@@ -456,7 +473,9 @@ or_polyset *or_polyset_new(const double *latlng, const int64_t *off, int64_t n_p
             if (v < vmin) vmin = v;
             if (v > vmax) vmax = v;
         }
-        if (off[k + 1] - off[k] < 3) face = -1;
+        if (ps->pr[k + 1] <= ps->pr[k]) face = -1;
+        for (int64_t r = ps->pr[k]; r < ps->pr[k + 1]; ++r)
+            if (ps->rv[r + 1] - ps->rv[r] < 3) face = -1;
         ps->face[k] = face < 0 ? -1 : face;
         ps->bbox[4 * k] = umin; ps->bbox[4 * k + 1] = umax;
         ps->bbox[4 * k + 2] = vmin; ps->bbox[4 * k + 3] = vmax;
@@ -523,7 +542,36 @@ or_polyset *or_polyset_new(const double *latlng, const int64_t *off, int64_t n_p
     return ps;
 }
 
+/* The same relation for rings given directly in uv: ring q spans the
+ * vertices ring_off[q] .. ring_off[q+1]-1 of uv (n_rings rings). */
+int or_rings_relate_uv(const double *uv, const int64_t *ring_off, int64_t n_rings, double pu, double pv) {
+    int parity = 0;
+    for (int64_t q = 0; q < n_rings; ++q) {
+        int rel = or_ring_relate_uv(uv + 2 * ring_off[q], ring_off[q + 1] - ring_off[q], pu, pv);
+        if (rel == 1) return 1;
+        if (rel == 2) parity ^= 1;
+    }
+    return parity ? 2 : 0;
+}
+
+/* Every polygon a single ring: polygon k = latlng[2*off[k] .. 2*off[k+1]). */
+or_polyset *or_polyset_new(const double *latlng, const int64_t *off, int64_t n_polys, int grid_n) {
+    int64_t *pr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_polys + 1));
+    for (int64_t k = 0; k <= n_polys; ++k) pr[k] = k;
+    or_polyset *ps = or_polyset_new_rings(latlng, off, pr, n_polys, grid_n);
+    free(pr);
+    return ps;
+}
+
 int or_polyset_face(const or_polyset *ps, int64_t k) { return ps->face[k]; }
+
+/* Relation of a point (in the polygon's face uv) to polygon k with all its
+ * rings: on the boundary (1) if it lies on an edge of any ring, else interior
+ * (2) if it is inside an odd number of rings (outer boundary minus holes),
+ * else exterior (0). */
+int or_polygon_relate_uv(const or_polyset *ps, int64_t k, double u, double v) {
+    return or_rings_relate_uv(ps->uv, ps->rv + ps->pr[k], ps->pr[k + 1] - ps->pr[k], u, v);
+}
 
 /* Selects the join predicate of the set: 0 ST_Covers (ST_Intersects is the
  * same predicate for a point), 1 ST_Contains. */
@@ -534,7 +582,7 @@ void or_polyset_set_contains(or_polyset *ps, int contains) { ps->contains = cont
 static int or_pred_uv(const or_polyset *ps, int64_t k, double u, double v) {
     const double *bb = ps->bbox + 4 * k;
     if (!(u >= bb[0] && u <= bb[1] && v >= bb[2] && v <= bb[3])) return 0;
-    int rel = or_ring_relate_uv(ps->uv + 2 * ps->off[k], ps->off[k + 1] - ps->off[k], u, v);
+    int rel = or_polygon_relate_uv(ps, k, u, v);
     return ps->contains ? rel == 2 : rel != 0;
 }
 
@@ -739,16 +787,18 @@ double or_dist_point_polygon_m(const or_polyset *ps, int64_t k, double lat, doub
         p[0] = cos(la) * cos(lo); p[1] = cos(la) * sin(lo); p[2] = sin(la);
     }
     int f = ps->face[k];
-    int64_t s = ps->off[k], e = ps->off[k + 1], nv = e - s;
     double best = INFINITY;
-    for (int64_t t = 0; t < nv; ++t) {
-        const double *a = ps->uv + 2 * (s + t);
-        const double *b = ps->uv + 2 * (s + (t + 1) % nv);
-        double A[3], B[3];
-        or_face_uv_to_xyz(f, a[0], a[1], A);
-        or_face_uv_to_xyz(f, b[0], b[1], B);
-        double ang = or_angle_point_arc(p, A, B);
-        if (ang < best) best = ang;
+    for (int64_t r = ps->pr[k]; r < ps->pr[k + 1]; ++r) {
+        int64_t s = ps->rv[r], nv = ps->rv[r + 1] - s;
+        for (int64_t t = 0; t < nv; ++t) {
+            const double *a = ps->uv + 2 * (s + t);
+            const double *b = ps->uv + 2 * (s + (t + 1) % nv);
+            double A[3], B[3];
+            or_face_uv_to_xyz(f, a[0], a[1], A);
+            or_face_uv_to_xyz(f, b[0], b[1], B);
+            double ang = or_angle_point_arc(p, A, B);
+            if (ang < best) best = ang;
+        }
     }
     return best * OR_EARTH_R;
 }
@@ -778,6 +828,17 @@ static int or_seg_meets_rect(const double a[2], const double b[2], const double 
     return 1;
 }
 
+/* Does an edge of any ring of polygon k meet the closed rectangle r? */
+static int or_polygon_meets_rect(const or_polyset *ps, int64_t k, const double r[4]) {
+    for (int64_t q = ps->pr[k]; q < ps->pr[k + 1]; ++q) {
+        const double *uv = ps->uv + 2 * ps->rv[q];
+        int64_t nv = ps->rv[q + 1] - ps->rv[q];
+        for (int64_t e = 0; e < nv; ++e)
+            if (or_seg_meets_rect(uv + 2 * e, uv + 2 * ((e + 1) % nv), r)) return 1;
+    }
+    return 0;
+}
+
 /* report[0] = overlapping neighbour pairs (disjointness),
  * report[1] = true refs whose cell is not wholly inside the polygon,
  * report[2] = candidate refs whose cell, widened by cand_margin in (u,v),
@@ -797,21 +858,17 @@ void or_check_covering(const or_polyset *ps, const uint64_t *cells, int64_t m, c
             uint32_t pid = refs[t] >> 1;
             int interior = (int)(refs[t] & 1u);
             if ((int64_t)pid >= ps->n_polys || ps->face[pid] != face) { report[4]++; continue; }
-            const double *uv = ps->uv + 2 * ps->off[pid];
-            int64_t nv = ps->off[pid + 1] - ps->off[pid];
             double cu = 0.5 * (r[0] + r[1]), cv = 0.5 * (r[2] + r[3]);
-            int center_in = or_ring_covers_uv(uv, nv, cu, cv);
+            int center_in = or_polygon_relate_uv(ps, pid, cu, cv) != 0;
             if (interior) {
-                int meets = 0;
-                for (int64_t e = 0; e < nv && !meets; ++e)
-                    meets = or_seg_meets_rect(uv + 2 * e, uv + 2 * ((e + 1) % nv), r);
+                int meets = or_polygon_meets_rect(ps, pid, r);
                 if (meets || !center_in) report[1]++;
             } else {
                 has_cand = 1;
                 double w[4] = {r[0] - cand_margin, r[1] + cand_margin, r[2] - cand_margin, r[3] + cand_margin};
-                int meets = 0, vertex_in = 0;
-                for (int64_t e = 0; e < nv && !meets; ++e)
-                    meets = or_seg_meets_rect(uv + 2 * e, uv + 2 * ((e + 1) % nv), w);
+                int meets = or_polygon_meets_rect(ps, pid, w), vertex_in = 0;
+                const double *uv = ps->uv + 2 * ps->off[pid];
+                int64_t nv = ps->off[pid + 1] - ps->off[pid];
                 for (int64_t e = 0; e < nv && !vertex_in; ++e)
                     vertex_in = uv[2 * e] >= w[0] && uv[2 * e] <= w[1] && uv[2 * e + 1] >= w[2] && uv[2 * e + 1] <= w[3];
                 if (!meets && !center_in && !vertex_in) report[2]++;
