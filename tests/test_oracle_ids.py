@@ -20,8 +20,9 @@ def ulp(x: float) -> float:
 
 
 def _mp_sincosd(d):
-    a = mpmath.mpf(d) * mpmath.pi / 180
-    return mpmath.sin(a), mpmath.cos(a)
+    with mpmath.workprec(200):
+        a = mpmath.mpf(d) * mpmath.pi / 180
+        return +mpmath.sin(a), +mpmath.cos(a)
 
 
 def test_sincosd_against_mpmath(oracle):
@@ -30,14 +31,15 @@ def test_sincosd_against_mpmath(oracle):
     ds += [0.0, 1e-300, -1e-300, 30.0, 45.0, -45.0, 44.999999999, 45.000000001, 60.0, 89.9999, 90.0, 120.0,
            135.0, 135.00000001, 179.999999, 180.0, -180.0, -90.0, 40.7, -73.95]
     worst = 0.0
-    for d in ds:
-        s, c = oracle.sincosd(d)
-        ms, mc = _mp_sincosd(d)
-        for got, want in ((s, ms), (c, mc)):
-            if abs(want) < mpmath.mpf("1e-40"):      # exact zero of sin/cos (mpmath's pi is finite)
-                assert abs(got) < 1e-40
-                continue
-            worst = max(worst, float(abs(mpmath.mpf(got) - want) / ulp(float(want))))
+    with mpmath.workprec(200):        # independent of the precision other tests leave set
+        for d in ds:
+            s, c = oracle.sincosd(d)
+            ms, mc = _mp_sincosd(d)
+            for got, want in ((s, ms), (c, mc)):
+                if abs(want) < mpmath.mpf("1e-40"):      # exact zero of sin/cos (mpmath's pi is finite)
+                    assert abs(got) < 1e-40
+                    continue
+                worst = max(worst, float(abs(mpmath.mpf(got) - want) / ulp(float(want))))
     assert worst <= 3.0, worst
 
 

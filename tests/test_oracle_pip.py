@@ -186,7 +186,11 @@ def test_distance_zero_inside_and_edge_distance(oracle):
     """Distance from a point to a polygon's geodesic edge, against dense
     sampling of that edge (straight in (u,v)) with mpmath great circles."""
     import mpmath
-    mpmath.mp.prec = 100
+    with mpmath.workprec(100):          # leaves the precision other tests set unchanged
+        _distance_against_sampling(oracle, mpmath)
+
+
+def _distance_against_sampling(oracle, mpmath):
     poly = np.array([[40.60, -74.05], [40.60, -73.85], [40.80, -73.85], [40.80, -74.05]])
     ps = oracle.PolySet([poly])
     assert ps.dist_m(0, 40.7, -73.95) == 0.0
