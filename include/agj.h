@@ -61,13 +61,23 @@ const char* agj_last_error(void);
 /* polygons and index build (host)                                          */
 /* ---------------------------------------------------------------------- */
 
-/* One simple polygon: a ring of n_vertices >= 3 (lat, lng) degree pairs,
- * implicitly closed, either orientation, all on one cube face.  Edges are
- * geodesics (straight in the face's gnomonic (u,v) plane).  ST_Covers
- * semantics (§II): points on edges and vertices are inside. */
+/* One polygon: a simple ring of (lat, lng) degree pairs, implicitly closed,
+ * either orientation, all on one cube face, optionally with holes.  Edges
+ * are geodesics (straight in the face's gnomonic (u,v) plane).  ST_Covers
+ * semantics (§II): points on edges and vertices are inside.
+ * Holes widen the paper's simple polygons: with n_rings >= 2, latlng holds
+ * the outer ring followed by the hole rings, ring q ending (exclusive) at
+ * vertex ring_ends[q] (ascending, the last = n_vertices, each ring >= 3
+ * vertices).  The polygon is the outer ring minus the interiors of its
+ * holes: a point on an edge of any ring is on the boundary, otherwise it is
+ * inside when it lies inside an odd number of rings (holes are expected
+ * inside the outer ring and disjoint; that rule defines the result anyway).
+ * n_rings 0 or 1: a single ring of n_vertices >= 3, ring_ends unused. */
 typedef struct {
-    uint32_t n_vertices;
+    uint32_t n_vertices;       /* all rings together */
+    uint32_t n_rings;          /* 0 or 1: one ring; k >= 2: the outer ring and k - 1 holes */
     const double* latlng;      /* host, 2 * n_vertices doubles */
+    const uint32_t* ring_ends; /* host, n_rings >= 2: n_rings ascending ring ends */
 } agj_polygon;
 
 typedef enum {
@@ -129,8 +139,9 @@ typedef struct agj_index agj_index;
  * the current device on `stream` (the call synchronises on `stream` before
  * returning).  precision_m is used in approx mode only.
  * Ownership: *out is owned by the caller and released with agj_free.
- * Errors: AGJ_EINVAL (null, n_vertices < 3, invalid vertex, precision_m <= 0
- * in approx mode, AGJ_AUTO without a memory budget, unknown predicate), AGJ_EUNSUPPORTED
+ * Errors: AGJ_EINVAL (null, a ring with < 3 vertices, ring ends not ascending
+ * to n_vertices, invalid vertex, precision_m <= 0 in approx mode, AGJ_AUTO
+ * without a memory budget, unknown predicate), AGJ_EUNSUPPORTED
  * (polygon spans faces, too many polygons), AGJ_EBUDGET (approx index above
  * memory_budget_bytes; AGJ_AUTO then builds the exact index instead),
  * AGJ_ENOMEM, AGJ_ECUDA.

@@ -56,6 +56,13 @@ struct Poly {
     const double* uv;   // 2 per vertex
     uint32_t nv;
     double bb[4];       // umin umax vmin vmax
+    // edges of a polygon with holes (first vertices; the second is the next
+    // vertex, rings stored explicitly closed); null: one ring, every vertex
+    // starts an edge and the last one's edge closes the ring
+    const uint32_t* edges = nullptr;
+    uint32_t n_edges = 0;
+    uint32_t edge_count() const { return edges ? n_edges : nv; }
+    uint32_t edge(uint32_t q) const { return edges ? edges[q] : q; }
 };
 
 struct Rect {
@@ -116,11 +123,14 @@ inline bool seg_meets_rect(const double* a, const double* b, const Rect& r) {
 
 // ST_Covers ring rule in (u,v): on-edge -> covered; otherwise odd number of
 // half-open crossings of the ray towards +u.
+// With holes the rule runs over the edges of every ring: on an edge of any
+// ring -> covered; otherwise an odd number of crossings in all -> covered.
 bool ring_covers(const Poly& P, double pu, double pv) {
     if (!(pu >= P.bb[0] && pu <= P.bb[1] && pv >= P.bb[2] && pv <= P.bb[3])) return false;
     bool inside = false;
     const uint32_t n = P.nv;
-    for (uint32_t k = 0; k < n; ++k) {
+    for (uint32_t q = 0, m = P.edge_count(); q < m; ++q) {
+        const uint32_t k = P.edge(q);
         const double* a = P.uv + 2 * k;
         const double* b = P.uv + 2 * (k + 1 == n ? 0 : k + 1);
         const double vlo = std::min(a[1], b[1]), vhi = std::max(a[1], b[1]);
@@ -150,7 +160,7 @@ int classify(const Poly& P, uint64_t id, const std::vector<uint32_t>* edges, std
     if (edges) {
         for (uint32_t k : *edges) test(k);
     } else {
-        for (uint32_t k = 0; k < n; ++k) test(k);
+        for (uint32_t q = 0, m = P.edge_count(); q < m; ++q) test(P.edge(q));
     }
     if (!out_edges->empty()) return kBoundary;
     return ring_covers(P, 0.5 * (r.u0 + r.u1), 0.5 * (r.v0 + r.v1)) ? kInside : kOutside;
@@ -734,6 +744,21 @@ void supercover(const uint64_t* cells, const uint32_t* refs, uint64_t n, std::ve
     }
 }
 
+void poly_edges(const Index& X, uint32_t k, std::vector<uint32_t>* out) {
+    out->clear();
+    const uint32_t V = X.poly_off[k + 1] - X.poly_off[k];
+    if (X.ring_off.size() != X.n_polys + 1 || X.ring_off[k + 1] == X.ring_off[k]) {
+        for (uint32_t t = 0; t < V; ++t) out->push_back(t);
+        return;
+    }
+    uint32_t start = 0;
+    for (uint32_t q = X.ring_off[k]; q < X.ring_off[k + 1]; ++q) {
+        const uint32_t end = X.ring_end[q];          // the closing duplicate is end - 1
+        for (uint32_t t = start; t + 1 < end; ++t) out->push_back(t);
+        start = end;
+    }
+}
+
 int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp, Index* out, std::string* err) {
     const auto t0 = std::chrono::steady_clock::now();
     if (n_polys > 0 && !polys) { *err = "null polygon array"; return AGJ_EINVAL; }
@@ -745,32 +770,68 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
     X.n_polys = n_polys;
     X.precision_m = bp.precision_m;
     X.poly_off.assign(n_polys + 1, 0);
+    X.ring_off.assign(n_polys + 1, 0);
+    X.ring_end.clear();
     for (uint32_t k = 0; k < n_polys; ++k) {
-        if (polys[k].n_vertices < 3 || !polys[k].latlng) { *err = "polygon needs >= 3 vertices"; return AGJ_EINVAL; }
-        X.poly_off[k + 1] = X.poly_off[k] + polys[k].n_vertices;
+        const agj_polygon& g = polys[k];
+        if (g.n_vertices < 3 || !g.latlng) { *err = "polygon needs >= 3 vertices"; return AGJ_EINVAL; }
+        if (g.n_rings >= 2) {
+            // rings stored explicitly closed: one more vertex per ring
+            if (!g.ring_ends) { *err = "polygon with holes needs ring ends"; return AGJ_EINVAL; }
+            uint32_t prev = 0;
+            for (uint32_t q = 0; q < g.n_rings; ++q) {
+                if (g.ring_ends[q] < prev + 3 || g.ring_ends[q] > g.n_vertices) {
+                    *err = "each ring needs >= 3 vertices and ring ends must ascend to n_vertices";
+                    return AGJ_EINVAL;
+                }
+                prev = g.ring_ends[q];
+                X.ring_end.push_back(g.ring_ends[q] + q + 1);
+            }
+            if (prev != g.n_vertices) { *err = "the last ring end must be n_vertices"; return AGJ_EINVAL; }
+            X.poly_off[k + 1] = X.poly_off[k] + g.n_vertices + g.n_rings;
+        } else {
+            X.poly_off[k + 1] = X.poly_off[k] + g.n_vertices;
+        }
+        X.ring_off[k + 1] = (uint32_t)X.ring_end.size();
     }
     X.poly_uv.assign(2ull * X.poly_off[n_polys], 0.0);
     X.poly_bbox.assign(4ull * n_polys, 0.0);
     X.poly_face.assign(n_polys, (int8_t)-1);
     std::vector<Poly> P(n_polys);
+    std::vector<std::vector<uint32_t>> edges(n_polys);
     for (uint32_t k = 0; k < n_polys; ++k) {
+        const agj_polygon& g = polys[k];
         int face = -1;
         double bb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
-        for (uint32_t t = 0; t < polys[k].n_vertices; ++t) {
-            const double lat = polys[k].latlng[2 * t], lng = polys[k].latlng[2 * t + 1];
+        uint32_t out = X.poly_off[k], ring = 0, ring_first = out;
+        for (uint32_t t = 0; t < g.n_vertices; ++t) {
+            const double lat = g.latlng[2 * t], lng = g.latlng[2 * t + 1];
             if (!point_valid(lat, lng)) { *err = "invalid polygon vertex"; return AGJ_EINVAL; }
             double u, v;
             const int f = face_uv(lat, lng, &u, &v);
             if (face >= 0 && f != face) { *err = "polygon spans more than one cube face"; return AGJ_EUNSUPPORTED; }
             face = f;
-            X.poly_uv[2 * (X.poly_off[k] + t)] = u;
-            X.poly_uv[2 * (X.poly_off[k] + t) + 1] = v;
+            X.poly_uv[2 * out] = u;
+            X.poly_uv[2 * out + 1] = v;
+            ++out;
             bb[0] = std::min(bb[0], u); bb[1] = std::max(bb[1], u);
             bb[2] = std::min(bb[2], v); bb[3] = std::max(bb[3], v);
+            if (g.n_rings >= 2 && t + 1 == g.ring_ends[ring]) {     // close the ring explicitly
+                X.poly_uv[2 * out] = X.poly_uv[2 * ring_first];
+                X.poly_uv[2 * out + 1] = X.poly_uv[2 * ring_first + 1];
+                ++out;
+                ++ring;
+                ring_first = out;
+            }
         }
         X.poly_face[k] = (int8_t)face;
         std::memcpy(&X.poly_bbox[4 * k], bb, sizeof bb);
-        P[k] = Poly{face, &X.poly_uv[2 * X.poly_off[k]], polys[k].n_vertices, {bb[0], bb[1], bb[2], bb[3]}};
+        P[k] = Poly{face, &X.poly_uv[2 * X.poly_off[k]], X.poly_off[k + 1] - X.poly_off[k], {bb[0], bb[1], bb[2], bb[3]}};
+        if (g.n_rings >= 2) {
+            poly_edges(X, k, &edges[k]);
+            P[k].edges = edges[k].data();
+            P[k].n_edges = (uint32_t)edges[k].size();
+        }
     }
 
     // per-polygon coverings and interior coverings
@@ -851,10 +912,16 @@ int retrain(Index* X, const uint64_t* ids, uint64_t n_ids, uint64_t budget, uint
     threads = threads ? threads : std::max(1u, std::thread::hardware_concurrency());
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<Poly> P(X->n_polys);
+    std::vector<std::vector<uint32_t>> edges(X->n_polys);
     for (uint32_t k = 0; k < X->n_polys; ++k) {
         const double* bb = &X->poly_bbox[4 * k];
         P[k] = Poly{X->poly_face[k], &X->poly_uv[2 * X->poly_off[k]], X->poly_off[k + 1] - X->poly_off[k],
                     {bb[0], bb[1], bb[2], bb[3]}};
+        if (X->ring_off.size() == X->n_polys + 1 && X->ring_off[k + 1] > X->ring_off[k]) {
+            poly_edges(*X, k, &edges[k]);
+            P[k].edges = edges[k].data();
+            P[k].n_edges = (uint32_t)edges[k].size();
+        }
     }
     std::vector<uint64_t> cells = X->cells;
     std::vector<Refs> refs(cells.size());

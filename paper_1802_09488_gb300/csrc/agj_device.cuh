@@ -34,6 +34,8 @@ struct DevIndex {
     const PolyLocal* poly_local;  // certified refine: per-polygon reference, bound, bbox
     const F2* poly_luv;           // certified refine: FP32 local vertex coordinates
     const uint16_t* poly_band;    // certified refine: per-polygon band tables
+    const uint32_t* ring_off;     // n_polys + 1: each polygon's entries in ring_end (none: one ring)
+    const uint32_t* ring_end;     // ends of a polygon with holes' rings (explicitly closed), relative to poly_off
     uint64_t n_nodes;
     uint64_t n_lut;
     uint32_t n_polys;

@@ -40,6 +40,12 @@ struct FaceRoot {
     uint64_t prefix;
 };
 
+// The edges of polygon k of X: the first vertex (relative to poly_off[k])
+// of every edge; the edge's second vertex is the next one, modulo the
+// vertex count for a one-ring polygon.
+struct Index;
+void poly_edges(const Index& X, uint32_t k, std::vector<uint32_t>* out);
+
 struct Index {
     agj_mode mode = AGJ_APPROX;
     uint32_t n_polys = 0;
@@ -56,6 +62,13 @@ struct Index {
     // polygons in face (u,v)
     std::vector<double> poly_uv;      // 2 per vertex
     std::vector<uint32_t> poly_off;   // n_polys + 1
+    // Polygons with holes store every ring explicitly closed (its first
+    // vertex repeated at its end), so each of their edges is (t, t + 1);
+    // ring_end[ring_off[k] .. ring_off[k+1]) are the ends of polygon k's rings
+    // relative to poly_off[k] (none for a one-ring polygon, whose ring is
+    // implicitly closed: edge t is (t, t + 1 mod V)).
+    std::vector<uint32_t> ring_off;   // n_polys + 1
+    std::vector<uint32_t> ring_end;
     std::vector<double> poly_bbox;    // 4 per polygon: umin umax vmin vmax
     std::vector<int8_t> poly_face;
     FastModel model{};                // certified fast cell ids (disabled: all zero)
@@ -67,7 +80,7 @@ struct Index {
     void* d_blob = nullptr;
     uint64_t blob_bytes = 0;
     uint64_t off_nodes = 0, off_lut = 0, off_uv = 0, off_vkey = 0, off_ukey = 0, off_poff = 0, off_bbox = 0,
-             off_face = 0, off_plocal = 0, off_pluv = 0, off_pband = 0;
+             off_face = 0, off_plocal = 0, off_pluv = 0, off_pband = 0, off_roff = 0, off_rend = 0;
     int device = 0;
 };
 

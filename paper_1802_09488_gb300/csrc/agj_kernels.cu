@@ -605,6 +605,8 @@ DevIndex make_dev_index(const Index& X) {
     D.poly_local = reinterpret_cast<const PolyLocal*>(b + X.off_plocal);
     D.poly_luv = reinterpret_cast<const F2*>(b + X.off_pluv);
     D.poly_band = reinterpret_cast<const uint16_t*>(b + X.off_pband);
+    D.ring_off = reinterpret_cast<const uint32_t*>(b + X.off_roff);
+    D.ring_end = reinterpret_cast<const uint32_t*>(b + X.off_rend);
     D.n_nodes = X.nodes.size() / 256;
     D.n_lut = X.lut.size();
     D.n_polys = X.n_polys;
@@ -619,7 +621,7 @@ namespace {
 
 // Byte offsets of the sections of an index's device blob (256-byte aligned).
 struct BlobLayout {
-    uint64_t nodes, lut, uv, vkey, ukey, poff, bbox, face, plocal, pluv, pband, total;
+    uint64_t nodes, lut, uv, vkey, ukey, poff, bbox, face, plocal, pluv, pband, roff, rend, total;
 };
 
 BlobLayout blob_layout(const Index& X) {
@@ -637,6 +639,8 @@ BlobLayout blob_layout(const Index& X) {
     B.plocal = o; o += align256((uint64_t)X.n_polys * sizeof(PolyLocal) + 16);
     B.pluv = o; o += align256(nv * sizeof(F2) + 16);
     B.pband = o; o += align256(X.poly_band.size() * 2 + 16);
+    B.roff = o; o += align256(X.ring_off.size() * 4 + 4);
+    B.rend = o; o += align256(X.ring_end.size() * 4 + 4);
     B.total = o;
     return B;
 }
@@ -650,7 +654,7 @@ int upload_index(Index* X, cudaStream_t s) {
     const BlobLayout B = blob_layout(*X);
     X->off_nodes = B.nodes; X->off_lut = B.lut; X->off_uv = B.uv; X->off_vkey = B.vkey; X->off_ukey = B.ukey;
     X->off_poff = B.poff; X->off_bbox = B.bbox; X->off_face = B.face; X->off_plocal = B.plocal;
-    X->off_pluv = B.pluv; X->off_pband = B.pband;
+    X->off_pluv = B.pluv; X->off_pband = B.pband; X->off_roff = B.roff; X->off_rend = B.rend;
     const uint64_t o = B.total;
     X->blob_bytes = o;
     std::vector<unsigned char> host(o, 0);
@@ -674,6 +678,8 @@ int upload_index(Index* X, cudaStream_t s) {
     put(X->off_plocal, X->poly_local.data(), X->poly_local.size() * sizeof(PolyLocal));
     put(X->off_pluv, X->poly_luv.data(), X->poly_luv.size() * sizeof(F2));
     put(X->off_pband, X->poly_band.data(), X->poly_band.size() * 2);
+    put(X->off_roff, X->ring_off.data(), X->ring_off.size() * 4);
+    put(X->off_rend, X->ring_end.data(), X->ring_end.size() * 4);
     if (cudaMalloc(&X->d_blob, o) != cudaSuccess) { cudaGetLastError(); X->d_blob = nullptr; return AGJ_ENOMEM; }
     if (cudaMemcpyAsync(X->d_blob, host.data(), o, cudaMemcpyHostToDevice, s) != cudaSuccess) return AGJ_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return AGJ_ECUDA;

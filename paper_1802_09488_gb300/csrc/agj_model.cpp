@@ -355,19 +355,29 @@ void fit_fast_model(Index* idx, unsigned threads) {
 // at most a unit of pv and a relative 2.4e-7 of the band count).  So every
 // edge the all-edges loop could straddle, or whose vertex could come within
 // D, is in the point's band: the banded test gives the same answer.
+// A polygon with holes always gets a table (its edges are listed there, the
+// device's all-edges loop assumes one ring) or, when none fits, no
+// certified test at all (L->ok = 0: every candidate takes the FP64 test).
 static void build_bands(Index* idx, uint32_t k, PolyLocal* L) {
     const uint32_t a = idx->poly_off[k], V = idx->poly_off[k + 1] - a;
-    if (!L->ok || !idx->model.uv_enabled || V < kBandMinVerts) return;
+    const bool holes = idx->ring_off.size() == idx->n_polys + 1 && idx->ring_off[k + 1] > idx->ring_off[k];
+    if (!L->ok || !idx->model.uv_enabled) return;
+    if (!holes && V < kBandMinVerts) return;
     const double lo = L->bv0, hi = L->bv1;
-    if (!(hi > lo)) return;
-    const uint32_t nb = std::min<uint32_t>(kBandMax, V / 4);
+    if (!(hi > lo) || V > 65535) {
+        if (holes) L->ok = 0;
+        return;
+    }
+    const uint32_t nb = std::max<uint32_t>(1, std::min<uint32_t>(kBandMax, V / 4));
     const double h = (hi - lo) / nb;
     const double big = std::max(std::fabs((double)L->bu0), std::fabs((double)L->bu1)) +
                        std::max(std::fabs((double)L->bv0), std::fabs((double)L->bv1));
     const double M = 2.0 * ((double)idx->model.err_uv + (double)L->dv) + big * 5e-7 + 8.0 + h * 1e-3;
     std::vector<std::vector<uint16_t>> lists(nb);
     const F2* lv = idx->poly_luv.data() + a;
-    for (uint32_t e = 0; e < V; ++e) {
+    std::vector<uint32_t> edges;
+    poly_edges(*idx, k, &edges);
+    for (const uint32_t e : edges) {
         const F2 A = lv[e], B = lv[e + 1 == V ? 0 : e + 1];
         const double ylo = std::min(A.y, B.y) - M, yhi = std::max(A.y, B.y) + M;
         const int64_t b0 = std::max<int64_t>(0, (int64_t)std::floor((ylo - lo) / h));
@@ -376,7 +386,10 @@ static void build_bands(Index* idx, uint32_t k, PolyLocal* L) {
     }
     uint64_t total = nb + 1;
     for (auto& l : lists) total += l.size();
-    if (total > kBandMaxWords) return;          // too large to stage: test every edge
+    if (total > kBandMaxWords) {                // too large to stage: test every edge
+        if (holes) L->ok = 0;
+        return;
+    }
     L->band = (uint32_t)idx->poly_band.size();
     L->nb = nb;
     L->inv_h = (float)((double)nb / (hi - lo));
@@ -419,7 +432,9 @@ void prepare_poly_local(Index* idx, bool bands) {
         if ((double)L.dv < dv) L.dv = std::nextafter(L.dv, 1.0f);
         L.bu0 = (float)(u0 - L.ru); L.bu1 = (float)(u1 - L.ru);
         L.bv0 = (float)(v0 - L.rv); L.bv1 = (float)(v1 - L.rv);
-        if (bands) build_bands(idx, k, &L);
+        // a polygon with holes needs its table whatever `bands` says
+        if (bands || (idx->ring_off.size() == P + 1 && idx->ring_off[k + 1] > idx->ring_off[k]))
+            build_bands(idx, k, &L);
         idx->poly_local[k] = L;
     }
 }

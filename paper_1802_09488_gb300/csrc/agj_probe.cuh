@@ -560,19 +560,28 @@ __device__ __forceinline__ bool covers_fp64(const DevIndex& X, uint32_t poly, do
     const int64_t* bb = X.poly_bbox + 4ull * poly;
     if (!(puk >= bb[0] && puk <= bb[1] && pvk >= bb[2] && pvk <= bb[3])) return false;
     const uint32_t v0 = X.poly_off[poly], V = X.poly_off[poly + 1] - v0;
+    const uint32_t r0 = X.ring_off[poly], r1 = X.ring_off[poly + 1];
     bool inside = false;
-    for (uint32_t k = 0; k < V; ++k) {
-        const uint32_t a = v0 + k, b = v0 + (k + 1 == V ? 0u : k + 1);
-        const int64_t av = X.poly_vkey[a], bv = X.poly_vkey[b];
-        const int64_t vlo = av < bv ? av : bv, vhi = av < bv ? bv : av;
-        if (pvk < vlo || pvk > vhi) continue;
-        const double2 A = X.poly_uv[a], B = X.poly_uv[b];
-        const double o = (B.x - A.x) * (pv - A.y) - (B.y - A.y) * (pu - A.x);
-        if (o == 0.0) {
-            const int64_t au = X.poly_ukey[a], bu = X.poly_ukey[b];
-            if (puk >= (au < bu ? au : bu) && puk <= (au < bu ? bu : au)) return X.contains == 0u;
+    for (uint32_t r = r0, start = 0;; ++r) {
+        // edges (k, k + 1) for k in [start, stop): one ring -> every vertex
+        // (the last edge wraps to vertex 0); with holes -> each ring up to
+        // its closing copy of its first vertex
+        const uint32_t stop = r1 > r0 ? X.ring_end[r] - 1 : V;
+        for (uint32_t k = start; k < stop; ++k) {
+            const uint32_t a = v0 + k, b = v0 + (k + 1 == V ? 0u : k + 1);
+            const int64_t av = X.poly_vkey[a], bv = X.poly_vkey[b];
+            const int64_t vlo = av < bv ? av : bv, vhi = av < bv ? bv : av;
+            if (pvk < vlo || pvk > vhi) continue;
+            const double2 A = X.poly_uv[a], B = X.poly_uv[b];
+            const double o = (B.x - A.x) * (pv - A.y) - (B.y - A.y) * (pu - A.x);
+            if (o == 0.0) {
+                const int64_t au = X.poly_ukey[a], bu = X.poly_ukey[b];
+                if (puk >= (au < bu ? au : bu) && puk <= (au < bu ? bu : au)) return X.contains == 0u;
+            }
+            if ((av <= pvk && pvk < bv && o > 0.0) || (bv <= pvk && pvk < av && o < 0.0)) inside = !inside;
         }
-        if ((av <= pvk && pvk < bv && o > 0.0) || (bv <= pvk && pvk < av && o < 0.0)) inside = !inside;
+        if (r + 1 >= r1) break;
+        start = X.ring_end[r];
     }
     return inside;
 }

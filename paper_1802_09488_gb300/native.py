@@ -32,7 +32,16 @@ class AgjError(RuntimeError):
 
 
 class Polygon(C.Structure):
-    _fields_ = [("n_vertices", C.c_uint32), ("latlng", C.c_void_p)]
+    _fields_ = [("n_vertices", C.c_uint32), ("n_rings", C.c_uint32), ("latlng", C.c_void_p),
+                ("ring_ends", C.c_void_p)]
+
+
+def _polygon_rings(p):
+    """A polygon as its rings: an (V,2) array is one ring; a list or tuple of
+    arrays is the outer ring followed by its holes."""
+    if isinstance(p, (list, tuple)):
+        return [np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 2) for r in p]
+    return [np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 2)]
 
 
 class BuildOpts(C.Structure):
@@ -196,11 +205,16 @@ class Index:
                  max_interior_level: int = 0, host_only: bool = False, fast_ids: bool = True, pip_bands: bool = True,
                  predicate: int = COVERS, stream=None):
         L = lib()
-        self._polys = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 2) for p in polygons]
+        # polygons: each an (V,2) (lat,lng) ring, or [outer, hole, ...]
+        rings = [_polygon_rings(p) for p in polygons]
+        self._polys = [np.ascontiguousarray(np.concatenate(rs)) for rs in rings]
+        self._ring_ends = [np.cumsum([len(r) for r in rs]).astype(np.uint32) for rs in rings]
         arr = (Polygon * max(len(self._polys), 1))()
         for k, p in enumerate(self._polys):
             arr[k].n_vertices = len(p)
             arr[k].latlng = p.ctypes.data
+            arr[k].n_rings = len(rings[k])
+            arr[k].ring_ends = self._ring_ends[k].ctypes.data
         opts = BuildOpts()
         opts.memory_budget_bytes = int(budget_bytes)
         opts.n_threads = int(threads)

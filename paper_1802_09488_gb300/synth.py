@@ -406,3 +406,81 @@ def batched_jobs(m: int = 64, seed: int = 11, polys: tuple[int, int] = (5, 40_00
         exact = exact_every > 0 and j % exact_every == exact_every - 1
         jobs.append(Job(pl, pts, exact, 4.0, tr if exact else None))
     return jobs
+
+
+# ---------------------------------------------------------------------------
+# polygons with holes
+# ---------------------------------------------------------------------------
+
+def _seg_dist(p: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Planar distances from point p (2,) to the segments a[i]-b[i]."""
+    d = b - a
+    t = np.clip(((p - a) * d).sum(-1) / np.maximum((d * d).sum(-1), 1e-300), 0.0, 1.0)
+    q = a + t[:, None] * d
+    return np.hypot(*(p - q).T)
+
+
+def _inside(p: np.ndarray, ring: np.ndarray) -> bool:
+    """Planar even-odd test (generator use only: it picks hole centres well
+    away from every edge)."""
+    a, b = ring, np.roll(ring, -1, axis=0)
+    cross = ((a[:, 1] > p[1]) != (b[:, 1] > p[1]))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        x = a[:, 0] + (p[1] - a[:, 1]) * (b[:, 0] - a[:, 0]) / (b[:, 1] - a[:, 1])
+    return bool(np.count_nonzero(cross & (x > p[0])) % 2)
+
+
+def with_holes(polys: list, seed: int, frac: float = 0.35, max_holes: int = 3, vmin: int = 6,
+               vmax: int = 16) -> list:
+    """A copy of polys where a fraction of the polygons get 1..max_holes holes:
+    jittered regular rings of vmin..vmax vertices, each centred on a random
+    interior point and sized to a third of its clearance from the outer ring
+    and the holes placed before it, listed in the opposite orientation.  A
+    polygon with holes is returned as [outer, hole, ...]; the others as
+    before.  Planar geometry in local metres (the polygons are a few km
+    across, so the thirds leave ample room for the curvature of the
+    geodesic edges)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for P in polys:
+        P = np.asarray(P, dtype=np.float64)
+        if rng.random() >= frac:
+            out.append(P)
+            continue
+        lat0 = float(P[:, 0].mean())
+        kx = 111195.0 * np.cos(np.radians(lat0))
+        xy = np.stack([(P[:, 1] - P[:, 1].mean()) * kx, (P[:, 0] - lat0) * 111195.0], -1)
+        a, b = xy, np.roll(xy, -1, axis=0)
+        holes_xy = []
+        want = int(rng.integers(1, max_holes + 1))
+        lo, hi = xy.min(0), xy.max(0)
+        for _ in range(200):
+            if len(holes_xy) == want:
+                break
+            c = rng.uniform(lo, hi)
+            if not _inside(c, xy):
+                continue
+            clear = float(_seg_dist(c, a, b).min())
+            for h in holes_xy:
+                clear = min(clear, float(_seg_dist(c, h, np.roll(h, -1, axis=0)).min()))
+                if _inside(c, h):
+                    clear = 0.0
+            r = clear / 3.0
+            if r < 20.0:          # metres: too tight a spot
+                continue
+            m = int(rng.integers(vmin, vmax + 1))
+            ang = np.linspace(0.0, 2 * np.pi, m, endpoint=False) + rng.uniform(0, 2 * np.pi)
+            rad = r * rng.uniform(0.7, 1.0, m)
+            ring = c + np.stack([rad * np.cos(ang), rad * np.sin(ang)], -1)
+            holes_xy.append(ring[::-1])
+        if not holes_xy:
+            out.append(P)
+            continue
+        to_ll = lambda q: np.stack([q[:, 1] / 111195.0 + lat0, q[:, 0] / kx + P[:, 1].mean()], -1)
+        out.append([P] + [np.ascontiguousarray(to_ll(h)) for h in holes_xy])
+    return out
+
+
+def c2_city_holes_polygons() -> list:
+    """The city polygons, a third of them with one to three holes (seed 8)."""
+    return with_holes(c2_city_polygons(), seed=8)
