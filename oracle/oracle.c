@@ -429,7 +429,21 @@ typedef struct {
     int64_t *g_start[6];   /* grid_n*grid_n + 1 */
     int32_t *g_items[6];
     int contains;          /* 0: ST_Covers / ST_Intersects, 1: ST_Contains (boundary excluded) */
+    /* polygons whose vertices lie on more than one face (face[k] == OR_CAP):
+     * each has a centre c (unit vector) and a tangent basis e1, e2; its
+     * vertices are projected gnomonically about c into cap_uv, its bbox
+     * there is bbox[4k..]; cap_ids lists them ascending */
+    double *xyz;           /* 3 per vertex */
+    double *cap_frame;     /* 9 per polygon: c, e1, e2 */
+    double *cap_uv;        /* 2 per vertex (cap polygons only) */
+    int64_t *cap_ids;
+    int64_t n_caps;
 } or_polyset;
+
+/* face[k] of a polygon spanning cube faces (its vertices within
+ * OR_CAP_COS of their normalised mean) */
+#define OR_CAP 6
+#define OR_CAP_COS 0.96592582628906831   /* cos 15 degrees */
 
 static int or_cmp_i32(const void *a, const void *b) {
     int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
@@ -439,8 +453,67 @@ static int or_cmp_i32(const void *a, const void *b) {
 void or_polyset_free(or_polyset *ps) {
     if (!ps) return;
     free(ps->off); free(ps->pr); free(ps->rv); free(ps->uv); free(ps->face); free(ps->bbox);
+    free(ps->xyz); free(ps->cap_frame); free(ps->cap_uv); free(ps->cap_ids);
     for (int f = 0; f < 6; ++f) { free(ps->g_start[f]); free(ps->g_items[f]); }
     free(ps);
+}
+
+/* A polygon whose vertices lie on more than one cube face: its geodesic
+ * edges are straight lines in any gnomonic projection whose centre sees all
+ * of it, so the ring rule runs in the projection about the normalised mean
+ * c of its vertices (a plane of the oracle's own, independent of the cube
+ * faces).  Supported when every vertex is within 15 degrees of c (then the
+ * polygon and any point tested lie well inside c's hemisphere).  Fills the
+ * frame, the projected vertices and the bbox; returns OR_CAP or -1. */
+static void or_cap_project(const double *frame, const double p[3], double *u, double *v) {
+    double w = frame[0] * p[0] + frame[1] * p[1] + frame[2] * p[2];
+    *u = (frame[3] * p[0] + frame[4] * p[1] + frame[5] * p[2]) / w;
+    *v = (frame[6] * p[0] + frame[7] * p[1] + frame[8] * p[2]) / w;
+}
+
+static int or_cap_prepare(or_polyset *ps, int64_t k) {
+    int64_t s = ps->off[k], e = ps->off[k + 1];
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int64_t t = s; t < e; ++t) {
+        const double *p = ps->xyz + 3 * t;
+        if (!(p[0] == p[0])) return -1;          /* an invalid vertex */
+        c[0] += p[0]; c[1] += p[1]; c[2] += p[2];
+    }
+    double n = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    if (!(n > 0.0)) return -1;
+    c[0] /= n; c[1] /= n; c[2] /= n;
+    for (int64_t t = s; t < e; ++t) {
+        const double *p = ps->xyz + 3 * t;
+        if (!(p[0] * c[0] + p[1] * c[1] + p[2] * c[2] >= OR_CAP_COS)) return -1;
+    }
+    /* e1 perpendicular to c (built from the axis least aligned with c), e2 = c x e1 */
+    double a[3] = {0.0, 0.0, 0.0};
+    int m = fabs(c[0]) <= fabs(c[1]) ? (fabs(c[0]) <= fabs(c[2]) ? 0 : 2) : (fabs(c[1]) <= fabs(c[2]) ? 1 : 2);
+    a[m] = 1.0;
+    double e1[3], e2[3];
+    double d = a[0] * c[0] + a[1] * c[1] + a[2] * c[2];
+    for (int q = 0; q < 3; ++q) e1[q] = a[q] - d * c[q];
+    double ne = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int q = 0; q < 3; ++q) e1[q] /= ne;
+    e2[0] = c[1] * e1[2] - c[2] * e1[1];
+    e2[1] = c[2] * e1[0] - c[0] * e1[2];
+    e2[2] = c[0] * e1[1] - c[1] * e1[0];
+    double *f = ps->cap_frame + 9 * k;
+    for (int q = 0; q < 3; ++q) { f[q] = c[q]; f[3 + q] = e1[q]; f[6 + q] = e2[q]; }
+    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    for (int64_t t = s; t < e; ++t) {
+        double u, v;
+        or_cap_project(f, ps->xyz + 3 * t, &u, &v);
+        ps->cap_uv[2 * t] = u; ps->cap_uv[2 * t + 1] = v;
+        if (u < umin) umin = u;
+        if (u > umax) umax = u;
+        if (v < vmin) vmin = v;
+        if (v > vmax) vmax = v;
+    }
+    ps->bbox[4 * k] = umin; ps->bbox[4 * k + 1] = umax;
+    ps->bbox[4 * k + 2] = vmin; ps->bbox[4 * k + 3] = vmax;
+    ps->cap_ids[ps->n_caps++] = k;
+    return OR_CAP;
 }
 
 or_polyset *or_polyset_new_rings(const double *latlng, const int64_t *ring_off, const int64_t *poly_ring_off,
@@ -455,6 +528,17 @@ or_polyset *or_polyset_new_rings(const double *latlng, const int64_t *ring_off, 
     ps->off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_polys + 1));
     for (int64_t k = 0; k <= n_polys; ++k) ps->off[k] = ring_off[poly_ring_off[k]];
     const int64_t *off = ps->off;
+    {
+        int64_t nvv = off[n_polys] > 0 ? off[n_polys] : 1;
+        ps->xyz = (double *)malloc(sizeof(double) * 3 * (size_t)nvv);
+        ps->cap_uv = (double *)calloc(2 * (size_t)nvv, sizeof(double));
+        ps->cap_frame = (double *)calloc(9 * (size_t)(n_polys > 0 ? n_polys : 1), sizeof(double));
+        ps->cap_ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_polys > 0 ? n_polys : 1));
+        ps->n_caps = 0;
+        for (int64_t t = 0; t < off[n_polys]; ++t)
+            if (or_point_valid(latlng[2 * t], latlng[2 * t + 1])) or_latlng_xyz(latlng[2 * t], latlng[2 * t + 1], ps->xyz + 3 * t);
+            else ps->xyz[3 * t] = ps->xyz[3 * t + 1] = ps->xyz[3 * t + 2] = NAN;
+    }
     int64_t nv = off[n_polys];
     ps->uv = (double *)malloc(sizeof(double) * 2 * (size_t)(nv > 0 ? nv : 1));
     ps->face = (int *)malloc(sizeof(int) * (size_t)(n_polys > 0 ? n_polys : 1));
@@ -473,12 +557,13 @@ or_polyset *or_polyset_new_rings(const double *latlng, const int64_t *ring_off, 
             if (v < vmin) vmin = v;
             if (v > vmax) vmax = v;
         }
-        if (ps->pr[k + 1] <= ps->pr[k]) face = -1;
+        int bad = ps->pr[k + 1] <= ps->pr[k];
         for (int64_t r = ps->pr[k]; r < ps->pr[k + 1]; ++r)
-            if (ps->rv[r + 1] - ps->rv[r] < 3) face = -1;
-        ps->face[k] = face < 0 ? -1 : face;
+            if (ps->rv[r + 1] - ps->rv[r] < 3) bad = 1;
         ps->bbox[4 * k] = umin; ps->bbox[4 * k + 1] = umax;
         ps->bbox[4 * k + 2] = vmin; ps->bbox[4 * k + 3] = vmax;
+        if (face == -1 && !bad) face = or_cap_prepare(ps, k);
+        ps->face[k] = (face < 0 || bad) ? -1 : face;
     }
     /* uniform grid per face over the union of the polygons' bboxes; each
      * polygon is registered in every grid cell its bbox, widened by 1e-9,
@@ -586,9 +671,29 @@ static int or_pred_uv(const or_polyset *ps, int64_t k, double u, double v) {
     return ps->contains ? rel == 2 : rel != 0;
 }
 
+/* The set's predicate for a polygon spanning faces (OR_CAP) and a point
+ * given by its unit vector: in the polygon's own gnomonic plane. */
+static int or_pred_cap(const or_polyset *ps, int64_t k, const double p[3]) {
+    const double *f = ps->cap_frame + 9 * k;
+    if (!(p[0] * f[0] + p[1] * f[1] + p[2] * f[2] > 0.5)) return 0;   /* > 60 degrees from the centre: outside */
+    double u, v;
+    or_cap_project(f, p, &u, &v);
+    const double *bb = ps->bbox + 4 * k;
+    if (!(u >= bb[0] && u <= bb[1] && v >= bb[2] && v <= bb[3])) return 0;
+    int rel = or_rings_relate_uv(ps->cap_uv, ps->rv + ps->pr[k], ps->pr[k + 1] - ps->pr[k], u, v);
+    return ps->contains ? rel == 2 : rel != 0;
+}
+
 /* ST_Covers(P_k, p) (or ST_Contains with the set's predicate): same face,
- * inside the closed uv bbox, ring rule. */
+ * inside the closed uv bbox, ring rule; a polygon spanning faces in its own
+ * gnomonic plane. */
 int or_polygon_covers(const or_polyset *ps, int64_t k, double lat, double lng) {
+    if (ps->face[k] == OR_CAP) {
+        if (!or_point_valid(lat, lng)) return 0;
+        double p[3];
+        or_latlng_xyz(lat, lng, p);
+        return or_pred_cap(ps, k, p);
+    }
     double u, v;
     int f = or_face_uv(lat, lng, &u, &v);
     if (f < 0 || f != ps->face[k]) return 0;
@@ -619,6 +724,21 @@ static int64_t or_point_hits(const or_polyset *ps, double lat, double lng, uint3
         int32_t k = items[t];
         if (or_pred_uv(ps, k, u, v)) {
             if (out) out[cnt] = (uint32_t)k;
+            ++cnt;
+        }
+    }
+    if (ps->n_caps) {
+        /* polygons spanning faces: every one, then merged in ascending order */
+        double p[3];
+        or_latlng_xyz(lat, lng, p);
+        for (int64_t t = 0; t < ps->n_caps; ++t) {
+            int64_t k = ps->cap_ids[t];
+            if (!or_pred_cap(ps, k, p)) continue;
+            if (out) {
+                int64_t b = cnt - 1;
+                while (b >= 0 && out[b] > (uint32_t)k) { out[b + 1] = out[b]; --b; }
+                out[b + 1] = (uint32_t)k;
+            }
             ++cnt;
         }
     }
@@ -791,11 +911,16 @@ double or_dist_point_polygon_m(const or_polyset *ps, int64_t k, double lat, doub
     for (int64_t r = ps->pr[k]; r < ps->pr[k + 1]; ++r) {
         int64_t s = ps->rv[r], nv = ps->rv[r + 1] - s;
         for (int64_t t = 0; t < nv; ++t) {
-            const double *a = ps->uv + 2 * (s + t);
-            const double *b = ps->uv + 2 * (s + (t + 1) % nv);
             double A[3], B[3];
-            or_face_uv_to_xyz(f, a[0], a[1], A);
-            or_face_uv_to_xyz(f, b[0], b[1], B);
+            if (f == OR_CAP) {
+                const double *a = ps->xyz + 3 * (s + t), *b = ps->xyz + 3 * (s + (t + 1) % nv);
+                for (int q = 0; q < 3; ++q) { A[q] = a[q]; B[q] = b[q]; }
+            } else {
+                const double *a = ps->uv + 2 * (s + t);
+                const double *b = ps->uv + 2 * (s + (t + 1) % nv);
+                or_face_uv_to_xyz(f, a[0], a[1], A);
+                or_face_uv_to_xyz(f, b[0], b[1], B);
+            }
             double ang = or_angle_point_arc(p, A, B);
             if (ang < best) best = ang;
         }
@@ -828,15 +953,32 @@ static int or_seg_meets_rect(const double a[2], const double b[2], const double 
     return 1;
 }
 
-/* Does an edge of any ring of polygon k meet the closed rectangle r? */
-static int or_polygon_meets_rect(const or_polyset *ps, int64_t k, const double r[4]) {
-    for (int64_t q = ps->pr[k]; q < ps->pr[k + 1]; ++q) {
-        const double *uv = ps->uv + 2 * ps->rv[q];
-        int64_t nv = ps->rv[q + 1] - ps->rv[q];
+/* Does an edge of any ring meet the closed rectangle r?  Ring q spans the
+ * vertices ring_off[q] .. ring_off[q+1]-1 of uv. */
+static int or_rings_meet_rect(const double *uv0, const int64_t *ring_off, int64_t n_rings, const double r[4]) {
+    for (int64_t q = 0; q < n_rings; ++q) {
+        const double *uv = uv0 + 2 * ring_off[q];
+        int64_t nv = ring_off[q + 1] - ring_off[q];
         for (int64_t e = 0; e < nv; ++e)
             if (or_seg_meets_rect(uv + 2 * e, uv + 2 * ((e + 1) % nv), r)) return 1;
     }
     return 0;
+}
+
+/* The (u,v) of a point given by its unit vector on the plane of `face`
+ * (the face's gnomonic coordinates, also beyond the face's square); 0 when
+ * the point is not in the face's open hemisphere. */
+static int or_xyz_uv_on_face(int face, const double xyz[3], double *u, double *v) {
+    double x = xyz[0], y = xyz[1], z = xyz[2];
+    switch (face) {
+    case 0: if (!(x > 0.0)) return 0; *u = y / x;  *v = z / x;  break;
+    case 1: if (!(y > 0.0)) return 0; *u = -x / y; *v = z / y;  break;
+    case 2: if (!(z > 0.0)) return 0; *u = -x / z; *v = -y / z; break;
+    case 3: if (!(x < 0.0)) return 0; *u = z / x;  *v = y / x;  break;
+    case 4: if (!(y < 0.0)) return 0; *u = z / y;  *v = -x / y; break;
+    default: if (!(z < 0.0)) return 0; *u = -y / z; *v = -x / z; break;
+    }
+    return 1;
 }
 
 /* report[0] = overlapping neighbour pairs (disjointness),
@@ -857,22 +999,41 @@ void or_check_covering(const or_polyset *ps, const uint64_t *cells, int64_t m, c
         for (uint64_t t = ref_off[c]; t < ref_off[c + 1]; ++t) {
             uint32_t pid = refs[t] >> 1;
             int interior = (int)(refs[t] & 1u);
-            if ((int64_t)pid >= ps->n_polys || ps->face[pid] != face) { report[4]++; continue; }
+            if ((int64_t)pid >= ps->n_polys || (ps->face[pid] != face && ps->face[pid] != OR_CAP)) {
+                report[4]++;
+                continue;
+            }
+            /* the polygon's rings in the cell's face coordinates: stored for a
+             * one-face polygon, projected onto the face for one spanning faces */
+            int64_t v0 = ps->off[pid], nv = ps->off[pid + 1] - v0;
+            int64_t nr = ps->pr[pid + 1] - ps->pr[pid];
+            const double *uv = ps->uv + 2 * v0;
+            double *tmp = NULL;
+            int64_t *roff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nr + 1));
+            for (int64_t q = 0; q <= nr; ++q) roff[q] = ps->rv[ps->pr[pid] + q] - v0;
+            if (ps->face[pid] == OR_CAP) {
+                tmp = (double *)malloc(sizeof(double) * 2 * (size_t)nv);
+                int ok = 1;
+                for (int64_t t = 0; t < nv && ok; ++t)
+                    ok = or_xyz_uv_on_face(face, ps->xyz + 3 * (v0 + t), tmp + 2 * t, tmp + 2 * t + 1);
+                if (!ok) { report[4]++; free(tmp); free(roff); continue; }
+                uv = tmp;
+            }
             double cu = 0.5 * (r[0] + r[1]), cv = 0.5 * (r[2] + r[3]);
-            int center_in = or_polygon_relate_uv(ps, pid, cu, cv) != 0;
+            int center_in = or_rings_relate_uv(uv, roff, nr, cu, cv) != 0;
             if (interior) {
-                int meets = or_polygon_meets_rect(ps, pid, r);
+                int meets = or_rings_meet_rect(uv, roff, nr, r);
                 if (meets || !center_in) report[1]++;
             } else {
                 has_cand = 1;
                 double w[4] = {r[0] - cand_margin, r[1] + cand_margin, r[2] - cand_margin, r[3] + cand_margin};
-                int meets = or_polygon_meets_rect(ps, pid, w), vertex_in = 0;
-                const double *uv = ps->uv + 2 * ps->off[pid];
-                int64_t nv = ps->off[pid + 1] - ps->off[pid];
+                int meets = or_rings_meet_rect(uv, roff, nr, w), vertex_in = 0;
                 for (int64_t e = 0; e < nv && !vertex_in; ++e)
                     vertex_in = uv[2 * e] >= w[0] && uv[2 * e] <= w[1] && uv[2 * e + 1] >= w[2] && uv[2 * e + 1] <= w[3];
                 if (!meets && !center_in && !vertex_in) report[2]++;
             }
+            free(tmp);
+            free(roff);
         }
         if (eps_m > 0.0 && has_cand && !(or_cell_diag_m(cells[c]) < eps_m)) report[3]++;
     }

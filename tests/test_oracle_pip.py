@@ -176,10 +176,13 @@ def test_grid_join_equals_brute_force_random(oracle):
         assert list(ids[offs[k]:offs[k + 1]]) == ps.hits_brute(*pts[k])
 
 
-def test_polygon_on_two_faces_is_rejected(oracle):
-    ps = oracle.PolySet([np.array([[0.0, 44.0], [1.0, 46.0], [-1.0, 46.0]])])   # straddles lng 45 (faces 0/1)
+def test_polygon_wider_than_the_cap_is_rejected(oracle):
+    """Polygons spanning cube faces are supported within 15 degrees of their
+    vertices' mean (tests/test_oracle_crossface.py); a wider one joins
+    nothing."""
+    ps = oracle.PolySet([np.array([[0.0, 30.0], [20.0, 45.0], [-20.0, 60.0]])])
     assert ps.face(0) == -1
-    assert not ps.covers(0, 0.0, 45.5)
+    assert not ps.covers(0, 0.0, 45.0)
 
 
 def test_distance_zero_inside_and_edge_distance(oracle):
