@@ -210,7 +210,9 @@ int agj_lut_encode(const uint32_t* refs, const uint64_t* ref_off, uint64_t n_lis
 /* Copies the flattened trie to host: nodes (n_nodes * 256 uint64 tagged
  * entries), the lookup table (n_lut_words) and the face table (6 x
  * {root node or 0xFFFFFFFF, prefix length in key bits, prefix}).  NULL arrays
- * are skipped. */
+ * are skipped.  The entries' polygon references name the index's pieces:
+ * the input polygons themselves unless a polygon crosses cube faces (then
+ * it has one piece per face it reaches, numbered in polygon order). */
 int agj_index_trie(const agj_index* index, uint64_t* nodes, uint32_t* lut, uint64_t face_table[18]);
 
 /* ---------------------------------------------------------------------- */
@@ -646,7 +648,8 @@ int agj_fast_ids_host(const agj_index* index, const double* h_points, uint64_t n
  * The certified FP32 refine test on the host, with the same model and
  * arithmetic the PIP kernel uses: for point k and polygon h_polys[k],
  * h_out[k] = 1 (covered), 0 (not covered) or -1 (undecided: the kernel then
- * recomputes the test in FP64).  Host only.
+ * recomputes the test in FP64).  A polygon across cube faces is tested as
+ * its piece on the point's face (0 when it has none there).  Host only.
  */
 int agj_covers_certified_host(const agj_index* index, const double* h_points, const uint32_t* h_polys, uint64_t n,
                               int8_t* h_out);

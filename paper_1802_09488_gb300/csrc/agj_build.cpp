@@ -46,6 +46,8 @@ namespace agj {
 namespace {
 
 constexpr double kMargin = 1e-12;
+constexpr double kCapCos = 0.96592582628906831;       // cos 15 degrees: a cross-face polygon's extent
+constexpr double kCapFaceCos = 0.34611705707749302;   // cos 69.75 degrees: faces such a polygon can reach
 constexpr double kEarthR = 6371008.8;
 constexpr double kDiagSlack = 2e-5;   // metres: widened-rectangle allowance in the precision test
 
@@ -767,16 +769,24 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
     const unsigned threads = bp.threads ? bp.threads : std::max(1u, std::thread::hardware_concurrency());
     Index& X = *out;
     X.mode = bp.mode;
-    X.n_polys = n_polys;
+    X.n_input_polys = n_polys;
     X.precision_m = bp.precision_m;
-    X.poly_off.assign(n_polys + 1, 0);
-    X.ring_off.assign(n_polys + 1, 0);
-    X.ring_end.clear();
+    // Validate the ring lists, then turn every polygon into pieces: one per
+    // cube face it reaches, each the whole polygon in that face's gnomonic
+    // (u,v) plane (its geodesic edges are straight there, and points on the
+    // face are tested against it).  A polygon on one face is one piece with
+    // the face coordinates of its vertices.  A polygon across faces must lie
+    // within 15 degrees of its vertices' normalised mean c; it gets a piece on
+    // each face whose axis is within 69.75 degrees of c (the faces its cap
+    // can reach; every vertex is then in the face's open hemisphere) and
+    // whose square its bbox meets.  Pieces are ordered by polygon, so piece
+    // ids map to polygon ids monotonically (piece_poly).
+    std::vector<uint32_t> piece_src;       // input polygon of each piece
+    std::vector<int> piece_face;
     for (uint32_t k = 0; k < n_polys; ++k) {
         const agj_polygon& g = polys[k];
         if (g.n_vertices < 3 || !g.latlng) { *err = "polygon needs >= 3 vertices"; return AGJ_EINVAL; }
         if (g.n_rings >= 2) {
-            // rings stored explicitly closed: one more vertex per ring
             if (!g.ring_ends) { *err = "polygon with holes needs ring ends"; return AGJ_EINVAL; }
             uint32_t prev = 0;
             for (uint32_t q = 0; q < g.n_rings; ++q) {
@@ -785,32 +795,86 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
                     return AGJ_EINVAL;
                 }
                 prev = g.ring_ends[q];
-                X.ring_end.push_back(g.ring_ends[q] + q + 1);
             }
             if (prev != g.n_vertices) { *err = "the last ring end must be n_vertices"; return AGJ_EINVAL; }
+        }
+        int face = -1;
+        bool one_face = true;
+        double c[3] = {0.0, 0.0, 0.0};
+        for (uint32_t t = 0; t < g.n_vertices; ++t) {
+            const double lat = g.latlng[2 * t], lng = g.latlng[2 * t + 1];
+            if (!point_valid(lat, lng)) { *err = "invalid polygon vertex"; return AGJ_EINVAL; }
+            double u, v, xyz[3];
+            const int f = face_uv(lat, lng, &u, &v);
+            if (face >= 0 && f != face) one_face = false;
+            face = f;
+            latlng_xyz(lat, lng, xyz);
+            c[0] += xyz[0]; c[1] += xyz[1]; c[2] += xyz[2];
+        }
+        if (one_face) {
+            piece_src.push_back(k);
+            piece_face.push_back(face);
+            continue;
+        }
+        const double n = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        for (int q = 0; q < 3; ++q) c[q] /= n;
+        for (uint32_t t = 0; t < g.n_vertices; ++t) {
+            double xyz[3];
+            latlng_xyz(g.latlng[2 * t], g.latlng[2 * t + 1], xyz);
+            if (!(xyz[0] * c[0] + xyz[1] * c[1] + xyz[2] * c[2] >= kCapCos)) {
+                *err = "a polygon across cube faces must lie within 15 degrees of its vertices' mean";
+                return AGJ_EUNSUPPORTED;
+            }
+        }
+        for (int f = 0; f < 6; ++f) {
+            const double axis = f < 3 ? c[f] : -c[f - 3];
+            if (axis < kCapFaceCos) continue;
+            double bb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
+            for (uint32_t t = 0; t < g.n_vertices; ++t) {
+                double xyz[3], u, v;
+                latlng_xyz(g.latlng[2 * t], g.latlng[2 * t + 1], xyz);
+                if (!xyz_uv_on_face(f, xyz, &u, &v)) { *err = "projection outside the face's hemisphere"; return AGJ_EUNSUPPORTED; }
+                bb[0] = std::min(bb[0], u); bb[1] = std::max(bb[1], u);
+                bb[2] = std::min(bb[2], v); bb[3] = std::max(bb[3], v);
+            }
+            if (bb[1] < -1.0 || bb[0] > 1.0 || bb[3] < -1.0 || bb[2] > 1.0) continue;
+            piece_src.push_back(k);
+            piece_face.push_back(f);
+        }
+    }
+    const uint32_t n_pieces = (uint32_t)piece_src.size();
+    if (n_pieces >= kMaxPolys) { *err = "too many polygon pieces"; return AGJ_EUNSUPPORTED; }
+    X.n_polys = n_pieces;
+    X.piece_poly.clear();
+    if (n_pieces != n_polys) X.piece_poly = piece_src;
+    X.poly_off.assign(n_pieces + 1, 0);
+    X.ring_off.assign(n_pieces + 1, 0);
+    X.ring_end.clear();
+    for (uint32_t k = 0; k < n_pieces; ++k) {
+        const agj_polygon& g = polys[piece_src[k]];
+        if (g.n_rings >= 2) {
+            // rings stored explicitly closed: one more vertex per ring
+            for (uint32_t q = 0; q < g.n_rings; ++q) X.ring_end.push_back(g.ring_ends[q] + q + 1);
             X.poly_off[k + 1] = X.poly_off[k] + g.n_vertices + g.n_rings;
         } else {
             X.poly_off[k + 1] = X.poly_off[k] + g.n_vertices;
         }
         X.ring_off[k + 1] = (uint32_t)X.ring_end.size();
     }
-    X.poly_uv.assign(2ull * X.poly_off[n_polys], 0.0);
-    X.poly_bbox.assign(4ull * n_polys, 0.0);
-    X.poly_face.assign(n_polys, (int8_t)-1);
-    std::vector<Poly> P(n_polys);
-    std::vector<std::vector<uint32_t>> edges(n_polys);
-    for (uint32_t k = 0; k < n_polys; ++k) {
-        const agj_polygon& g = polys[k];
-        int face = -1;
+    X.poly_uv.assign(2ull * X.poly_off[n_pieces], 0.0);
+    X.poly_bbox.assign(4ull * n_pieces, 0.0);
+    X.poly_face.assign(n_pieces, (int8_t)-1);
+    std::vector<Poly> P(n_pieces);
+    std::vector<std::vector<uint32_t>> edges(n_pieces);
+    for (uint32_t k = 0; k < n_pieces; ++k) {
+        const agj_polygon& g = polys[piece_src[k]];
+        const int face = piece_face[k];
         double bb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
         uint32_t out = X.poly_off[k], ring = 0, ring_first = out;
         for (uint32_t t = 0; t < g.n_vertices; ++t) {
-            const double lat = g.latlng[2 * t], lng = g.latlng[2 * t + 1];
-            if (!point_valid(lat, lng)) { *err = "invalid polygon vertex"; return AGJ_EINVAL; }
-            double u, v;
-            const int f = face_uv(lat, lng, &u, &v);
-            if (face >= 0 && f != face) { *err = "polygon spans more than one cube face"; return AGJ_EUNSUPPORTED; }
-            face = f;
+            double u, v, xyz[3];
+            latlng_xyz(g.latlng[2 * t], g.latlng[2 * t + 1], xyz);
+            xyz_uv_on_face(face, xyz, &u, &v);       // = face_uv's (u,v) for a vertex on this face
             X.poly_uv[2 * out] = u;
             X.poly_uv[2 * out + 1] = v;
             ++out;
@@ -833,6 +897,7 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
             P[k].n_edges = (uint32_t)edges[k].size();
         }
     }
+    n_polys = n_pieces;       // from here on the index's polygons are the pieces
 
     // per-polygon coverings and interior coverings
     std::vector<std::vector<uint64_t>> cov(n_polys), inter(n_polys);
@@ -901,7 +966,7 @@ int build_host(const agj_polygon* polys, uint32_t n_polys, const BuildParams& bp
     X.stats.fast_ids = (uint32_t)X.model.enabled;
     X.stats.fast_err_cells = X.model.enabled ? (double)X.model.err : 0.0;
     X.stats.mode = (uint32_t)bp.mode;
-    X.stats.n_polys = n_polys;
+    X.stats.n_polys = X.n_input_polys;
     X.stats.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return AGJ_OK;
 }

@@ -144,7 +144,16 @@ int agj_index_logical(const agj_index* index, uint64_t* cells, uint64_t* ref_off
     if (n_refs) *n_refs = X.refs.size();
     if (cells) std::copy(X.cells.begin(), X.cells.end(), cells);
     if (ref_off) std::copy(X.ref_off.begin(), X.ref_off.end(), ref_off);
-    if (refs) std::copy(X.refs.begin(), X.refs.end(), refs);
+    if (refs) {
+        // references name input polygons (the index refers to pieces; a cell
+        // lies on one face, so it holds at most one piece of a polygon)
+        if (X.piece_poly.empty()) {
+            std::copy(X.refs.begin(), X.refs.end(), refs);
+        } else {
+            for (size_t t = 0; t < X.refs.size(); ++t)
+                refs[t] = X.piece_poly[X.refs[t] >> 1] << 1 | (X.refs[t] & 1u);
+        }
+    }
     return AGJ_OK;
 }
 
@@ -468,8 +477,18 @@ int agj_covers_certified_host(const agj_index* index, const double* h_points, co
     if (!index || (n && (!h_points || !h_polys || !h_out))) return AGJ_EINVAL;
     const agj::Index& X = index->X;
     for (uint64_t k = 0; k < n; ++k) {
-        const uint32_t poly = h_polys[k];
-        if (poly >= X.n_polys) return AGJ_EINVAL;
+        if (h_polys[k] >= X.n_input_polys) return AGJ_EINVAL;
+        // the polygon's piece on the point's face (one piece: the polygon)
+        uint32_t poly = h_polys[k];
+        if (!X.piece_poly.empty()) {
+            double u, v;
+            const int f = agj::point_valid(h_points[2 * k], h_points[2 * k + 1])
+                              ? agj::face_uv(h_points[2 * k], h_points[2 * k + 1], &u, &v) : -1;
+            poly = 0xFFFFFFFFu;
+            for (uint32_t q = 0; q < X.n_polys; ++q)
+                if (X.piece_poly[q] == h_polys[k] && X.poly_face[q] == f) poly = q;
+            if (poly == 0xFFFFFFFFu) { h_out[k] = 0; continue; }
+        }
         const agj::PolyLocal& L = X.poly_local[poly];
         const uint32_t v0 = X.poly_off[poly], V = X.poly_off[poly + 1] - v0;
         float pu, pv, dp;

@@ -36,9 +36,11 @@ struct DevIndex {
     const uint16_t* poly_band;    // certified refine: per-polygon band tables
     const uint32_t* ring_off;     // n_polys + 1: each polygon's entries in ring_end (none: one ring)
     const uint32_t* ring_end;     // ends of a polygon with holes' rings (explicitly closed), relative to poly_off
+    const uint32_t* piece_poly;   // input polygon of each piece (null: piece k = polygon k)
     uint64_t n_nodes;
     uint64_t n_lut;
-    uint32_t n_polys;
+    uint32_t n_polys;           // pieces (the polygons of the references and the refine)
+    uint32_t n_out_polys;       // input polygons (the ids of joins and counts)
     uint32_t max_depth;
     uint32_t contains;          // 1: the refine test excludes the boundary (ST_Contains)
     DevFace faces[6];
@@ -93,6 +95,11 @@ __device__ __forceinline__ uint64_t walk_exact(const DevIndex& X, const DevFace*
     }
     atomicOr((unsigned long long*)err, kErrTrieBounds);
     return 0;
+}
+
+// The polygon id a join reports for a piece reference.
+__device__ __forceinline__ uint32_t out_poly(const DevIndex& X, uint32_t piece) {
+    return X.piece_poly ? __ldg(X.piece_poly + piece) : piece;
 }
 
 // Number of references (true + candidate) an entry holds.

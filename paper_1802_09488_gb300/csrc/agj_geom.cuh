@@ -137,6 +137,33 @@ AGJ_HD int face_uv(double lat, double lng, double* u, double* v) {
     return face;
 }
 
+// The unit vector of a point, as face_uv computes it.
+AGJ_HD void latlng_xyz(double lat, double lng, double p[3]) {
+    double sp, cp, sl, cl;
+    sincos_deg(lat, &sp, &cp);
+    sincos_deg(lng, &sl, &cl);
+    p[0] = cp * cl;
+    p[1] = cp * sl;
+    p[2] = sp;
+}
+
+// (u,v) of a unit vector on the plane of `face` (the face's gnomonic
+// coordinates, also beyond its square), with face_uv's expressions, so a
+// point on that face gets exactly face_uv's (u,v).  False when the point is
+// not in the face's open hemisphere.
+AGJ_HD bool xyz_uv_on_face(int face, const double p[3], double* u, double* v) {
+    const double x = p[0], y = p[1], z = p[2];
+    switch (face) {
+        case 0: if (!(x > 0.0)) return false; *u = y / x; *v = z / x; break;
+        case 1: if (!(y > 0.0)) return false; *u = -x / y; *v = z / y; break;
+        case 2: if (!(z > 0.0)) return false; *u = -x / z; *v = -y / z; break;
+        case 3: if (!(x < 0.0)) return false; *u = z / x; *v = y / x; break;
+        case 4: if (!(y < 0.0)) return false; *u = z / y; *v = -x / y; break;
+        default: if (!(z < 0.0)) return false; *u = -y / z; *v = -x / z; break;
+    }
+    return true;
+}
+
 AGJ_HD double uv_to_st(double u) {
     if (u >= 0.0) return 0.5 * geom_sqrt(1.0 + 3.0 * u);
     return 1.0 - 0.5 * geom_sqrt(1.0 - 3.0 * u);

@@ -48,7 +48,14 @@ void poly_edges(const Index& X, uint32_t k, std::vector<uint32_t>* out);
 
 struct Index {
     agj_mode mode = AGJ_APPROX;
-    uint32_t n_polys = 0;
+    // The index's polygons are pieces: one per cube face an input polygon
+    // reaches (most polygons are one piece).  References, geometry and the
+    // refine run on pieces; joins and counts report input polygon ids
+    // (piece_poly maps them; empty when every polygon is one piece, piece k
+    // = polygon k).
+    uint32_t n_polys = 0;             // pieces
+    uint32_t n_input_polys = 0;       // polygons given to agj_build
+    std::vector<uint32_t> piece_poly; // input polygon of each piece (ascending), or empty
     bool contains = false;      // exact join by ST_Contains (boundary points excluded) instead of ST_Covers
     double precision_m = 0;
     // logical index (super covering)
@@ -80,7 +87,7 @@ struct Index {
     void* d_blob = nullptr;
     uint64_t blob_bytes = 0;
     uint64_t off_nodes = 0, off_lut = 0, off_uv = 0, off_vkey = 0, off_ukey = 0, off_poff = 0, off_bbox = 0,
-             off_face = 0, off_plocal = 0, off_pluv = 0, off_pband = 0, off_roff = 0, off_rend = 0;
+             off_face = 0, off_plocal = 0, off_pluv = 0, off_pband = 0, off_roff = 0, off_rend = 0, off_ppoly = 0;
     int device = 0;
 };
 

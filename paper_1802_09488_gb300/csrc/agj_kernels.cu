@@ -336,7 +336,7 @@ __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces,
             uint32_t poly = kNoPoly;
             if (tag == 1 || tag == 2) {
                 const uint32_t pl = payload_of(e[k], 0);
-                if (pl != kInvalidPayloadDev && (!exact || (pl & 1u))) poly = pl >> 1;
+                if (pl != kInvalidPayloadDev && (!exact || (pl & 1u))) poly = out_poly(J.X, pl >> 1);
             }
             agg_add_warp(poly, s_hist, counts);
         }
@@ -344,7 +344,7 @@ __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces,
             uint32_t poly = kNoPoly;
             if (tag == 2) {
                 const uint32_t pl = payload_of(e[k], 1);
-                if (!exact || (pl & 1u)) poly = pl >> 1;
+                if (!exact || (pl & 1u)) poly = out_poly(J.X, pl >> 1);
             }
             agg_add_warp(poly, s_hist, counts);
         }
@@ -352,10 +352,11 @@ __device__ __forceinline__ void agg_tile(const JobDesc& J, const DevFace* faces,
         if (tag == 3) {
             const uint32_t off = payload_of(e[k], 0);
             const uint32_t nt3 = __ldg(J.X.lut + off);
-            for (uint32_t t = 0; t < nt3; ++t) agg_add_lane(__ldg(J.X.lut + off + 1 + t), s_hist, counts);
+            for (uint32_t t = 0; t < nt3; ++t) agg_add_lane(out_poly(J.X, __ldg(J.X.lut + off + 1 + t)), s_hist, counts);
             if (!exact) {
                 const uint32_t nc3 = __ldg(J.X.lut + off + 1 + nt3);
-                for (uint32_t t = 0; t < nc3; ++t) agg_add_lane(__ldg(J.X.lut + off + 2 + nt3 + t), s_hist, counts);
+                for (uint32_t t = 0; t < nc3; ++t)
+                    agg_add_lane(out_poly(J.X, __ldg(J.X.lut + off + 2 + nt3 + t)), s_hist, counts);
             }
         }
     }
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
     const bool smem = stripes != nullptr;
     const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
     if (smem)
-        for (uint32_t p = threadIdx.x; p < J.X.n_polys; p += blockDim.x) s_hist[p] = 0;
+        for (uint32_t p = threadIdx.x; p < J.X.n_out_polys; p += blockDim.x) s_hist[p] = 0;
     if (threadIdx.x < 4) s_tot[threadIdx.x] = 0;
     cp_async_wait_all();
     __syncthreads();
@@ -407,8 +408,8 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
         if (s_tot[3]) atomicAdd((unsigned long long*)&J.status[2], (unsigned long long)s_tot[3]);
     }
     if (smem) {
-        uint32_t* stripe = stripes + (uint64_t)(blockIdx.x % kAggStripes) * J.X.n_polys;
-        for (uint32_t p = threadIdx.x; p < J.X.n_polys; p += blockDim.x)
+        uint32_t* stripe = stripes + (uint64_t)(blockIdx.x % kAggStripes) * J.X.n_out_polys;
+        for (uint32_t p = threadIdx.x; p < J.X.n_out_polys; p += blockDim.x)
             if (s_hist[p]) atomicAdd(&stripe[p], s_hist[p]);
     }
 }
@@ -607,9 +608,11 @@ DevIndex make_dev_index(const Index& X) {
     D.poly_band = reinterpret_cast<const uint16_t*>(b + X.off_pband);
     D.ring_off = reinterpret_cast<const uint32_t*>(b + X.off_roff);
     D.ring_end = reinterpret_cast<const uint32_t*>(b + X.off_rend);
+    D.piece_poly = X.piece_poly.empty() ? nullptr : reinterpret_cast<const uint32_t*>(b + X.off_ppoly);
     D.n_nodes = X.nodes.size() / 256;
     D.n_lut = X.lut.size();
     D.n_polys = X.n_polys;
+    D.n_out_polys = X.n_input_polys;
     D.max_depth = X.stats.max_depth;
     D.contains = X.contains ? 1u : 0u;
     for (int f = 0; f < 6; ++f) D.faces[f] = dev_face(f, X.faces[f]);
@@ -621,7 +624,7 @@ namespace {
 
 // Byte offsets of the sections of an index's device blob (256-byte aligned).
 struct BlobLayout {
-    uint64_t nodes, lut, uv, vkey, ukey, poff, bbox, face, plocal, pluv, pband, roff, rend, total;
+    uint64_t nodes, lut, uv, vkey, ukey, poff, bbox, face, plocal, pluv, pband, roff, rend, ppoly, total;
 };
 
 BlobLayout blob_layout(const Index& X) {
@@ -641,6 +644,7 @@ BlobLayout blob_layout(const Index& X) {
     B.pband = o; o += align256(X.poly_band.size() * 2 + 16);
     B.roff = o; o += align256(X.ring_off.size() * 4 + 4);
     B.rend = o; o += align256(X.ring_end.size() * 4 + 4);
+    B.ppoly = o; o += align256(X.piece_poly.size() * 4 + 4);
     B.total = o;
     return B;
 }
@@ -655,6 +659,7 @@ int upload_index(Index* X, cudaStream_t s) {
     X->off_nodes = B.nodes; X->off_lut = B.lut; X->off_uv = B.uv; X->off_vkey = B.vkey; X->off_ukey = B.ukey;
     X->off_poff = B.poff; X->off_bbox = B.bbox; X->off_face = B.face; X->off_plocal = B.plocal;
     X->off_pluv = B.pluv; X->off_pband = B.pband; X->off_roff = B.roff; X->off_rend = B.rend;
+    X->off_ppoly = B.ppoly;
     const uint64_t o = B.total;
     X->blob_bytes = o;
     std::vector<unsigned char> host(o, 0);
@@ -680,6 +685,7 @@ int upload_index(Index* X, cudaStream_t s) {
     put(X->off_pband, X->poly_band.data(), X->poly_band.size() * 2);
     put(X->off_roff, X->ring_off.data(), X->ring_off.size() * 4);
     put(X->off_rend, X->ring_end.data(), X->ring_end.size() * 4);
+    put(X->off_ppoly, X->piece_poly.data(), X->piece_poly.size() * 4);
     if (cudaMalloc(&X->d_blob, o) != cudaSuccess) { cudaGetLastError(); X->d_blob = nullptr; return AGJ_ENOMEM; }
     if (cudaMemcpyAsync(X->d_blob, host.data(), o, cudaMemcpyHostToDevice, s) != cudaSuccess) return AGJ_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return AGJ_ECUDA;
@@ -769,7 +775,7 @@ JoinLayout count_layout(const Index& X, uint64_t n) {
     const bool exact = X.mode == AGJ_EXACT;
     return join_layout(tiles * 32 * kJoinPPT, tiles, exact,
                        exact ? 32u * kJoinPPT * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
-                       exact ? X.n_polys : 0, true, X.n_polys <= kAggSmemPolys ? X.n_polys : 0);
+                       exact ? X.n_polys : 0, true, X.n_input_polys <= kAggSmemPolys ? X.n_input_polys : 0);
 }
 
 }  // namespace
@@ -779,7 +785,7 @@ uint64_t count_scratch_bytes(const Index& X, uint64_t n) { return count_layout(X
 int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaStream_t s, uint64_t* d_counts,
                       uint64_t* d_status, void* scratch, uint64_t scratch_bytes, bool accumulate,
                       cudaEvent_t const* events) {
-    if (!d_status || (X.n_polys && !d_counts) || (n && !d_points) || !scratch) return AGJ_EINVAL;
+    if (!d_status || (X.n_input_polys && !d_counts) || (n && !d_points) || !scratch) return AGJ_EINVAL;
     if (n >= 0xFFFFFFFFull) return AGJ_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0 || (reinterpret_cast<uintptr_t>(scratch) & 255u) != 0)
         return AGJ_EINVAL;
@@ -796,7 +802,7 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
     // zero the header, scan states and per-polygon candidate counts, the
     // status words and (unless accumulating) the counts
     {
-        const uint64_t zw = L.zero_end / 8, cw = accumulate ? 0 : X.n_polys;
+        const uint64_t zw = L.zero_end / 8, cw = accumulate ? 0 : X.n_input_polys;
         const int grid = (int)std::min<uint64_t>((zw + cw + 4 + 255) / 256 + 1, (uint64_t)sms * 4);
         k_zero<<<grid, 256, 0, s>>>(reinterpret_cast<uint64_t*>(sc), zw, d_status, 4);
         if (cw) k_zero<<<grid, 256, 0, s>>>(d_counts, cw, nullptr, 0);
@@ -813,7 +819,7 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
         if (exact) k_agg_probe<kJoinPPT, kModeExact><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
         else k_agg_probe<kJoinPPT, kModeApprox><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
         if (stripes)
-            k_agg_reduce<<<(X.n_polys + 255) / 256, 256, 0, s>>>(stripes, X.n_polys, d_counts);
+            k_agg_reduce<<<(X.n_input_polys + 255) / 256, 256, 0, s>>>(stripes, X.n_input_polys, d_counts);
     }
     mark(1);
     if (exact && L.n_tiles && L.n_polys) {

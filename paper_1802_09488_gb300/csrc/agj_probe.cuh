@@ -523,10 +523,10 @@ __device__ __forceinline__ uint32_t payload_of(uint64_t e, int which) {
 __device__ __forceinline__ void emit_all(const DevIndex& X, uint64_t e, uint32_t* ids, uint64_t o) {
     const uint32_t tag = (uint32_t)(e & 3ull);
     if (tag == 1) {
-        ids[o] = payload_of(e, 0) >> 1;
+        ids[o] = out_poly(X, payload_of(e, 0) >> 1);
     } else if (tag == 2) {
-        ids[o] = payload_of(e, 0) >> 1;
-        ids[o + 1] = payload_of(e, 1) >> 1;
+        ids[o] = out_poly(X, payload_of(e, 0) >> 1);
+        ids[o + 1] = out_poly(X, payload_of(e, 1) >> 1);
     } else if (tag == 3) {
         const uint32_t off = payload_of(e, 0);
         const uint32_t nt = __ldg(X.lut + off);
@@ -537,8 +537,8 @@ __device__ __forceinline__ void emit_all(const DevIndex& X, uint64_t e, uint32_t
         while (a < nt || b < nc) {
             const uint32_t ta = a < nt ? __ldg(T + a) : 0xFFFFFFFFu;
             const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
-            if (ta < cb) { ids[o++] = ta; ++a; }
-            else { ids[o++] = cb; ++b; }
+            if (ta < cb) { ids[o++] = out_poly(X, ta); ++a; }
+            else { ids[o++] = out_poly(X, cb); ++b; }
         }
     }
 }
@@ -998,7 +998,7 @@ __global__ void __launch_bounds__(kPipBlock, AGJ_PIP_MIN_BLOCKS) k_pip(const Src
         if constexpr (kCount) {
             const int passed = __syncthreads_count(r);
             if (threadIdx.x == 0 && passed) {
-                atomicAdd((unsigned long long*)&counts[poly], (unsigned long long)passed);
+                atomicAdd((unsigned long long*)&counts[out_poly(JP.X, poly)], (unsigned long long)passed);
                 atomicAdd((unsigned long long*)&JP.status[0], (unsigned long long)passed);
             }
         }
@@ -1127,13 +1127,13 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
             const uint32_t p0 = payload_of(ek, 0), p1 = payload_of(ek, 1);
             const bool keep0 = (p0 & 1u) || (ps & 1u);
             const bool keep1 = tag == 2 && ((p1 & 1u) || ((ps >> ((p0 & 1u) ? 0 : 1)) & 1u));
-            if (keep0) J.ids[w] = p0 >> 1;
-            if (keep1) J.ids[w + (keep0 ? 1 : 0)] = p1 >> 1;
+            if (keep0) J.ids[w] = out_poly(J.X, p0 >> 1);
+            if (keep1) J.ids[w + (keep0 ? 1 : 0)] = out_poly(J.X, p1 >> 1);
         } else if (tag == 1 || tag == 2) {
             for (int t = 0; t < (int)tag; ++t) {
                 const uint32_t pl = payload_of(ek, t);
-                if (pl & 1u) J.ids[w++] = pl >> 1;
-                else if (pd[ci++]) J.ids[w++] = pl >> 1;
+                if (pl & 1u) J.ids[w++] = out_poly(J.X, pl >> 1);
+                else if (pd[ci++]) J.ids[w++] = out_poly(J.X, pl >> 1);
             }
         } else if (tag == 3) {
             const uint32_t off = payload_of(ek, 0);
@@ -1145,8 +1145,8 @@ __device__ __forceinline__ void emit_tile(const Src& src, uint32_t j, uint64_t w
             while (a < nt || b < nc) {
                 const uint32_t ta = a < nt ? __ldg(Tt + a) : 0xFFFFFFFFu;
                 const uint32_t cb = b < nc ? __ldg(Cc + b) : 0xFFFFFFFFu;
-                if (ta < cb) { J.ids[w++] = ta; ++a; }
-                else { if (direct ? pd[b] : (ps >> b) & 1u) J.ids[w++] = cb; ++b; }
+                if (ta < cb) { J.ids[w++] = out_poly(J.X, ta); ++a; }
+                else { if (direct ? pd[b] : (ps >> b) & 1u) J.ids[w++] = out_poly(J.X, cb); ++b; }
             }
         }
     }

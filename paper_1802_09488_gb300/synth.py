@@ -484,3 +484,20 @@ def with_holes(polys: list, seed: int, frac: float = 0.35, max_holes: int = 3, v
 def c2_city_holes_polygons() -> list:
     """The city polygons, a third of them with one to three holes (seed 8)."""
     return with_holes(c2_city_polygons(), seed=8)
+
+
+# ---------------------------------------------------------------------------
+# polygons across cube faces
+# ---------------------------------------------------------------------------
+
+# A 40 km box centred on the cube edge between faces 0 (+x) and 1 (+y) at
+# the equator, and one on the corner of faces 0, 1 and 2 (lat 35.26, lng 45).
+BOX_EDGE = Box(40.0, 40.0, lat0=0.0, lng0=45.0)
+BOX_CORNER = Box(40.0, 40.0, lat0=35.2643896827547, lng0=45.0)
+
+
+def crossface_tiling(box: Box, n_polys: int = 40, seed: int = 12) -> list:
+    """A Voronoi tiling (8-64 vertices per polygon) of a box that straddles
+    cube faces: the polygons across the face boundaries span two or three
+    faces."""
+    return voronoi_tiling(n_polys, box, seed=seed, vmin=8, vmax=64)

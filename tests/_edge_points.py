@@ -80,3 +80,31 @@ def check_approx_property(oracle, ps, cells, off, refs, points, eps_m):
         assert 0.0 <= d <= eps_m * (1 + 1e-9), (p, q, d)
         worst = max(worst, d)
     return len(ekey), len(extra), worst
+
+
+def edge_points_3d(polys, offsets_m=(0.0, 1e-6, -1e-6), ts=(0.5, 0.25), stride=1):
+    """Like edge_points for polygons that may span cube faces: points on each
+    geodesic edge (normalised chords between the vertices' unit vectors) and
+    moved by offsets_m metres along the edge's great-circle normal, plus
+    every vertex.  (lat, lng) rows."""
+    R = 6371008.8
+    out = []
+    for P in polys:
+        P = np.asarray(P, dtype=np.float64)
+        la, lo = np.radians(P[:, 0]), np.radians(P[:, 1])
+        xyz = np.stack([np.cos(la) * np.cos(lo), np.cos(la) * np.sin(lo), np.sin(la)], -1)
+        out.append(P)
+        for k in range(0, len(P), stride):
+            a, b = xyz[k], xyz[(k + 1) % len(P)]
+            n = np.cross(a, b)
+            if np.linalg.norm(n) == 0.0:
+                continue
+            n /= np.linalg.norm(n)
+            for t in ts:
+                p = (1 - t) * a + t * b
+                p /= np.linalg.norm(p)
+                for off in offsets_m:
+                    q = p + n * (off / R)
+                    q /= np.linalg.norm(q)
+                    out.append(np.array([[np.degrees(np.arcsin(q[2])), np.degrees(np.arctan2(q[1], q[0]))]]))
+    return np.concatenate(out)

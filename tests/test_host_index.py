@@ -225,8 +225,10 @@ def test_build_rejects_bad_polygons(agj):
     with pytest.raises(agj.AgjError) as e:
         agj.Index([np.array([[40.0, -74.0], [40.1, -74.0]])], agj.APPROX, 10.0, host_only=True)
     assert e.value.status == 1
+    # a polygon across cube faces is supported within 15 degrees of its
+    # vertices' mean (tests/test_host_crossface.py); a wider one is refused
     with pytest.raises(agj.AgjError) as e:
-        agj.Index([np.array([[0.0, 44.0], [1.0, 46.0], [-1.0, 46.0]])], agj.APPROX, 10.0, host_only=True)
+        agj.Index([np.array([[0.0, 30.0], [20.0, 45.0], [-20.0, 60.0]])], agj.APPROX, 10.0, host_only=True)
     assert e.value.status == 2
     with pytest.raises(agj.AgjError) as e:
         agj.Index([np.array([[40.0, -74.0], [40.1, -74.0], [np.nan, -74.1]])], agj.APPROX, 10.0, host_only=True)
