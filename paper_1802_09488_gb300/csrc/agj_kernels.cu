@@ -439,16 +439,16 @@ __global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
     __shared__ DevFace s_faces[6];
-    __shared__ uint4 s_tail[kWarpsPerBlock][32 * kJoinPPT];
+    __shared__ uint4 s_tail[kWarpsPerBlock][32 * kJoinSmallPPT];
     const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const bool active = wt < T;
-    const uint64_t base = wt * (32 * kJoinPPT);
-    PointIJ pij[kJoinPPT];
-    bool ok[kJoinPPT];
+    const uint64_t base = wt * (32 * kJoinSmallPPT);
+    PointIJ pij[kJoinSmallPPT];
+    bool ok[kJoinSmallPPT];
 #pragma unroll
-    for (int k = 0; k < kJoinPPT; ++k) {
+    for (int k = 0; k < kJoinSmallPPT; ++k) {
         const uint64_t p = base + lane + 32 * k;
         ok[k] = false;
         if (active && p < J.n) {
@@ -459,12 +459,12 @@ __global__ void __launch_bounds__(kJoinBlock, AGJ_PROBE_MIN_BLOCKS)
     cp_async_wait_all();
     __syncthreads();
     if (!active) return;
-    uint64_t e[kJoinPPT];
+    uint64_t e[kJoinSmallPPT];
     uint32_t fallbacks = 0;
-    probe_cells<kJoinPPT>(J.X, s_faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], &fallbacks,
+    probe_cells<kJoinSmallPPT>(J.X, s_faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e, &J.status[1], &fallbacks,
                           s_tail[threadIdx.x >> 5]);
 #pragma unroll
-    for (int k = 0; k < kJoinPPT; ++k) {
+    for (int k = 0; k < kJoinSmallPPT; ++k) {
         uint32_t nt, nc;
         entry_counts(J.X, e[k], &nt, &nc);
         const uint32_t mask = __ballot_sync(kFull, nc > 0);
@@ -696,19 +696,27 @@ int upload_index(Index* X, cudaStream_t s) {
 
 namespace {
 
-JoinLayout plain_layout(const Index& X, uint64_t n) {
-    const uint64_t tiles = (n + 32 * kJoinPPT - 1) / (32 * kJoinPPT);
+int plain_ppt(uint64_t n) { return n >= kJoinWidePoints ? kJoinPPT : kJoinSmallPPT; }
+
+JoinLayout plain_layout(const Index& X, uint64_t n, int ppt) {
+    const uint64_t tiles = (n + 32 * ppt - 1) / (32 * ppt);
     const bool exact = X.mode == AGJ_EXACT;
-    return join_layout(tiles * 32 * kJoinPPT, tiles, exact,
-                       exact ? 32u * kJoinPPT * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
+    return join_layout(tiles * 32 * ppt, tiles, exact,
+                       exact ? 32u * ppt * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
                        exact ? X.n_polys : 0);
 }
 
 }  // namespace
 
+// The work space stated for n points serves every join of at most n points:
+// the larger of the layout n itself takes and the largest one a narrow
+// (small-join) layout of fewer points takes.
 int join_requirements(const Index& X, uint64_t n, agj_requirements* r) {
     r->ids_capacity = n * std::max<uint64_t>(X.stats.max_refs, 1);
-    r->scratch_bytes = plain_layout(X, n).total;
+    r->scratch_bytes = plain_layout(X, n, plain_ppt(n)).total;
+    if (n >= kJoinWidePoints)
+        r->scratch_bytes =
+            std::max(r->scratch_bytes, plain_layout(X, kJoinWidePoints - 1, kJoinSmallPPT).total);
     return AGJ_OK;
 }
 
@@ -739,7 +747,8 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
     if (!out || !out->offsets || !out->status || (n && !d_points)) return AGJ_EINVAL;
     if (n >= 0xFFFFFFFFull) return AGJ_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_points) & 15u) != 0) return AGJ_EINVAL;
-    const JoinLayout L = plain_layout(X, n);
+    const int ppt = plain_ppt(n);
+    const JoinLayout L = plain_layout(X, n, ppt);
     agj_requirements req;
     join_requirements(X, n, &req);
     if (req.ids_capacity >= 0xFFFFFFFFull || L.queue_cap >= 0xFFFFFFFFull) return AGJ_ECAPACITY;   // 32-bit offsets
@@ -763,18 +772,20 @@ int launch_join(const Index& X, const double* d_points, uint64_t n, cudaStream_t
     G.pip_grid = G.sms * AGJ_PIP_MIN_BLOCKS;
     const cudaError_t e =
         X.mode == AGJ_APPROX
-            ? enqueue_join<kJoinPPT, OneJob, kModeApprox>(src, L, sc, G, out->status, 4, s, events)
-            : enqueue_join<kJoinPPT, OneJob, kModeExact>(src, L, sc, G, out->status, 4, s, events);
+            ? (ppt == kJoinPPT ? enqueue_join<kJoinPPT, OneJob, kModeApprox>(src, L, sc, G, out->status, 4, s, events)
+                               : enqueue_join<kJoinSmallPPT, OneJob, kModeApprox>(src, L, sc, G, out->status, 4, s, events))
+            : (ppt == kJoinPPT ? enqueue_join<kJoinPPT, OneJob, kModeExact>(src, L, sc, G, out->status, 4, s, events)
+                               : enqueue_join<kJoinSmallPPT, OneJob, kModeExact>(src, L, sc, G, out->status, 4, s, events));
     return e == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
 }
 
 namespace {
 
 JoinLayout count_layout(const Index& X, uint64_t n) {
-    const uint64_t tiles = (n + 32 * kJoinPPT - 1) / (32 * kJoinPPT);
+    const uint64_t tiles = (n + 32 * kJoinSmallPPT - 1) / (32 * kJoinSmallPPT);
     const bool exact = X.mode == AGJ_EXACT;
-    return join_layout(tiles * 32 * kJoinPPT, tiles, exact,
-                       exact ? 32u * kJoinPPT * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
+    return join_layout(tiles * 32 * kJoinSmallPPT, tiles, exact,
+                       exact ? 32u * kJoinSmallPPT * std::max<uint32_t>(X.stats.max_cand_refs, 1) : 0u,
                        exact ? X.n_polys : 0, true, X.n_input_polys <= kAggSmemPolys ? X.n_input_polys : 0);
 }
 
@@ -816,8 +827,8 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
     uint32_t* stripes = L.stripes ? reinterpret_cast<uint32_t*>(sc + L.stripes) : nullptr;
     if (L.n_tiles) {
         const int grid = (int)((L.n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        if (exact) k_agg_probe<kJoinPPT, kModeExact><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
-        else k_agg_probe<kJoinPPT, kModeApprox><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
+        if (exact) k_agg_probe<kJoinSmallPPT, kModeExact><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
+        else k_agg_probe<kJoinSmallPPT, kModeApprox><<<grid, kJoinBlock, 0, s>>>(J, L.n_tiles, S, d_counts, stripes);
         if (stripes)
             k_agg_reduce<<<(X.n_input_polys + 255) / 256, 256, 0, s>>>(stripes, X.n_input_polys, d_counts);
     }
@@ -836,7 +847,7 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
                                           reinterpret_cast<uint32_t*>(sc + L.cursor),
                                           reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
         k_pip<OneJob, true><<<sms * AGJ_PIP_MIN_BLOCKS, kPipBlock, 0, s>>>(
-            src, 32 * kJoinPPT, reinterpret_cast<const uint2*>(sc + L.sorted), reinterpret_cast<const uint4*>(sc + L.cpoly),
+            src, 32 * kJoinSmallPPT, reinterpret_cast<const uint2*>(sc + L.sorted), reinterpret_cast<const uint4*>(sc + L.cpoly),
             hdr + 2, nullptr, nullptr, d_counts);
         // the polygon scan's wait status goes to the join's error word
         k_merge_err<<<1, 32, 0, s>>>(reinterpret_cast<const uint64_t*>(sc) + kHdrScanErr, d_status + 1);
@@ -849,7 +860,7 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
 int launch_collect_expensive(const Index& X, const double* d_points, uint64_t n, uint64_t* d_out,
                              uint64_t* d_count, uint64_t* d_status, cudaStream_t s) {
     if (n == 0) return AGJ_OK;
-    const uint64_t tiles = (n + 32 * kJoinPPT - 1) / (32 * kJoinPPT);
+    const uint64_t tiles = (n + 32 * kJoinSmallPPT - 1) / (32 * kJoinSmallPPT);
     agj_pairs none;
     memset(&none, 0, sizeof none);
     none.status = d_status;

@@ -36,9 +36,15 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 // trie gathers), so more resident warps pay while the registers last: at 5
 // CTAs (40 warps, 48 registers) the probes, single-job and batched, need no
 // spills and beat 4 CTAs on the city workload; at 6 (40 registers) the walk
-// spills.
+// spills.  A plain join of kJoinWidePoints points or more runs 4 points per
+// lane: its approximate probe at 4 CTAs (64 registers, 32 warps = 4096
+// walks per SM), its exact probe at 5 (48 registers; a few spilled bytes
+// cost less than the lost warps).
 #ifndef AGJ_PROBE_MIN_BLOCKS
 #define AGJ_PROBE_MIN_BLOCKS 5
+#endif
+#ifndef AGJ_JOIN_APPROX_PROBE_MIN_BLOCKS
+#define AGJ_JOIN_APPROX_PROBE_MIN_BLOCKS 4
 #endif
 #ifndef AGJ_BATCH_PROBE_MIN_BLOCKS
 #define AGJ_BATCH_PROBE_MIN_BLOCKS 5
@@ -52,7 +58,16 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 #define AGJ_PREFETCH_AHEAD 1
 #endif
 constexpr int kJoinBlock = 256;
-constexpr int kJoinPPT = 2;                    // points per lane of the plain join
+// Points per lane.  A wide plain join (kJoinWidePoints and more) takes 4:
+// fewer tiles, more walks in flight per warp.  A smaller join takes 2, which
+// spreads its few points over twice the warps (below a few resident waves
+// the probe's time is the slowest warp's walk, 11.0 against 13.8 us per
+// 1e5-point join); so do the count(*) aggregation, whose per-point
+// histogram work makes the wider tile slower (58.0 against 51.6 G points/s
+// on the city workload), and the training pass.
+constexpr int kJoinPPT = 4;
+constexpr int kJoinSmallPPT = 2;
+constexpr uint64_t kJoinWidePoints = 1ull << 21;
 constexpr int kWarpsPerBlock = kJoinBlock / 32;
 constexpr int kPipBlock = 256;
 constexpr int kPipSmemVerts = 2048;            // vertices staged per CTA (8 B each)
@@ -821,10 +836,16 @@ __device__ __forceinline__ const uint64_t* cta_stage_job(const JobDesc& J, DevFa
 // changes; the grid either covers the tile space (one warp per tile) or, with
 // kPersist, is persistent and strides over it (separate instances, so the
 // one-warp-per-tile form carries no loop state).
+// Resident CTAs per SM a probe instance is compiled for.
+template <int PPT, class Src, int MODE>
+constexpr int probe_min_blocks() {
+    return MODE == kModeApprox ? (Src::kSingle && PPT >= 4 ? AGJ_JOIN_APPROX_PROBE_MIN_BLOCKS : AGJ_APPROX_PROBE_MIN_BLOCKS)
+           : !Src::kSingle     ? AGJ_BATCH_PROBE_MIN_BLOCKS
+                               : AGJ_PROBE_MIN_BLOCKS;
+}
+
 template <int PPT, class Src, int MODE, bool kPersist = false>
-__global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_PROBE_MIN_BLOCKS
-                                             : !Src::kSingle          ? AGJ_BATCH_PROBE_MIN_BLOCKS
-                                                                      : AGJ_PROBE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kJoinBlock, probe_min_blocks<PPT, Src, MODE>())
     k_probe(const Src src, uint64_t T, const JoinScratch S) {
     __shared__ __align__(16) uint16_t s_hlut[1024];
     __shared__ __align__(16) uint64_t s_rootbuf[256];
@@ -841,7 +862,7 @@ __global__ void __launch_bounds__(kJoinBlock, MODE == kModeApprox ? AGJ_APPROX_P
             uint32_t nsm;
             asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
             const uint64_t group_pts = (uint64_t)kWarpsPerBlock * 32 * PPT;
-            const uint64_t ahead = (uint64_t)nsm * (MODE == kModeApprox ? AGJ_APPROX_PROBE_MIN_BLOCKS : AGJ_PROBE_MIN_BLOCKS);
+            const uint64_t ahead = (uint64_t)nsm * probe_min_blocks<PPT, Src, MODE>();
             if (AGJ_PREFETCH_AHEAD) prefetch_points_l2(src.job(0).pts, src.job(0).n, (blockIdx.x + ahead) * group_pts, group_pts);
         }
         const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;

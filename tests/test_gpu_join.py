@@ -130,6 +130,28 @@ def test_pairs_reuse_and_capacity_errors(torch, agj, c1):
     assert e.value.status == 8
 
 
+def test_tile_width_switch_and_scratch_reuse(torch, agj, oracle):
+    """A plain join of 2**21 points or more runs 4 points per lane, a smaller
+    one 2; work space sized for the wider join serves both, and both match
+    the oracle row for row on either side of the switch."""
+    from paper_1802_09488_gb300 import synth
+    wide = (1 << 21) + 300
+    w = synth.c1_tiny(wide)
+    pts = _dev(torch, w.points)
+    for mode in (agj.APPROX, agj.EXACT):
+        ix = agj.Index(w.polygons, mode, w.eps_m)
+        pr = agj.Pairs(ix, wide)
+        if mode == agj.APPROX:
+            cells, ro, refs = ix.logical()
+            eo, ei = oracle.join_approx_logical(cells, ro, refs, w.points)
+        else:
+            eo, ei = oracle.PolySet(w.polygons).join_exact(w.points)
+        for n in (wide, (1 << 21) - 1, 70_000):
+            off, ids = agj.join(ix, pts[:n], pr).to_host()
+            assert len(off) == n + 1
+            _csr_equal(off, ids, eo[:n + 1], ei[:int(eo[n])])
+
+
 @pytest.fixture(scope="module")
 def city_small():
     from paper_1802_09488_gb300 import synth
