@@ -41,8 +41,8 @@ LAUNCHES_PER_STEP = {"approx": 4, "exact": 8}
 # launch's traffic scales with its points (the trie gathers per point do not
 # depend on n).  Re-captured whenever a probe kernel changes (empty: the
 # kernels changed since the last capture, traffic reported as null).
-PROBE_DRAM_BYTES_PER_POINT = {"k_probe_approx": (320.4e6 + 89.7e6) / 16e6,
-                              "k_probe_exact": (311.0e6 + 105.6e6) / 16e6}
+PROBE_DRAM_BYTES_PER_POINT = {"k_probe_approx": (320.0e6 + 89.2e6) / 16e6,
+                              "k_probe_exact": (312.9e6 + 106.0e6) / 16e6}
 
 
 def parse():

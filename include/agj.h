@@ -265,9 +265,10 @@ int agj_pairs_free(agj_pairs* pairs, void* stream);
  * reaches that point.  n == 0 writes offsets[0] = 0.  n must be < 2^32.
  * Errors (returned immediately): AGJ_EINVAL, AGJ_ECAPACITY (buffers too
  * small for n), AGJ_ECUDA (launch failed).  Device-side conditions are
- * reported in out->status[1] (bit 0 ids capacity exceeded, bit 1 scan wait
- * timed out, bit 2 trie bounds check, bit 3 candidate queue overflow) and
- * by agj_join_check.
+ * reported in out->status[1] (bit 0 ids capacity exceeded, bit 1 a device
+ * wait timed out: the scan's look-back or a probe block's wait for its
+ * shared tables, bit 2 trie bounds check, bit 3 candidate queue overflow)
+ * and by agj_join_check.
  */
 int agj_join(const agj_index* index, const double* d_points, uint64_t n, void* stream, agj_pairs* out);
 

@@ -54,6 +54,11 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 #endif
 // Each CTA of the plain join's probe prefetches into the L2 the points of
 // the CTA one grid of resident CTAs ahead (1) or not (0).
+// The plain join's probe waits for its CTA's shared tables on a
+// tables-ready mbarrier (1) or on a CTA barrier after the cell ids (0).
+#ifndef AGJ_PROBE_READY_BARRIER
+#define AGJ_PROBE_READY_BARRIER 1
+#endif
 #ifndef AGJ_PREFETCH_AHEAD
 #define AGJ_PREFETCH_AHEAD 1
 #endif
@@ -502,6 +507,45 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
+// A CTA's "tables ready" barrier (an mbarrier in shared memory, phase 0):
+// every thread's cp.async copies arrive on it when they land (noinc: the
+// expected count includes them), and the threads that store the face table
+// arrive after their stores.  A warp that waits on it waits for the copies
+// only, not for the CTA's other warps, as a CTA barrier would.
+constexpr uint32_t kReadyArrivals = kJoinBlock + 6;
+__device__ __forceinline__ void ready_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(kReadyArrivals)
+                 : "memory");
+}
+__device__ __forceinline__ void ready_arrive_on_copies(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void ready_arrive(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
+// Waits (acquire) for phase 0 of the barrier, at most kReadyPolls polls;
+// false if it did not complete.
+constexpr uint32_t kReadyPolls = 1u << 20;
+__device__ __forceinline__ bool ready_wait(uint64_t* bar) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    for (uint32_t i = 0; i < kReadyPolls; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(0u)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Bulk L2 prefetch of points p0 .. p0 + count - 1 (clipped to n; 16 bytes
 // each, so the range is 16-byte aligned and a multiple of 16 bytes).
 __device__ __forceinline__ void prefetch_points_l2(const double2* pts, uint64_t n, uint64_t p0, uint64_t count) {
@@ -518,15 +562,22 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // they land; the face table is stored directly.  Every thread must call
 // cp_async_wait_all and then __syncthreads before reading any of the three.
 // Returns the shared root (or null).
+// With ready (an initialised tables-ready barrier, see ready_init) the
+// copies and the face stores arrive on it instead, and a warp reads the
+// tables once ready_wait returns.
 __device__ __forceinline__ const uint64_t* cta_setup_async(const DevIndex& X, uint16_t* s_hlut, DevFace* s_faces,
-                                                           uint64_t* s_root) {
+                                                           uint64_t* s_root, uint64_t* ready = nullptr) {
     static_assert(kJoinBlock == 256, "one 16-byte copy per thread: 128 for the table, 128 for the root");
     const uint32_t t = threadIdx.x;
     if (t < 128) cp_async16(s_hlut + 8 * t, g_hilbert_lut.v + 8 * t);
     const uint32_t root = X.model.enabled ? X.faces[X.model.face].root : kNoRootDev;
     if (root != kNoRootDev && t >= 128) cp_async16(s_root + 2 * (t - 128), X.nodes + (uint64_t)root * 256 + 2 * (t - 128));
-    cp_async_commit();
-    if (t < 6) s_faces[t] = X.faces[t];
+    if (ready) ready_arrive_on_copies(ready);
+    else cp_async_commit();
+    if (t < 6) {
+        s_faces[t] = X.faces[t];
+        if (ready) ready_arrive(ready);
+    }
     return root != kNoRootDev ? s_root : nullptr;
 }
 
@@ -743,11 +794,40 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
 // per-tile global atomics on the job's status words all hit one 32-byte
 // sector and serialise in its L2 slice.  Without it they go to the job's
 // status words directly.
+// Loads the points of tile lt of job J (lane + 32 k) into q; lanes past
+// the job's last point (or an inactive warp) get zeros, which the tile
+// does not use.
+template <int PPT>
+__device__ __forceinline__ void load_tile_points(const JobDesc& J, uint64_t lt, bool active, double2* q) {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const uint64_t p = lt * (32 * PPT) + (threadIdx.x & 31) + 32 * k;
+        q[k] = make_double2(0.0, 0.0);
+        if (active && p < J.n) q[k] = __ldcs(J.pts + p);      // streamed once
+    }
+}
+
+// The start of a probe CTA: zeroes its n_cnt shared counters and (with
+// AGJ_PROBE_READY_BARRIER) initialises its tables-ready barrier, then the
+// CTA's one barrier makes both visible.  Returns the barrier (or null: the
+// tile waits on a CTA barrier after its cell ids instead).
+__device__ __forceinline__ uint64_t* cta_begin(uint32_t* s_cnt, int n_cnt, uint64_t* s_ready) {
+    if ((int)threadIdx.x < n_cnt) s_cnt[threadIdx.x] = 0;
+    if (!AGJ_PROBE_READY_BARRIER) return nullptr;
+    if (threadIdx.x == 0) ready_init(s_ready);
+    __syncthreads();
+    return s_ready;
+}
+
+// With ready (kAsync only) the warp waits on the CTA's tables-ready
+// barrier instead of the CTA barrier; should that wait ever give up, the
+// tile joins nothing and sets the timed-out-wait bit of status[1].
 template <int PPT, int MODE, bool kAsync = false>
 __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
                                            const uint64_t* s_root, uint64_t wt, uint64_t lt, uint32_t gpoly0,
                                            const JoinScratch& S, bool active = true, uint32_t* s_cnt = nullptr,
-                                           uint4* tail = nullptr) {
+                                           uint4* tail = nullptr, uint64_t* ready = nullptr,
+                                           const double2* loaded = nullptr) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t base = lt * (32 * PPT);
     const uint64_t gbase = wt * (32 * PPT);
@@ -760,13 +840,24 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
         const uint64_t p = base + lane + 32 * k;
         ok[k] = false;
         if (active && p < J.n) {
-            const double2 q = __ldcs(J.pts + p);     // streamed once
+            const double2 q = loaded ? loaded[k] : __ldcs(J.pts + p);     // streamed once
             ok[k] = point_ij(J.X.model, q.x, q.y, false, pij[k]);
         }
     }
     if constexpr (kAsync) {
-        cp_async_wait_all();
-        __syncthreads();
+        if (ready) {
+            if (!active) return;
+            if (!ready_wait(ready)) {
+                // the tile's points join nothing and no walk reads the
+                // tables; the join reports the timed-out wait
+                if (lane == 0) atomicOr((unsigned long long*)&J.status[1], (unsigned long long)kErrScanTimeout);
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) ok[k] = false;
+            }
+        } else {
+            cp_async_wait_all();
+            __syncthreads();
+        }
     }
     if (!active) return;
     const uint32_t gathers = probe_cells<PPT>(J.X, faces, s_hlut, s_root, pij, ok, J.pts + base + lane, e,
@@ -803,6 +894,7 @@ __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* face
 // Adds a CTA's shared counters (see probe_tile) to job J's status words
 // and diagnostics; called by every thread after the CTA's tiles.
 __device__ __forceinline__ void flush_cta_counts(const JobDesc& J, const uint32_t* s_cnt) {
+    asm volatile("cp.async.wait_all;" ::: "memory");   // no copy of the CTA's outlives it
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_cnt[0]) atomicAdd((unsigned long long*)&J.status[3], (unsigned long long)s_cnt[0]);
@@ -852,10 +944,18 @@ __global__ void __launch_bounds__(kJoinBlock, probe_min_blocks<PPT, Src, MODE>()
     __shared__ DevFace s_faces[6];
     __shared__ uint32_t s_cnt[3];
     __shared__ uint4 s_tail[kWarpsPerBlock][32 * PPT];
+    __shared__ uint64_t s_ready;
     const uint32_t warp = threadIdx.x >> 5;
     if constexpr (Src::kSingle) {
-        if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
-        const uint64_t* s_root = cta_setup_async(src.job(0).X, s_hlut, s_faces, s_rootbuf);
+        // the tile's point loads are issued first; then the tables-ready
+        // barrier and the shared counters are set up before the CTA's one
+        // barrier ahead of the tile, and each warp waits for the table
+        // copies alone (its cell ids overlap them)
+        const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
+        double2 q[PPT];
+        if (AGJ_PROBE_READY_BARRIER) load_tile_points<PPT>(src.job(0), wt, wt < T, q);
+        uint64_t* ready = cta_begin(s_cnt, 3, &s_ready);
+        const uint64_t* s_root = cta_setup_async(src.job(0).X, s_hlut, s_faces, s_rootbuf, ready);
         if (threadIdx.x == 32) {
             // the points of the CTA one full grid of resident CTAs ahead go
             // to the L2 now, so that CTA finds them there
@@ -865,20 +965,22 @@ __global__ void __launch_bounds__(kJoinBlock, probe_min_blocks<PPT, Src, MODE>()
             const uint64_t ahead = (uint64_t)nsm * probe_min_blocks<PPT, Src, MODE>();
             if (AGJ_PREFETCH_AHEAD) prefetch_points_l2(src.job(0).pts, src.job(0).n, (blockIdx.x + ahead) * group_pts, group_pts);
         }
-        const uint64_t wt = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
-        probe_tile<PPT, MODE, true>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S, wt < T, s_cnt, s_tail[warp]);
+        probe_tile<PPT, MODE, true>(src.job(0), s_faces, s_hlut, s_root, wt, wt, 0, S, wt < T, s_cnt, s_tail[warp],
+                                    ready, AGJ_PROBE_READY_BARRIER ? q : nullptr);
         flush_cta_counts(src.job(0), s_cnt);
     } else {
         const uint64_t g0 = src.t0 / kWarpsPerBlock;
         if constexpr (!kPersist) {                                  // one CTA per 8 tiles of one job
             const uint64_t g = g0 + blockIdx.x;
             if (g * kWarpsPerBlock >= T) return;
-            if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
             const JobDesc& J = src.job(src.find_tile(g * kWarpsPerBlock));
-            const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf);
             const uint64_t wt = g * kWarpsPerBlock + warp;
+            double2 q[PPT];
+            if (AGJ_PROBE_READY_BARRIER) load_tile_points<PPT>(J, wt - J.tile0, true, q);
+            uint64_t* ready = cta_begin(s_cnt, 3, &s_ready);
+            const uint64_t* s_root = cta_setup_async(J.X, s_hlut, s_faces, s_rootbuf, ready);
             probe_tile<PPT, MODE, true>(J, s_faces, s_hlut, s_root, wt, wt - J.tile0, J.poly0, S, true, s_cnt,
-                                        s_tail[warp]);
+                                        s_tail[warp], ready, AGJ_PROBE_READY_BARRIER ? q : nullptr);
             flush_cta_counts(J, s_cnt);
         } else {                                                    // persistent grid
             cta_setup(nullptr, s_hlut, s_faces, s_rootbuf);
