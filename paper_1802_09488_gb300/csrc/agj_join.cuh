@@ -158,15 +158,15 @@ cudaError_t enqueue_join(const Src& src, const JoinLayout& L, char* sc, const Jo
     const bool refine = MODE != kModeApprox && L.exact && L.n_polys;
     if (refine && L.n_tiles) {
         const uint32_t ct = refine_chunk_tiles(L.n_tiles, G.sms, L.n_polys);
-        k_count<<<G.sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, S.poly_count,
-                                          (uint32_t)L.n_polys);
+        k_count<<<refine_sort_grid(L.n_tiles, ct, G.sms, AGJ_COUNT_CTAS_PER_SM), 256, 0, s>>>(
+            S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, S.poly_count, (uint32_t)L.n_polys);
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
             S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.cursor), hdr + 2,
             reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
             reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
-        k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct,
-                                            reinterpret_cast<uint32_t*>(sc + L.cursor),
-                                            reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
+        k_scatter<<<refine_sort_grid(L.n_tiles, ct, G.sms, AGJ_SCATTER_CTAS_PER_SM), 256, 0, s>>>(
+            S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, reinterpret_cast<uint32_t*>(sc + L.cursor),
+            reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
         k_pip<Src><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, reinterpret_cast<const uint2*>(sc + L.sorted),
                                                     reinterpret_cast<const uint4*>(sc + L.cpoly), hdr + 2, S.pass,
                                                     S.tile_count);
@@ -240,14 +240,14 @@ cudaError_t enqueue_join_split(const ManyJobs& src, const JoinLayout& L, char* s
             // the refine over the exact tiles' queue regions (slots relative to tile ta)
             const uint64_t q0 = ta * L.tile_slots;
             const uint32_t ct = refine_chunk_tiles(T - ta, G.sms, L.n_polys);
-            k_count<<<G.sms * 2, 256, 0, s>>>(S.queue + q0, S.tile_cand + ta, T - ta, L.tile_slots, ct, S.poly_count,
-                                              (uint32_t)L.n_polys);
+            k_count<<<refine_sort_grid(T - ta, ct, G.sms, AGJ_COUNT_CTAS_PER_SM), 256, 0, s>>>(
+                S.queue + q0, S.tile_cand + ta, T - ta, L.tile_slots, ct, S.poly_count, (uint32_t)L.n_polys);
             k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
                 S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.cursor), hdr + 2,
                 reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3, err);
-            k_scatter<<<G.sms * 4, 256, 0, s>>>(S.queue + q0, S.tile_cand + ta, T - ta, L.tile_slots, ct,
-                                                reinterpret_cast<uint32_t*>(sc + L.cursor),
-                                                reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
+            k_scatter<<<refine_sort_grid(T - ta, ct, G.sms, AGJ_SCATTER_CTAS_PER_SM), 256, 0, s>>>(
+                S.queue + q0, S.tile_cand + ta, T - ta, L.tile_slots, ct, reinterpret_cast<uint32_t*>(sc + L.cursor),
+                reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
             k_pip<ManyJobs><<<G.pip_grid, kPipBlock, 0, s>>>(src, 32 * PPT, reinterpret_cast<const uint2*>(sc + L.sorted),
                                                             reinterpret_cast<const uint4*>(sc + L.cpoly), hdr + 2,
                                                             S.pass + q0, S.tile_count);

@@ -858,15 +858,15 @@ int launch_join_count(const Index& X, const double* d_points, uint64_t n, cudaSt
         OneJob src;
         src.d = J;
         const uint32_t ct = refine_chunk_tiles(L.n_tiles, sms, L.n_polys);
-        k_count<<<sms * 2, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, S.poly_count,
-                                        (uint32_t)L.n_polys);
+        k_count<<<refine_sort_grid(L.n_tiles, ct, sms, AGJ_COUNT_CTAS_PER_SM), 256, 0, s>>>(
+            S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, S.poly_count, (uint32_t)L.n_polys);
         k_poly_scan<<<(unsigned)L.n_pchunks, 256, 0, s>>>(
             S.poly_count, (uint32_t)L.n_polys, reinterpret_cast<uint32_t*>(sc + L.cursor), hdr + 2,
             reinterpret_cast<uint4*>(sc + L.cpoly), reinterpret_cast<uint64_t*>(sc + L.pchunks), hdr + 3,
             reinterpret_cast<uint64_t*>(sc) + kHdrScanErr);
-        k_scatter<<<sms * 4, 256, 0, s>>>(S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct,
-                                          reinterpret_cast<uint32_t*>(sc + L.cursor),
-                                          reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
+        k_scatter<<<refine_sort_grid(L.n_tiles, ct, sms, AGJ_SCATTER_CTAS_PER_SM), 256, 0, s>>>(
+            S.queue, S.tile_cand, L.n_tiles, L.tile_slots, ct, reinterpret_cast<uint32_t*>(sc + L.cursor),
+            reinterpret_cast<uint2*>(sc + L.sorted), (uint32_t)L.n_polys);
         k_pip<OneJob, true><<<sms * AGJ_PIP_MIN_BLOCKS, kPipBlock, 0, s>>>(
             src, 32 * kJoinSmallPPT, reinterpret_cast<const uint2*>(sc + L.sorted), reinterpret_cast<const uint4*>(sc + L.cpoly),
             hdr + 2, nullptr, nullptr, d_counts);
