@@ -621,6 +621,20 @@ int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, do
 int agj_selftest_scan_timeout(void* stream);
 
 /*
+ * Self-test of the probe's bounded wait for its block's shared tables (no
+ * counterpart in the paper).  A probe block stages the Hilbert table and
+ * the trie's root node in shared memory with asynchronous copies that
+ * arrive on a block-local barrier; each warp waits on that barrier with a
+ * bounded loop (about a second), after which its tile joins nothing and the
+ * join's status[1] gets bit 1 (a device wait timed out).  This stages the
+ * tables on a barrier expecting one arrival too many: it returns
+ * AGJ_ETIMEOUT when the wait ran out and was reported (the expected
+ * outcome), AGJ_OK if it was not, AGJ_ENOMEM / AGJ_ECUDA on setup errors.
+ * The context stays usable.  Synchronises `stream`.
+ */
+int agj_selftest_ready_timeout(void* stream);
+
+/*
  * Measurement utility (no counterpart in the paper): the FP64 fused
  * multiply-add rate of the current device in flop/s (2 per FMA), from the
  * library's own kernel of independent FMA chains on every SM, best of five

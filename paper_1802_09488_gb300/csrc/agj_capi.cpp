@@ -446,6 +446,8 @@ int agj_join_host(const agj_index* index, const double* h_points, uint64_t n, do
 
 int agj_selftest_scan_timeout(void* stream) { return agj::selftest_scan_timeout(as_stream(stream)); }
 
+int agj_selftest_ready_timeout(void* stream) { return agj::selftest_ready_timeout(as_stream(stream)); }
+
 int agj_cell_ids(const double* d_points, uint64_t n, uint64_t* d_ids, void* stream) {
     if (n && (!d_points || !d_ids)) return AGJ_EINVAL;
     return agj::launch_cell_ids(d_points, n, d_ids, as_stream(stream));

@@ -976,6 +976,44 @@ int selftest_scan_timeout(cudaStream_t s) {
     return rc;
 }
 
+// The probe's wait for its CTA's shared tables (ready_wait) is bounded the
+// same way.  Here one CTA stages its tables as the probe does, on a
+// tables-ready barrier that expects one arrival more than the staging
+// makes, so the phase never completes: every warp's wait must run out and
+// report kErrScanTimeout.  The index is all zero (no fast model), so the
+// staging copies only the Hilbert table.
+__global__ void __launch_bounds__(kJoinBlock) k_selftest_ready(const DevIndex X, uint64_t* __restrict__ err) {
+    __shared__ __align__(16) uint16_t s_hlut[1024];
+    __shared__ __align__(16) uint64_t s_rootbuf[256];
+    __shared__ DevFace s_faces[6];
+    __shared__ uint64_t s_ready;
+    if (threadIdx.x == 0) ready_init(&s_ready, kReadyArrivals + 1);
+    __syncthreads();
+    cta_setup_async(X, s_hlut, s_faces, s_rootbuf, &s_ready);
+    const bool ok = ready_wait(&s_ready);
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr((unsigned long long*)err, (unsigned long long)kErrScanTimeout);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+int selftest_ready_timeout(cudaStream_t s) {
+    uint64_t* d = nullptr;
+    if (cudaMalloc(&d, 8) != cudaSuccess) { cudaGetLastError(); return AGJ_ENOMEM; }
+    DevIndex X;
+    memset(&X, 0, sizeof X);
+    int rc = cudaMemsetAsync(d, 0, 8, s) == cudaSuccess ? AGJ_OK : AGJ_ECUDA;
+    if (rc == AGJ_OK) {
+        k_selftest_ready<<<1, kJoinBlock, 0, s>>>(X, d);
+        uint64_t e = 0;
+        if (cudaMemcpyAsync(&e, d, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            rc = AGJ_ECUDA;
+        else
+            rc = (e & kErrScanTimeout) ? AGJ_ETIMEOUT : AGJ_OK;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(d);
+    return rc;
+}
+
 // ---------------------------------------------------------------------------
 // approximate join without any allocation
 // ---------------------------------------------------------------------------

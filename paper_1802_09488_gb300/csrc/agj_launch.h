@@ -36,6 +36,7 @@ int launch_collect_expensive(const Index& X, const double* d_points, uint64_t n,
 int measure_fp64_rate(cudaStream_t s, double* flops_per_s);
 // Runs the tile scan with a predecessor that never publishes (see agj.h).
 int selftest_scan_timeout(cudaStream_t s);
+int selftest_ready_timeout(cudaStream_t s);
 
 // Batched form (agj_batch.cu): a plan for m (index, point count) jobs with
 // its own work space and, with use_graph, an instantiated CUDA graph.

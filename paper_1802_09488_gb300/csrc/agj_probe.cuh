@@ -513,9 +513,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // arrive after their stores.  A warp that waits on it waits for the copies
 // only, not for the CTA's other warps, as a CTA barrier would.
 constexpr uint32_t kReadyArrivals = kJoinBlock + 6;
-__device__ __forceinline__ void ready_init(uint64_t* bar) {
+__device__ __forceinline__ void ready_init(uint64_t* bar, uint32_t arrivals = kReadyArrivals) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
-                 "r"(kReadyArrivals)
+                 "r"(arrivals)
                  : "memory");
 }
 __device__ __forceinline__ void ready_arrive_on_copies(uint64_t* bar) {
@@ -528,20 +528,25 @@ __device__ __forceinline__ void ready_arrive(uint64_t* bar) {
                      (uint32_t)__cvta_generic_to_shared(bar))
                  : "memory");
 }
-// Waits (acquire) for phase 0 of the barrier, at most kReadyPolls polls;
-// false if it did not complete.
-constexpr uint32_t kReadyPolls = 1u << 20;
+__device__ __forceinline__ bool ready_test(uint32_t a) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(0u)
+        : "memory");
+    return done != 0;
+}
+// Waits (acquire) for phase 0 of the barrier: non-blocking tests, with a
+// short sleep between them after the first, kSpinLimit of them at most
+// (about a second, as the scan's look-back); false if it did not complete.
 __device__ __forceinline__ bool ready_wait(uint64_t* bar) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
-    for (uint32_t i = 0; i < kReadyPolls; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(0u)
-            : "memory");
-        if (done) return true;
+    if (ready_test(a)) return true;
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        __nanosleep(32);
+        if (ready_test(a)) return true;
     }
     return false;
 }

@@ -150,6 +150,7 @@ def lib():
             "agj_join_host": (i32, [P, P, u64, P, P, P, P, u64, P, P]),
             "agj_cell_ids": (i32, [P, u64, P, P]),
             "agj_selftest_scan_timeout": (i32, [P]),
+            "agj_selftest_ready_timeout": (i32, [P]),
             "agj_cell_ids_host": (i32, [P, u64, P]),
             "agj_fast_ids_host": (i32, [P, P, u64, P, P]),
             "agj_covers_certified_host": (i32, [P, P, P, u64, P]),

@@ -309,6 +309,17 @@ def test_scan_wait_is_bounded_and_reported(torch, agj, c1):
     assert off[-1] == len(ids) > 0
 
 
+def test_probe_table_wait_is_bounded_and_reported(torch, agj, c1):
+    """A probe block whose shared-table barrier never completes runs out its
+    bounded wait, reports AGJ_ETIMEOUT, and leaves the device usable."""
+    import ctypes
+    rc = agj.lib().agj_selftest_ready_timeout(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 6                      # AGJ_ETIMEOUT
+    ix = agj.Index(c1.polygons, agj.APPROX, c1.eps_m)
+    off, ids = agj.join(ix, _dev(torch, c1.points[:10_000])).to_host()
+    assert off[-1] == len(ids) > 0
+
+
 def test_join_host_large(torch, agj):
     """A 2e7-point host join equals the device join bit for bit, approximate
     and exact, with page-locked or pageable buffers; an ids buffer one short
