@@ -791,8 +791,10 @@ __device__ __forceinline__ void queue_tile(const JobDesc& J, const uint64_t* e, 
 // another.
 // With kAsync the CTA's shared tables are still in flight (cta_setup_async):
 // every thread of the CTA calls this (active false: a warp past the last
-// tile), and the wait and barrier come after the cell ids, before the first
-// table read.
+// tile), and the wait comes after the cell ids, before the first table
+// read: on the tables-ready barrier `ready` when given, else a copy wait and
+// a CTA barrier.  With `loaded` the caller loaded the tile's points
+// (load_tile_points) before the CTA's setup.
 // With s_cnt (a CTA's shared counters: trie entries read, FP64 fallbacks,
 // candidates queued; zeroed before the CTA's barrier) the tile adds its
 // counts there and the kernel flushes them once per CTA (flush_cta_counts):
@@ -824,9 +826,8 @@ __device__ __forceinline__ uint64_t* cta_begin(uint32_t* s_cnt, int n_cnt, uint6
     return s_ready;
 }
 
-// With ready (kAsync only) the warp waits on the CTA's tables-ready
-// barrier instead of the CTA barrier; should that wait ever give up, the
-// tile joins nothing and sets the timed-out-wait bit of status[1].
+// Should the wait on `ready` ever give up, the tile joins nothing and sets
+// the timed-out-wait bit of status[1].
 template <int PPT, int MODE, bool kAsync = false>
 __device__ __forceinline__ void probe_tile(const JobDesc& J, const DevFace* faces, const uint16_t* s_hlut,
                                            const uint64_t* s_root, uint64_t wt, uint64_t lt, uint32_t gpoly0,
