@@ -266,3 +266,21 @@ def test_auto_mode_picks_approx_or_exact_by_budget(agj, oracle):
     with pytest.raises(agj.AgjError) as e:
         agj.Index(w.polygons, agj.AUTO, w.eps_m, host_only=True)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("mode", ["approx", "exact"])
+def test_join_work_space_covers_every_smaller_join(agj, c1, mode):
+    """agj_join_requirements(n) must cover every join of m <= n points, also
+    across the size where a join switches from 2 to 4 points per lane (2^21):
+    buffers sized once for the largest batch are reused for smaller ones."""
+    m = agj.APPROX if mode == "approx" else agj.EXACT
+    ix = agj.Index(c1.polygons, m, c1.eps_m, host_only=True)
+    wide = 1 << 21
+    sizes = sorted({0, 1, 127, 128, 129, 4097, 65537, 1_000_003, wide - 129, wide - 128, wide - 2, wide - 1,
+                    wide, wide + 1, wide + 127, wide + 300, 3 * wide + 5, 10**8})
+    reqs = [ix.requirements(n) for n in sizes]
+    best_ids = best_scratch = 0
+    for n, (ids_cap, scratch) in zip(sizes, reqs):
+        assert ids_cap == n * max(ix.stats()["max_refs"], 1)
+        best_ids, best_scratch = max(best_ids, ids_cap), max(best_scratch, scratch)
+        assert ids_cap == best_ids and scratch == best_scratch, n     # non-decreasing in n
