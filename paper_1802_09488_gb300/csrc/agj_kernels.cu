@@ -3,14 +3,16 @@
 // allocation-free approximate join.  The probe, refine and emit kernels are
 // in agj_probe.cuh; the plain join runs them on one job:
 //
-//   k_probe<approx>  per 64-point warp tile: cell id, face/prefix stage, trie
-//                    walk (Listing "Probe Adaptive Cell Trie"); stores each
+//   k_probe<approx>  per warp tile (128 points from 2^21 points on, 64 below):
+//                    point loads, cell id, face/prefix stage, trie walk
+//                    (Listing "Probe Adaptive Cell Trie"); stores each
 //                    point's tagged entry and the tile's reference count
 //   k_scan_counts    exclusive scan of tile counts (decoupled look-back over
 //                    CTA chunks of 4096 tiles)
 //   k_emit<approx>   offsets and ids (every reference: §V "approx")
 //   k_probe<exact>   the same walk; true hits counted, candidate references
 //                    compacted by warp ballot into a queue
+//   k_count          candidates per polygon (shared histograms per chunk)
 //   k_poly_scan      per-polygon candidate counts -> queue segments + chunks
 //   k_scatter        queue grouped by polygon
 //   k_pip            exact ST_Covers refine (§II "PIP"): one CTA per chunk of
